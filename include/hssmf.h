@@ -1,0 +1,151 @@
+/*
+ * hssmf.h -- C ABI of a GB300 (sm_103a) HSS-structured multifrontal sparse
+ * solver with randomized sampling (Ghysels, Li, Rouet, Williams, Napov,
+ * "An efficient multi-core implementation of a novel HSS-structured
+ * multifrontal solver using randomized sampling", arXiv 1502.07405).
+ *
+ * The problem is the paper's: solve a sparse system A x = b by
+ * reordering (nested dissection, Section 3.1), numerical factorization with
+ * dense or HSS frontal matrices (Sections 3.2 and 4), and a solve used
+ * directly, through iterative refinement or as a GMRES(30) preconditioner
+ * (Sections 3.3, 4.6 and 6.1).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_host are host memory.  Matrix values, right-hand
+ *     sides and solutions may be host or device memory (detected with
+ *     cudaPointerGetAttributes); device memory is read or written on the
+ *     context's stream, host memory is copied through it.
+ *   - Dense blocks are column-major with the leading dimension given.
+ *   - Every call returns an hssmf_status and never aborts or traps.  On an
+ *     error, hssmf_last_error() describes it.  Device-side failures (a zero
+ *     pivot, a non-finite value, a wait that ran out) are recorded in a
+ *     device status word and reported by the call that launched the work.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef HSSMF_H
+#define HSSMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hssmf_ctx hssmf_ctx;
+
+typedef enum {
+  HSSMF_OK = 0,
+  HSSMF_ERR_ARG = 1,       /* bad argument or call order */
+  HSSMF_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+  HSSMF_ERR_SINGULAR = 3,  /* zero or non-finite pivot in a frontal factorization */
+  HSSMF_ERR_NOCONV = 4,    /* the outer iteration did not reach rtol within maxit */
+  HSSMF_ERR_OOM = 5,       /* device memory exhausted */
+  HSSMF_ERR_TIMEOUT = 6    /* a bounded device-side wait ran out */
+} hssmf_status;
+
+/* Arithmetic of the factorization.  The outer iteration, the sparse
+ * residual product and the ID pivot/truncation decisions are FP64 in every
+ * mode. */
+typedef enum {
+  HSSMF_PREC_FP64 = 0,  /* plain FP64 method */
+  HSSMF_PREC_FP32 = 1   /* FP32 fronts, sampling, ID and ULV; FP64 outer loop */
+} hssmf_precision;
+
+typedef struct {
+  double hss_tol;      /* relative ID tolerance eps (Section 5.3 rule) */
+  int d0;              /* initial number of random sample columns */
+  int dd;              /* sample columns added when an ID fails (Section 4.3) */
+  int oversample_p;    /* an ID succeeds if rank <= d - p (default 10) */
+  int hss_min_front;   /* fronts with n_f >= this are HSS (replaces l_s, Section 4.1) */
+  int hss_leaf;        /* HSS leaf size b (default 128, Section 4.2) */
+  int nd_leaf;         /* nested dissection stops at boxes of this side (default 8) */
+  uint64_t seed;       /* key of the counter-based generator of R */
+  int precision;       /* hssmf_precision */
+  int gmres_restart;   /* default 30 (Section 6.1) */
+  int maxit;           /* outer iterations; 0 = apply the factorization once */
+  double rtol;         /* relative residual target ||b - A x|| / ||b|| (default 1e-10) */
+} hssmf_opts;
+
+typedef struct {
+  int n;                 /* matrix order */
+  int n_fronts;          /* elimination-tree nodes */
+  int n_levels;          /* elimination-tree levels */
+  int n_hss_fronts;      /* fronts stored in HSS form */
+  int max_front;         /* largest n_f */
+  int max_rank;          /* largest HSS rank found (row or column) */
+  int max_d;             /* largest number of sample columns used */
+  int adaptive_rounds;   /* total extra sampling rounds over all fronts */
+  int iterations;        /* outer iterations of the last solve (max over rhs) */
+  double relres;         /* final true relative residual (max over rhs) */
+  double factor_flops;   /* algorithmic flops of the last factorization */
+  double factor_bytes;   /* bytes of the stored factors */
+  double t_analyze_ms;   /* host wall time of analyze */
+  double t_factor_ms;    /* device time of the last factor (CUDA events) */
+  double t_solve_ms;     /* device time of the last solve (CUDA events) */
+  int gpu_launches;      /* kernels launched by the last factor + solve */
+} hssmf_stats;
+
+/* Fill *opts with the defaults named above (hss_tol 1e-4, d0 128, dd 64,
+ * p 10, hss_min_front 1024, hss_leaf 128, nd_leaf 8, seed 0, FP64,
+ * restart 30, maxit 300, rtol 1e-10). */
+void hssmf_default_opts(hssmf_opts* opts);
+
+/* Create a context on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  The context owns every
+ * device allocation it makes; hssmf_destroy frees them. */
+hssmf_status hssmf_create(hssmf_ctx** ctx, const hssmf_opts* opts, void* cuda_stream);
+
+/* Symbolic phase for a matrix on an nx x ny x nz grid (nz = 1 in 2D) whose
+ * pattern is given in CSR form in natural numbering x + nx*(y + ny*z)
+ * (host arrays, n + 1 and nnz entries, column indices ascending per row).
+ * The pattern must be structurally symmetric and every edge must join grid
+ * neighbours (|dx|, |dy|, |dz| <= 1).  Computes the geometric nested
+ * dissection and separator reordering (Sections 3.1, 4.2, 6.1), the
+ * elimination tree, I^sep / I^upd of every front (Section 5.4), the HSS
+ * trees of the fronts and all index maps, and uploads them once. */
+hssmf_status hssmf_analyze_grid(hssmf_ctx* ctx, int nx, int ny, int nz, int n,
+                                const int* rowptr_host, const int* colind_host);
+
+/* Numerical factorization (Sections 3.2 and 4): values are the nnz matrix
+ * entries in the CSR order given to analyze (host or device, FP64).
+ * Fronts below hss_min_front are assembled by extend-add and partially
+ * factored by LU with partial pivoting inside F11; larger fronts are
+ * sampled by the skinny extend-add, compressed by Algorithm 1 with the
+ * adaptive rank scheme and ULV-factored with a low-rank Schur update.
+ * HSSMF_ERR_SINGULAR if a pivot is zero or not finite. */
+hssmf_status hssmf_factor(hssmf_ctx* ctx, const double* values);
+
+/* Solve A X = B for nrhs columns (B, X: n x nrhs, leading dimension ldb,
+ * host or device, FP64, natural numbering; X may alias B).  With
+ * opts.maxit == 0 the factorization is applied once (forward then backward
+ * sweep, Section 3.3).  Otherwise iterative refinement (no HSS front) or
+ * right-preconditioned GMRES(restart) with modified Gram-Schmidt and
+ * x0 = 0 (HSS fronts present) runs every column until its true relative
+ * residual is <= rtol; HSSMF_ERR_NOCONV if one does not within maxit. */
+hssmf_status hssmf_solve(hssmf_ctx* ctx, const double* B, double* X, int nrhs, int ldb);
+
+/* Same for A^T X = B: the transposed operators of the factorization in
+ * reverse order, with the outer iteration on A^T. */
+hssmf_status hssmf_solve_T(hssmf_ctx* ctx, const double* B, double* X, int nrhs, int ldb);
+
+hssmf_status hssmf_get_stats(const hssmf_ctx* ctx, hssmf_stats* out);
+
+/* Copy out the symbolic structure (host arrays sized by the caller):
+ *   perm[n]: perm[new] = natural index;
+ *   sep_begin[n_fronts], sep_end[n_fronts], parent[n_fronts] (-1 at the
+ *   root), n_upd[n_fronts]: fronts in postorder, separators in new numbering.
+ * Any pointer may be NULL. */
+hssmf_status hssmf_get_symbolic(const hssmf_ctx* ctx, int* perm, int* sep_begin, int* sep_end,
+                                int* parent, int* n_upd);
+
+/* I^upd of front f (ascending new indices) into upd[n_upd[f]]. */
+hssmf_status hssmf_get_upd(const hssmf_ctx* ctx, int f, int* upd);
+
+const char* hssmf_last_error(const hssmf_ctx* ctx);
+void hssmf_destroy(hssmf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSSMF_H */

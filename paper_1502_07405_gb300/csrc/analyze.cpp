@@ -1,0 +1,245 @@
+// Geometric nested dissection and symbolic factorization (host C++).
+//
+// Ordering rules (Sections 3.1, 4.2 and 6.1 of the paper, with the readings
+// where it is silent):
+//   - boxes are half-open per axis; a box with every side <= nd_leaf is a
+//     leaf of the elimination tree;
+//   - otherwise the longest side is cut (ties: lowest axis) at
+//     mid = lo + len / 2; the plane at mid is the separator, the children
+//     are [lo, mid) and [mid + 1, hi);
+//   - postorder numbering: left subtree, right subtree, separator;
+//   - the vertices of a separator (or leaf box) are ordered by recursive
+//     bisection of its box with the same cut rule into [lo, mid) and
+//     [mid, hi) until a piece has <= hss_leaf vertices; pieces in order, x
+//     fastest inside a piece.  The bisection tree is the F11 cluster tree.
+// Symbolic (Section 5.4): I^upd of a front is the set of vertices numbered
+// after its separator that are adjacent to the separator or in a child's
+// I^upd, ascending.  The F22 cluster tree halves the I^upd list at
+// floor(n/2) until a node has <= hss_leaf indices; the front tree is
+// root -> [F11 tree, F22 tree] (the F11 tree alone without I^upd).
+#include "analyze.h"
+
+#include <algorithm>
+#include <array>
+#include <cstdlib>
+#include <cstdio>
+
+namespace hssmf {
+namespace {
+
+using Box = std::array<int, 6>;  // lo x, lo y, lo z, hi x, hi y, hi z
+
+int cut_axis(const Box& b, int* len) {
+  for (int a = 0; a < 3; ++a) len[a] = b[3 + a] - b[a];
+  int best = 0;
+  for (int a = 1; a < 3; ++a)
+    if (len[a] > len[best]) best = a;
+  return best;
+}
+
+struct Builder {
+  int nx, ny, nz, nd_leaf, hss_leaf;
+  std::vector<int> perm;
+  std::vector<FrontSym> fronts;
+
+  void box_vertices(const Box& b) {
+    for (int z = b[2]; z < b[5]; ++z)
+      for (int y = b[1]; y < b[4]; ++y)
+        for (int x = b[0]; x < b[3]; ++x) perm.push_back(x + nx * (y + ny * z));
+  }
+
+  // Recursive bisection of a box into pieces; appends vertices and adds the
+  // cluster nodes (postorder) to tree with ranges offset by the local start.
+  int bisect(const Box& b, ClusterTree& tree, int& local) {
+    long vol = (long)(b[3] - b[0]) * (b[4] - b[1]) * (b[5] - b[2]);
+    if (vol <= hss_leaf) {
+      int lo = local;
+      box_vertices(b);
+      local += (int)vol;
+      return tree.add(lo, local);
+    }
+    int len[3];
+    int a = cut_axis(b, len);
+    int mid = b[a] + len[a] / 2;
+    Box l = b, r = b;
+    l[3 + a] = mid;
+    r[a] = mid;
+    int lo = local;
+    int t1 = bisect(l, tree, local);
+    int t2 = bisect(r, tree, local);
+    return tree.add(lo, local, t1, t2);
+  }
+
+  int add_front(const Box& sepbox, int first, int c1, int c2) {
+    FrontSym f;
+    f.first = first;
+    f.sep_begin = (int)perm.size();
+    int local = 0;
+    f.k_node = bisect(sepbox, f.tree, local);
+    f.sep_end = (int)perm.size();
+    if (c1 >= 0) {
+      f.child[0] = c1;
+      f.child[1] = c2;
+      f.nchild = 2;
+    }
+    fronts.push_back(std::move(f));
+    int me = (int)fronts.size() - 1;
+    if (c1 >= 0) {
+      fronts[c1].parent = me;
+      fronts[c2].parent = me;
+    }
+    return me;
+  }
+
+  int rec(const Box& b) {
+    int len[3];
+    int a = cut_axis(b, len);
+    int first = (int)perm.size();
+    if (len[0] <= nd_leaf && len[1] <= nd_leaf && len[2] <= nd_leaf)
+      return add_front(b, first, -1, -1);
+    int mid = b[a] + len[a] / 2;
+    Box l = b, r = b, s = b;
+    l[3 + a] = mid;
+    r[a] = mid + 1;
+    s[a] = mid;
+    s[3 + a] = mid + 1;
+    int c1 = rec(l);
+    int c2 = rec(r);
+    return add_front(s, first, c1, c2);
+  }
+};
+
+int halving(ClusterTree& t, int lo, int hi, int b) {
+  if (hi - lo <= b) return t.add(lo, hi);
+  int mid = lo + (hi - lo) / 2;
+  int l = halving(t, lo, mid, b);
+  int r = halving(t, mid, hi, b);
+  return t.add(lo, hi, l, r);
+}
+
+}  // namespace
+
+std::string analyze_grid(int nx, int ny, int nz, int n, const int* rowptr, const int* colind,
+                         int nd_leaf, int hss_leaf, Symbolic& out) {
+  if (nx < 1 || ny < 1 || nz < 1 || (long)nx * ny * nz != n) return "grid dims do not match n";
+  if (nd_leaf < 1 || hss_leaf < 1) return "nd_leaf and hss_leaf must be positive";
+  if (!rowptr || !colind) return "null CSR pattern";
+  if (rowptr[0] != 0) return "rowptr[0] must be 0";
+  for (int i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return "rowptr not monotone";
+  out = Symbolic();
+  out.nx = nx; out.ny = ny; out.nz = nz; out.n = n;
+  out.nnz = rowptr[n];
+  out.nd_leaf = nd_leaf;
+  out.hss_leaf = hss_leaf;
+  // pattern checks: in range, ascending, grid neighbours, structurally symmetric
+  out.tpos.assign(out.nnz, -1);
+  for (int i = 0; i < n; ++i) {
+    int xi = i % nx, yi = (i / nx) % ny, zi = i / (nx * ny);
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      int j = colind[p];
+      if (j < 0 || j >= n) return "column index out of range";
+      if (p > rowptr[i] && colind[p - 1] >= j) return "column indices not ascending";
+      int xj = j % nx, yj = (j / nx) % ny, zj = j / (nx * ny);
+      if (std::abs(xi - xj) > 1 || std::abs(yi - yj) > 1 || std::abs(zi - zj) > 1)
+        return "pattern edge joins vertices that are not grid neighbours";
+      const int* b = colind + rowptr[j];
+      const int* e = colind + rowptr[j + 1];
+      const int* f = std::lower_bound(b, e, i);
+      if (f == e || *f != i) return "pattern is not structurally symmetric";
+      out.tpos[p] = (int)(f - colind);
+    }
+  }
+  Builder B{nx, ny, nz, nd_leaf, hss_leaf, {}, {}};
+  B.perm.reserve(n);
+  B.rec(Box{0, 0, 0, nx, ny, nz});
+  out.perm = std::move(B.perm);
+  out.fronts = std::move(B.fronts);
+  if ((int)out.perm.size() != n) return "internal: ordering size mismatch";
+  out.iperm.assign(n, -1);
+  for (int v = 0; v < n; ++v) out.iperm[out.perm[v]] = v;
+
+  // symbolic factorization, bottom-up (fronts are in postorder)
+  std::vector<int> buf;
+  for (size_t fi = 0; fi < out.fronts.size(); ++fi) {
+    FrontSym& f = out.fronts[fi];
+    buf.clear();
+    for (int v = f.sep_begin; v < f.sep_end; ++v) {
+      int o = out.perm[v];
+      for (int p = rowptr[o]; p < rowptr[o + 1]; ++p) {
+        int g = out.iperm[colind[p]];
+        if (g >= f.sep_end) buf.push_back(g);
+      }
+    }
+    for (int c = 0; c < f.nchild; ++c)
+      for (int g : out.fronts[f.child[c]].upd)
+        if (g >= f.sep_end) buf.push_back(g);
+    std::sort(buf.begin(), buf.end());
+    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+    f.upd = buf;
+    f.height = 0;
+    for (int c = 0; c < f.nchild; ++c)
+      f.height = std::max(f.height, out.fronts[f.child[c]].height + 1);
+  }
+  int maxh = 0;
+  for (auto& f : out.fronts) maxh = std::max(maxh, f.height);
+  out.levels.assign(maxh + 1, {});
+  for (size_t fi = 0; fi < out.fronts.size(); ++fi) out.levels[out.fronts[fi].height].push_back((int)fi);
+
+  // local index of a new index g in front f (-1 if absent)
+  auto local_index = [&](const FrontSym& f, int g) -> int {
+    if (g >= f.sep_begin && g < f.sep_end) return g - f.sep_begin;
+    auto it = std::lower_bound(f.upd.begin(), f.upd.end(), g);
+    if (it == f.upd.end() || *it != g) return -1;
+    return f.ns() + (int)(it - f.upd.begin());
+  };
+
+  for (size_t fi = 0; fi < out.fronts.size(); ++fi) {
+    FrontSym& f = out.fronts[fi];
+    // cluster tree: F11 already built by bisect(); add F22 and the root
+    if (f.nu() > 0) {
+      f.q_node = halving(f.tree, f.ns(), f.nf(), hss_leaf);
+      f.tree.add(0, f.nf(), f.k_node, f.q_node);
+    }
+    // positions of I^upd in the parent's I
+    if (f.parent >= 0) {
+      const FrontSym& p = out.fronts[f.parent];
+      f.pos_in_parent.resize(f.nu());
+      for (int j = 0; j < f.nu(); ++j) {
+        int l = local_index(p, f.upd[j]);
+        if (l < 0) return "internal: I^upd not contained in the parent's index set";
+        f.pos_in_parent[j] = l;
+      }
+    } else if (f.nu() > 0) {
+      return "internal: root front with a non-empty I^upd";
+    }
+    // local sparse part A_i = [A(sep, I) ; A(upd, sep)]
+    int nf = f.nf(), ns = f.ns();
+    std::vector<std::vector<std::pair<int, int>>> rows(nf);
+    for (int r = 0; r < ns; ++r) {
+      int o = out.perm[f.sep_begin + r];
+      for (int p = rowptr[o]; p < rowptr[o + 1]; ++p) {
+        int g = out.iperm[colind[p]];
+        int c = local_index(f, g);
+        if (c >= 0) {
+          rows[r].push_back({c, p});
+          if (c >= ns) rows[c].push_back({r, out.tpos[p]});  // A(upd, sep) via the transpose entry
+        } else if (g >= f.sep_end) {
+          return "internal: separator neighbour outside the front";
+        }
+      }
+    }
+    f.a_rowptr.assign(nf + 1, 0);
+    for (int r = 0; r < nf; ++r) {
+      std::sort(rows[r].begin(), rows[r].end());
+      f.a_rowptr[r + 1] = f.a_rowptr[r] + (int)rows[r].size();
+    }
+    f.a_col.resize(f.a_rowptr[nf]);
+    f.a_val.resize(f.a_rowptr[nf]);
+    for (int r = 0, k = 0; r < nf; ++r)
+      for (auto& e : rows[r]) { f.a_col[k] = e.first; f.a_val[k] = e.second; ++k; }
+  }
+  return "";
+}
+
+}  // namespace hssmf

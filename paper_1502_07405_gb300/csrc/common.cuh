@@ -1,0 +1,44 @@
+// Shared device-side definitions of the sm_103a kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace hssmf {
+
+// Bits of the device status word (sticky, OR-ed by kernels, read by the host
+// at the end of every phase).  Kernels never trap: they record and return.
+enum : unsigned {
+  ST_ZERO_PIVOT = 1u,    // zero pivot in a partial LU / root LU
+  ST_NONFINITE = 2u,     // non-finite pivot or norm
+  ST_TIMEOUT = 4u,       // a bounded wait ran out
+  ST_BAD_INDEX = 8u,     // an index map entry out of range (skipped)
+};
+
+struct GemmJob {
+  // C[crow(i), j] = alpha * sum_k op(A)(i, k) op(B)(k, j) + beta * C[crow(i), j]
+  // op(A) is M x K, op(B) is K x N; column-major with leading dimensions.
+  const void* A;
+  const void* B;
+  void* C;
+  const int* crow;  // optional row map of C (nullptr = identity)
+  long long lda, ldb, ldc;
+  int M, N, K;
+  int ta, tb;  // 1 = use the transpose
+  double alpha, beta;
+};
+
+struct Tile {  // one 64 x 64 output tile of one job
+  int job, tm, tn;
+};
+
+constexpr int GEMM_TILE = 64;
+
+inline int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }
+
+__device__ __forceinline__ void set_status(unsigned* st, unsigned bit) { atomicOr(st, bit); }
+
+template <typename T>
+__device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+}  // namespace hssmf

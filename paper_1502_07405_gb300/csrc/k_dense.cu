@@ -1,0 +1,265 @@
+// Dense-front kernels: batched GEMM, front assembly by extend-add
+// (Section 3.2, eq. extend-add), blocked partial LU with row partial
+// pivoting restricted to F11 (Section 3.2).
+#include <cfloat>
+
+#include "kernels.h"
+
+namespace hssmf {
+
+// ---------------------------------------------------------------------------
+// Batched variable-size GEMM over a tile list (64 x 64 tiles, 256 threads,
+// 4 x 4 outputs per thread, K staged through shared memory 16 at a time).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(const GemmJob* __restrict__ jobs,
+                                              const Tile* __restrict__ tiles) {
+  const Tile tl = tiles[blockIdx.x];
+  const GemmJob jb = jobs[tl.job];
+  const T* A = static_cast<const T*>(jb.A);
+  const T* B = static_cast<const T*>(jb.B);
+  T* C = static_cast<T*>(jb.C);
+  const int m0 = tl.tm * 64, n0 = tl.tn * 64;
+  __shared__ T As[16][64 + 1];
+  __shared__ T Bs[16][64 + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < jb.K; k0 += 16) {
+    // A tile: op(A)(m0 + i, k0 + k), i < 64, k < 16
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int i, k;
+      if (!jb.ta) { i = e & 63; k = e >> 6; } else { k = e & 15; i = e >> 4; }
+      int gi = m0 + i, gk = k0 + k;
+      T v = T(0);
+      if (gi < jb.M && gk < jb.K) v = jb.ta ? A[gk + (long long)gi * jb.lda] : A[gi + (long long)gk * jb.lda];
+      As[k][i] = v;
+    }
+    // B tile: op(B)(k0 + k, n0 + j), k < 16, j < 64
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int j, k;
+      if (!jb.tb) { k = e & 15; j = e >> 4; } else { j = e & 63; k = e >> 6; }
+      int gj = n0 + j, gk = k0 + k;
+      T v = T(0);
+      if (gj < jb.N && gk < jb.K) v = jb.tb ? B[gj + (long long)gk * jb.ldb] : B[gk + (long long)gj * jb.ldb];
+      Bs[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  const T alpha = T(jb.alpha), beta = T(jb.beta);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int gj = n0 + ty + 16 * j;
+    if (gj >= jb.N) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int gi = m0 + tx + 16 * i;
+      if (gi >= jb.M) continue;
+      long long r = jb.crow ? jb.crow[gi] : gi;
+      T* c = C + r + (long long)gj * jb.ldc;
+      *c = (jb.beta == 0.0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
+    }
+  }
+}
+
+template <typename T>
+void Kern<T>::gemm(const GemmJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  k_gemm<T><<<ntiles, 256, 0, s>>>(jobs, tiles);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Front assembly (A3): F_i = A_i (+) U_child0 (+) U_child1, written once per
+// element as a gather over the children's update matrices (children in
+// order: deterministic, no atomics), then the entries of A_i of the tile's
+// rows are added.  Tiles are 32 x 32; tile list entries (front, tm, tn).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_assemble(const DFront* __restrict__ fr,
+                                                  const int* __restrict__ ints, T* __restrict__ ar,
+                                                  const double* __restrict__ values,
+                                                  const Tile* __restrict__ tiles) {
+  const Tile tl = tiles[blockIdx.x];
+  const DFront f = fr[tl.job];
+  __shared__ T tile[32][33];
+  const int r = tl.tm * 32 + (threadIdx.x & 31);
+  const int cbase = tl.tn * 32;
+  for (int cc = threadIdx.x >> 5; cc < 32; cc += 8) {
+    int c = cbase + cc;
+    T v = T(0);
+    if (r < f.nf && c < f.nf) {
+      for (int k = 0; k < f.nchild; ++k) {
+        const DFront ch = fr[k == 0 ? f.child0 : f.child1];
+        const int* inv = ints + f.inv_off + (long long)k * f.nf;
+        int ir = inv[r], ic = inv[c];
+        if (ir >= 0 && ic >= 0) v += ar[ch.u_off + ir + (long long)ic * ch.u_ld];
+      }
+    }
+    tile[threadIdx.x & 31][cc] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32 && r < f.nf) {
+    const int* arow = ints + f.arow_off;
+    const int nnz_f = arow[f.nf];
+    const int* acol = arow + f.nf + 1;
+    const int* aval = acol + nnz_f;
+    for (int p = arow[r]; p < arow[r + 1]; ++p) {
+      int c = acol[p] - cbase;
+      if (c >= 0 && c < 32) tile[threadIdx.x][c] += T(values[aval[p]]);
+    }
+  }
+  __syncthreads();
+  for (int cc = threadIdx.x >> 5; cc < 32; cc += 8) {
+    int c = cbase + cc;
+    if (r < f.nf && c < f.nf) ar[f.off + r + (long long)c * f.nf] = tile[threadIdx.x & 31][cc];
+  }
+}
+
+template <typename T>
+void Kern<T>::assemble(const DevSym& ds, T* arena, const double* values, const Tile* tiles,
+                       int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  k_assemble<T><<<ntiles, 256, 0, s>>>(ds.fronts, ds.ints, arena, values, tiles);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Panel factorization of columns [k0, k0 + nb) of every listed front: pivot
+// search restricted to rows < ns (first maximum of |a| wins), full-row swap
+// across all nf columns, scaling of the column below the pivot and rank-1
+// update of the remaining panel columns.  One CTA per front.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_panel(const DFront* __restrict__ fr, T* __restrict__ ar,
+                                               int* __restrict__ piv, const int* __restrict__ flist,
+                                               int k0, int nb, unsigned* status) {
+  const DFront f = fr[flist[blockIdx.x]];
+  if (k0 >= f.ns) return;
+  const int k1 = min(k0 + nb, f.ns);
+  T* F = ar + f.off;
+  const long long ld = f.nf;
+  __shared__ T s_val[8];
+  __shared__ int s_idx[8];
+  __shared__ int s_p;
+  for (int j = k0; j < k1; ++j) {
+    // pivot search over rows j .. ns-1 of column j
+    T best = T(-1);
+    int bi = f.ns;
+    for (int r = j + threadIdx.x; r < f.ns; r += blockDim.x) {
+      T a = tabs(F[r + j * ld]);
+      if (a > best) { best = a; bi = r; }  // ascending r per thread: first max kept
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      T ob = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { s_val[threadIdx.x >> 5] = best; s_idx[threadIdx.x >> 5] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T b = s_val[0];
+      int i = s_idx[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (s_val[w] > b || (s_val[w] == b && s_idx[w] < i)) { b = s_val[w]; i = s_idx[w]; }
+      if (!(b > T(0)) || !isfinite((double)b)) {
+        set_status(status, b == T(0) ? ST_ZERO_PIVOT : ST_NONFINITE);
+        i = j;
+      }
+      s_p = i;
+      piv[f.piv_off + j] = i;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j) {
+      for (int c = threadIdx.x; c < f.nf; c += blockDim.x) {
+        T t = F[j + c * ld];
+        F[j + c * ld] = F[p + c * ld];
+        F[p + c * ld] = t;
+      }
+    }
+    __syncthreads();
+    const T d = F[j + j * ld];
+    const T inv = (d != T(0)) ? T(1) / d : T(0);
+    for (int r = j + 1 + threadIdx.x; r < f.nf; r += blockDim.x) {
+      T l = F[r + j * ld] * inv;
+      F[r + j * ld] = l;
+      for (int c = j + 1; c < k1; ++c) F[r + c * ld] -= l * F[j + c * ld];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void Kern<T>::panel_lu(const DevSym& ds, T* arena, int* piv, const int* flist, int nfr, int k0,
+                       int nb, unsigned* status, cudaStream_t s) {
+  if (nfr <= 0) return;
+  k_panel<T><<<nfr, 256, 0, s>>>(ds.fronts, arena, piv, flist, k0, nb, status);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Row block of U12 after a panel: rows [k0, k1), columns [k1, nf) are
+// replaced by L_panel^-1 times themselves (unit lower, nb <= 32).  Grid:
+// (front, chunk of 128 columns); one column per thread.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) k_panel_trsm(const DFront* __restrict__ fr,
+                                                    T* __restrict__ ar,
+                                                    const int* __restrict__ flist, int k0, int nb) {
+  const DFront f = fr[flist[blockIdx.y]];
+  if (k0 >= f.ns) return;
+  const int k1 = min(k0 + nb, f.ns);
+  const int w = k1 - k0;
+  T* F = ar + f.off;
+  const long long ld = f.nf;
+  __shared__ T L[32][33];
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    int i = e & 31, j = e >> 5;
+    L[i][j] = (i < w && j < w) ? F[(k0 + i) + (k0 + j) * ld] : T(0);
+  }
+  __syncthreads();
+  const int c = k1 + blockIdx.x * 128 + threadIdx.x;
+  if (c >= f.nf) return;
+  T x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) x[i] = (i < w) ? F[(k0 + i) + c * ld] : T(0);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+#pragma unroll
+    for (int r = i + 1; r < 32; ++r) x[r] -= L[r][i] * x[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    if (i < w) F[(k0 + i) + c * ld] = x[i];
+}
+
+template <typename T>
+void Kern<T>::panel_trsm(const DevSym& ds, T* arena, const int* flist, int nfr, int k0, int nb,
+                         int max_chunks, cudaStream_t s) {
+  if (nfr <= 0 || max_chunks <= 0) return;
+  dim3 g(max_chunks, nfr);
+  k_panel_trsm<T><<<g, 128, 0, s>>>(ds.fronts, arena, flist, k0, nb);
+  count_launch();
+}
+
+template struct Kern<double>;
+template struct Kern<float>;
+
+}  // namespace hssmf

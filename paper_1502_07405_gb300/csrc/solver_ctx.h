@@ -1,0 +1,121 @@
+// The solver context behind the opaque hssmf_ctx handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/hssmf.h"
+#include "analyze.h"
+#include "kernels.h"
+
+namespace hssmf {
+
+struct StepPlan {  // one panel step of the dense partial LU of a level
+  int k0 = 0, trsm_chunks = 0, tile_off = 0, ntiles = 0;
+};
+
+struct LevelPlan {
+  std::vector<int> dense, hss;
+  int all_off = 0, nall = 0, dense_off = 0, ndense = 0, hss_off = 0;
+  int max_nf = 0, max_nu = 0;
+  int asm_off = 0, asm_n = 0;
+  std::vector<StepPlan> steps;
+};
+
+struct HssState;  // HSS-front factor data (hss.cu)
+
+}  // namespace hssmf
+
+struct hssmf_ctx {
+  hssmf_opts opts{};
+  bool fp32 = false;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool analyzed = false, factored = false;
+  hssmf::Symbolic sym;
+  std::vector<hssmf::LevelPlan> plan;
+  std::vector<int> is_hss;
+  int n_hss = 0;
+  hssmf::DevSym ds{};
+  std::vector<hssmf::DFront> fronts_host;
+  std::vector<hssmf::GemmJob> dense_jobs_host;
+  std::vector<int> ints_host, flist_host, rowptr_host, colind_host;
+  std::vector<hssmf::Tile> tiles_host;
+  long long piv_total_host = 0;
+  bool on_device = false;
+  // device memory owned by the context
+  std::vector<void*> owned, owned_host;
+  unsigned* d_status = nullptr;
+  int *d_perm = nullptr, *d_rowptr = nullptr, *d_colind = nullptr, *d_tpos = nullptr;
+  double* d_values = nullptr;
+  hssmf::DFront* d_fronts = nullptr;
+  int* d_ints = nullptr;
+  int* d_flist = nullptr;
+  hssmf::Tile* d_tiles = nullptr;
+  hssmf::GemmJob* d_jobs = nullptr;
+  int* d_piv = nullptr;
+  void* d_arena = nullptr;
+  long long arena_elems = 0;
+  // solve workspace
+  void* d_W = nullptr;
+  size_t w_bytes = 0;
+  int w_nrhs = -1;
+  double* d_io = nullptr;
+  size_t io_bytes = 0;
+  // Krylov workspace
+  size_t kry_bytes = 0;
+  int kry_nrhs = -1;
+  double *k_V = nullptr, *k_Z = nullptr, *k_x = nullptr, *k_r = nullptr, *k_w = nullptr,
+         *k_b = nullptr, *k_t = nullptr, *k_H = nullptr, *k_cs = nullptr, *k_sn = nullptr,
+         *k_g = nullptr, *k_y = nullptr, *k_part = nullptr, *k_s = nullptr;
+  int* k_active = nullptr;
+  void* h_pin = nullptr;
+  // statistics
+  hssmf_stats stats{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double dense_flops = 0.0, hss_flops = 0.0, factor_bytes_dense = 0.0, hss_bytes = 0.0;
+  int hss_max_rank = 0, hss_max_d = 0, hss_rounds = 0;
+  int factor_launches = 0;
+  int last_iters = 0;
+  double last_relres = 0.0;
+  // HSS-front state
+  hssmf::HssState* hss = nullptr;
+
+  hssmf_status fail(hssmf_status st, const std::string& msg);
+  hssmf_status cuda_check(cudaError_t e, const char* what);
+  void* dalloc(size_t bytes);
+  void free_all();
+  void reset_device_pointers() {
+    d_status = nullptr;
+    d_perm = d_rowptr = d_colind = d_tpos = nullptr;
+    d_values = nullptr;
+    d_fronts = nullptr;
+    d_ints = d_flist = d_piv = nullptr;
+    d_tiles = nullptr;
+    d_jobs = nullptr;
+    d_arena = nullptr;
+    d_W = nullptr;
+    w_bytes = 0;
+    w_nrhs = -1;
+    d_io = nullptr;
+    io_bytes = 0;
+    kry_bytes = 0;
+    kry_nrhs = -1;
+    h_pin = nullptr;
+  }
+  hssmf_status upload(void* dst, const void* src, size_t bytes);
+  hssmf_status read_status();
+  hssmf_status build_plan();
+  hssmf_status ensure_device();
+  template <typename T>
+  hssmf_status factor_impl();
+  template <typename T>
+  hssmf_status apply_impl(const double* b, double* x, int nrhs, int transpose);
+  hssmf_status apply(const double* b, double* x, int nrhs, int transpose);
+  hssmf_status ensure_krylov(int nrhs);
+  hssmf_status read_cols(const double* dev, long long stride, int nrhs, std::vector<double>& out);
+  hssmf_status outer_solve(const double* B, long long ldb, double* X, long long ldx, int nrhs,
+                           int transpose);
+};
