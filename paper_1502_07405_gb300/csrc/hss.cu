@@ -1,22 +1,1148 @@
-// HSS fronts on the device: placeholder until the HSS kernels land.
+// HSS frontal matrices on the device: host orchestration (Section 4).
+//
+// All HSS fronts of one elimination-tree level are processed together, and
+// inside them all nodes of one HSS-tree height: every step below is one
+// batched launch over (front, node) jobs.
+//
+// Per level:
+//   1. R_i(r, c) = G(seed, I_i(r), c) (the child blocks R(I^upd_child, :) are
+//      generated from the child's global indices, which is eq. Rmerge);
+//      S^r = A_i R (+) U_child R_child, S^c = A_i^T R (+) U_child^T R_child
+//      (eq. FtimesR; children's update matrices are dense in HBM).
+//   2. Algorithm 1 bottom-up, heights of the front trees in order.  A round
+//      processes every node whose children are compressed with all d
+//      columns; IDs already accepted are kept (Section 2.2.1).  A node fails
+//      if its rank exceeds d - p and its size; then d += dd for its front
+//      and the next round samples only the new columns.
+//   3. ULV-like factorization of F11 (Section 2.3), low-rank Schur update
+//      Theta^* Phi (Section 4.4), and the dense update matrix
+//      F22 - Theta^* Phi for the parent.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "hss.h"
+#include "hss_kernels.h"
 
 namespace hssmf {
 
-struct HssState {};
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+struct Pool {  // device bump allocator over large chunks
+  std::vector<std::pair<char*, size_t>> chunks;
+  size_t ci = 0, off = 0, used = 0, peak = 0;
+  char* alloc(size_t bytes) {
+    bytes = std::max<size_t>((bytes + ALIGN - 1) / ALIGN * ALIGN, ALIGN);
+    for (;;) {
+      if (ci < chunks.size()) {
+        if (off + bytes <= chunks[ci].second) {
+          char* p = chunks[ci].first + off;
+          off += bytes;
+          used += bytes;
+          peak = std::max(peak, used);
+          return p;
+        }
+        ++ci;
+        off = 0;
+        continue;
+      }
+      size_t sz = std::max<size_t>(bytes, (size_t)256 << 20);
+      char* p = nullptr;
+      if (cudaMalloc(&p, sz) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      chunks.push_back({p, sz});
+    }
+  }
+  void reset() { ci = 0; off = 0; used = 0; }
+  void release() {
+    for (auto& c : chunks) cudaFree(c.first);
+    chunks.clear();
+    reset();
+  }
+};
+
+struct Ring {  // job descriptors: pinned host staging -> device, reused after a sync
+  char* h = nullptr;
+  char* d = nullptr;
+  size_t cap = 0, off = 0;
+  bool grow(size_t need) {
+    if (h) cudaFreeHost(h);
+    if (d) cudaFree(d);
+    h = d = nullptr;
+    cap = std::max(need, (size_t)64 << 20);
+    if (cudaMallocHost(&h, cap) != cudaSuccess || cudaMalloc(&d, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    off = 0;
+    return true;
+  }
+  template <class J>
+  const J* put(const std::vector<J>& v, cudaStream_t s) {
+    size_t bytes = std::max<size_t>((v.size() * sizeof(J) + ALIGN - 1) / ALIGN * ALIGN, ALIGN);
+    if (off + bytes > cap) {
+      cudaStreamSynchronize(s);
+      off = 0;
+      if (bytes > cap && !grow(bytes)) return nullptr;
+    }
+    if (!v.empty()) {
+      std::memcpy(h + off, v.data(), v.size() * sizeof(J));
+      cudaMemcpyAsync(d + off, h + off, v.size() * sizeof(J), cudaMemcpyHostToDevice, s);
+    }
+    const J* p = (const J*)(d + off);
+    off += bytes;
+    return p;
+  }
+  void release() {
+    if (h) cudaFreeHost(h);
+    if (d) cudaFree(d);
+    h = d = nullptr;
+    cap = off = 0;
+  }
+};
+
+struct NodeRt {
+  int m = 0, mc = 0, n = 0;  // ID row counts (S^r, S^c) and node size
+  int kr = 0, kc = 0;
+  bool done = false, extracted = false;
+  void *D = nullptr, *B12 = nullptr, *B21 = nullptr;
+  int *piv_r = nullptr, *piv_c = nullptr;
+  void *Xr = nullptr, *Xc = nullptr;
+  int *Ir = nullptr, *Ic = nullptr;
+  int slot = -1;
+  // per round
+  void *Yr = nullptr, *Yc = nullptr, *Srp = nullptr, *Scp = nullptr, *Rrp = nullptr, *Rcp = nullptr;
+  // factor
+  void *Uexp = nullptr, *Vexp = nullptr, *Dt = nullptr, *Vt = nullptr, *tau = nullptr;
+  int* lupiv = nullptr;
+  void *Ubig = nullptr, *Vbig = nullptr;
+  // solve scratch
+  void *bt = nullptr, *bo = nullptr, *w = nullptr, *x = nullptr;
+};
+
+struct FrontRt {
+  int f = -1, nf = 0, ns = 0, nu = 0;
+  int d = 0, dprev = 0, dalloc = 0, rounds = 0;
+  bool compressed = false, failed = false;
+  void *R = nullptr, *Sr = nullptr, *Sc = nullptr;
+  void* Rch[2] = {nullptr, nullptr};
+  long long gidx_off = 0;
+  long long pos_off[2] = {-1, -1};  // ints offset of the children's positions in I_i
+  std::vector<NodeRt> nd;
+  std::vector<int> height;
+  int tree_h = 0;
+  // low-rank Schur and solve data
+  void* Z = nullptr;
+  int k = -1, q = -1, root = -1;
+  std::vector<int> f11;  // F11 subtree nodes in postorder
+};
+
+}  // namespace
+
+struct HssState {
+  Pool fac, lvl, rnd, sol;
+  Ring ring;
+  int* d_ranks = nullptr;
+  int* h_ranks = nullptr;
+  int rank_cap = 0;
+  long long iota_off = 0;
+  std::vector<int> index;  // front id -> slot in fronts (-1 if dense)
+  std::vector<FrontRt> fronts;
+  int sol_nrhs = -1;
+  double flops = 0.0, bytes = 0.0;
+};
 
 hssmf_status hss_prepare(hssmf_ctx& c) {
-  if (c.n_hss > 0) return c.fail(HSSMF_ERR_ARG, "HSS fronts are not available in this build");
+  hss_release(c);
+  if (c.n_hss == 0) return HSSMF_OK;
+  HssState* H = new HssState();
+  c.hss = H;
+  const Symbolic& S = c.sym;
+  H->index.assign(S.fronts.size(), -1);
+  c.hss_first_level = -1;
+  for (size_t h = 0; h < c.plan.size() && c.hss_first_level < 0; ++h)
+    if (!c.plan[h].hss.empty()) c.hss_first_level = (int)h;
+  int max_nf = 0;
+  for (size_t i = 0; i < S.fronts.size(); ++i) max_nf = std::max(max_nf, S.fronts[i].nf());
+  H->iota_off = (long long)c.ints_host.size();
+  for (int i = 0; i < max_nf; ++i) c.ints_host.push_back(i);
+  for (size_t i = 0; i < S.fronts.size(); ++i) {
+    if (!c.is_hss[i]) continue;
+    const FrontSym& f = S.fronts[i];
+    H->index[i] = (int)H->fronts.size();
+    H->fronts.emplace_back();
+    FrontRt& F = H->fronts.back();
+    F.f = (int)i;
+    F.nf = f.nf();
+    F.ns = f.ns();
+    F.nu = f.nu();
+    F.gidx_off = (long long)c.ints_host.size();
+    for (int v = f.sep_begin; v < f.sep_end; ++v) c.ints_host.push_back(v);
+    c.ints_host.insert(c.ints_host.end(), f.upd.begin(), f.upd.end());
+    for (int k = 0; k < f.nchild; ++k) {
+      const FrontSym& ch = S.fronts[f.child[k]];
+      F.pos_off[k] = (long long)c.ints_host.size();
+      c.ints_host.insert(c.ints_host.end(), ch.pos_in_parent.begin(), ch.pos_in_parent.end());
+    }
+    const ClusterTree& t = f.tree;
+    F.nd.assign(t.size(), NodeRt());
+    F.height.assign(t.size(), 0);
+    for (int u = 0; u < t.size(); ++u) {
+      F.nd[u].n = t.hi[u] - t.lo[u];
+      if (!t.leaf(u)) F.height[u] = 1 + std::max(F.height[t.c1[u]], F.height[t.c2[u]]);
+    }
+    F.tree_h = F.height[t.root()];
+    F.k = f.k_node;
+    F.q = f.q_node;
+    F.root = t.root();
+    // F11 subtree in postorder (nodes are stored in postorder, the subtree is contiguous)
+    std::vector<int> st{F.k};
+    while (!st.empty()) {
+      int u = st.back();
+      st.pop_back();
+      F.f11.push_back(u);
+      if (!t.leaf(u)) {
+        st.push_back(t.c1[u]);
+        st.push_back(t.c2[u]);
+      }
+    }
+    std::sort(F.f11.begin(), F.f11.end());
+  }
   return HSSMF_OK;
 }
-hssmf_status hss_device_init(hssmf_ctx&) { return HSSMF_OK; }
-void hss_release(hssmf_ctx& c) { c.hss = nullptr; }
+
+hssmf_status hss_device_init(hssmf_ctx& c) {
+  if (!c.hss) return HSSMF_OK;
+  HssState& H = *c.hss;
+  if (!H.ring.grow((size_t)64 << 20)) return c.fail(HSSMF_ERR_OOM, "job ring allocation failed");
+  H.rank_cap = 1 << 20;
+  if (cudaMalloc(&H.d_ranks, sizeof(int) * H.rank_cap) != cudaSuccess ||
+      cudaMallocHost(&H.h_ranks, sizeof(int) * H.rank_cap) != cudaSuccess) {
+    cudaGetLastError();
+    return c.fail(HSSMF_ERR_OOM, "rank buffer allocation failed");
+  }
+  return HSSMF_OK;
+}
+
+void hss_release(hssmf_ctx& c) {
+  if (!c.hss) return;
+  HssState& H = *c.hss;
+  H.fac.release();
+  H.lvl.release();
+  H.rnd.release();
+  H.sol.release();
+  H.ring.release();
+  if (H.d_ranks) cudaFree(H.d_ranks);
+  if (H.h_ranks) cudaFreeHost(H.h_ranks);
+  delete c.hss;
+  c.hss = nullptr;
+}
+
+namespace {
+
 template <typename T>
-hssmf_status hss_factor_level(hssmf_ctx& c, int) { return c.fail(HSSMF_ERR_ARG, "no HSS"); }
+struct Ctx {  // per-call helpers
+  hssmf_ctx& c;
+  HssState& H;
+  cudaStream_t s;
+  bool oom = false;
+  std::vector<GemmJob> gj;
+  std::vector<CopyJob> cj;
+  explicit Ctx(hssmf_ctx& cc) : c(cc), H(*cc.hss), s(cc.stream) {}
+  T* arena() { return static_cast<T*>(c.d_arena); }
+  T* A(Pool& p, long long elems) {
+    char* q = p.alloc(sizeof(T) * (size_t)std::max(elems, 1LL));
+    if (!q) oom = true;
+    return (T*)q;
+  }
+  int* I(Pool& p, long long n) {
+    char* q = p.alloc(sizeof(int) * (size_t)std::max(n, 1LL));
+    if (!q) oom = true;
+    return (int*)q;
+  }
+  const int* ints(long long off) const { return c.d_ints + off; }
+  // C = alpha op(A) op(B) + beta C
+  void gemm(const void* A_, long long lda, int ta, const void* B_, long long ldb, int tb, void* C_,
+            long long ldc, int M, int N, int K, double alpha, double beta, const int* crow = nullptr) {
+    if (M <= 0 || N <= 0) return;
+    if (K <= 0 && beta == 1.0) return;
+    GemmJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.A = A_; j.B = B_; j.C = C_; j.crow = crow;
+    j.lda = lda; j.ldb = ldb; j.ldc = ldc;
+    j.M = M; j.N = N; j.K = std::max(K, 0);
+    j.ta = ta; j.tb = tb; j.alpha = alpha; j.beta = beta;
+    gj.push_back(j);
+    H.flops += 2.0 * M * N * std::max(K, 0);
+  }
+  void flush_gemm() {
+    if (gj.empty()) return;
+    std::vector<Tile> tiles;
+    for (size_t i = 0; i < gj.size(); ++i) {
+      int tm = ceil_div(gj[i].M, 64), tn = ceil_div(gj[i].N, 64);
+      for (int b = 0; b < tn; ++b)
+        for (int a = 0; a < tm; ++a) tiles.push_back(Tile{(int)i, a, b});
+    }
+    const GemmJob* dj = H.ring.put(gj, s);
+    const Tile* dt = H.ring.put(tiles, s);
+    if (!dj || !dt) { oom = true; gj.clear(); return; }
+    Kern<T>::gemm(dj, dt, (int)tiles.size(), s);
+    gj.clear();
+  }
+  void copy(const void* src, long long lds, int trans, void* dst, long long ldd, int rows, int cols,
+            const int* rmap = nullptr, const int* cmap = nullptr, const void* src2 = nullptr,
+            long long lds2 = 0, int split = 0) {
+    if (rows <= 0 || cols <= 0) return;
+    CopyJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.src = src; j.src2 = src2; j.lds2 = lds2; j.split = split;
+    j.dst = dst; j.rmap = rmap; j.cmap = cmap; j.lds = lds; j.ldd = ldd;
+    j.rows = rows; j.cols = cols; j.src_trans = trans;
+    cj.push_back(j);
+  }
+  void flush_copy() {
+    if (cj.empty()) return;
+    const CopyJob* d = H.ring.put(cj, s);
+    if (!d) { oom = true; cj.clear(); return; }
+    HssKern<T>::copy(d, (int)cj.size(), s);
+    cj.clear();
+  }
+  template <class J, class F>
+  void launch(std::vector<J>& v, F f) {
+    if (v.empty()) return;
+    const J* d = H.ring.put(v, s);
+    if (!d) { oom = true; v.clear(); return; }
+    f(d, (int)v.size());
+    v.clear();
+  }
+};
+
+// Columns [dprev, d) of R, R(I^upd_child, :), S^r and S^c of every listed
+// front (eq. FtimesR; eq. Rmerge holds because R depends only on global rows).
 template <typename T>
-hssmf_status hss_solve_fwd_level(hssmf_ctx& c, int, T*, int, int) { return c.fail(HSSMF_ERR_ARG, "no HSS"); }
+void sample_fronts(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
+  hssmf_ctx& c = X.c;
+  const Symbolic& S = c.sym;
+  std::vector<PhiloxJob> pj;
+  std::vector<SampleAJob> sj;
+  int max_rows = 0, max_nf = 0;
+  for (FrontRt* F : fs) {
+    const FrontSym& f = S.fronts[F->f];
+    const int c0 = F->dprev, c1 = F->d;
+    if (c1 <= c0) continue;
+    pj.push_back(PhiloxJob{X.ints(F->gidx_off), F->R, F->nf, F->nf, c0, c1, 0});
+    max_rows = std::max(max_rows, F->nf);
+    max_nf = std::max(max_nf, F->nf);
+    for (int k = 0; k < f.nchild; ++k) {
+      const DFront& ch = c.fronts_host[f.child[k]];
+      if (ch.nu == 0) continue;
+      pj.push_back(PhiloxJob{X.ints(ch.upd_off), F->Rch[k], ch.nu, ch.nu, c0, c1, 0});
+      max_rows = std::max(max_rows, ch.nu);
+    }
+    sj.push_back(SampleAJob{F->Sr, F->Sc, F->R, F->nf, F->f, c0, c1, 0});
+  }
+  X.launch(pj, [&](const PhiloxJob* d, int n) { HssKern<T>::philox(d, n, max_rows, c.opts.seed, X.s); });
+  X.launch(sj, [&](const SampleAJob* d, int n) { HssKern<T>::sample_a(c.ds, c.d_values, d, n, max_nf, X.s); });
+  for (int k = 0; k < 2; ++k) {  // one launch per child slot: deterministic order of the sums
+    for (FrontRt* F : fs) {
+      const FrontSym& f = S.fronts[F->f];
+      if (k >= f.nchild) continue;
+      const DFront& ch = c.fronts_host[f.child[k]];
+      const int c0 = F->dprev, w = F->d - F->dprev;
+      if (ch.nu == 0 || w <= 0) continue;
+      const T* U = X.arena() + ch.u_off;
+      const T* Rk = (const T*)F->Rch[k] + (long long)c0 * ch.nu;
+      const int* pos = X.ints(F->pos_off[k]);
+      X.gemm(U, ch.u_ld, 0, Rk, ch.nu, 0, (T*)F->Sr + (long long)c0 * F->nf, F->nf, ch.nu, w, ch.nu,
+             1.0, 1.0, pos);
+      X.gemm(U, ch.u_ld, 1, Rk, ch.nu, 0, (T*)F->Sc + (long long)c0 * F->nf, F->nf, ch.nu, w, ch.nu,
+             1.0, 1.0, pos);
+    }
+    X.flush_gemm();
+  }
+}
+
+// Room for d columns in R, R_child, S^r, S^c (old columns copied over).
 template <typename T>
-hssmf_status hss_solve_bwd_level(hssmf_ctx& c, int, T*, T*, int, int) { return c.fail(HSSMF_ERR_ARG, "no HSS"); }
+void ensure_cols(Ctx<T>& X, FrontRt& F, const FrontSym& f) {
+  if (F.d <= F.dalloc) return;
+  const int na = std::min(F.nf, F.d + X.c.opts.dd);
+  auto grow = [&](void*& p, int rows) {
+    T* q = X.A(X.H.lvl, (long long)rows * na);
+    if (p && F.dprev > 0 && q)
+      cudaMemcpyAsync(q, p, sizeof(T) * (size_t)rows * F.dprev, cudaMemcpyDeviceToDevice, X.s);
+    p = q;
+  };
+  grow(F.R, F.nf);
+  grow(F.Sr, F.nf);
+  grow(F.Sc, F.nf);
+  for (int k = 0; k < f.nchild; ++k) grow(F.Rch[k], X.c.fronts_host[f.child[k]].nu);
+  F.dalloc = na;
+}
+
+// Algorithm 1 with the adaptive rank scheme over all fronts of a level.
+template <typename T>
+hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
+  hssmf_ctx& c = X.c;
+  HssState& H = X.H;
+  const Symbolic& S = c.sym;
+  const int p = c.opts.oversample_p;
+  const double eps = c.opts.hss_tol;
+  const int* iota = X.ints(H.iota_off);
+  for (FrontRt* F : fs) {
+    for (auto& N : F->nd) {
+      int n = N.n;
+      N = NodeRt();
+      N.n = n;
+    }
+    F->d = std::min(c.opts.d0, F->nf);
+    F->dprev = 0;
+    F->dalloc = 0;
+    F->rounds = 0;
+    F->compressed = false;
+    F->R = F->Sr = F->Sc = nullptr;
+    F->Rch[0] = F->Rch[1] = nullptr;
+    ensure_cols(X, *F, S.fronts[F->f]);
+  }
+  std::vector<FrontRt*> todo = fs;
+  sample_fronts(X, todo);
+  struct Item {
+    FrontRt* F;
+    int t;
+  };
+  while (!todo.empty()) {
+    if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during HSS compression");
+    int maxh = 0;
+    for (FrontRt* F : todo) maxh = std::max(maxh, F->tree_h);
+    for (int lv = 0; lv < maxh; ++lv) {
+      std::vector<Item> batch;
+      for (FrontRt* F : todo) {
+        const ClusterTree& tr = S.fronts[F->f].tree;
+        for (int t = 0; t < tr.size(); ++t) {
+          if (t == tr.root() || F->height[t] != lv) continue;
+          if (!tr.leaf(t) && !(F->nd[tr.c1[t]].done && F->nd[tr.c2[t]].done)) continue;
+          batch.push_back({F, t});
+        }
+      }
+      if (batch.empty()) continue;
+      for (auto& it : batch) {
+        const ClusterTree& tr = S.fronts[it.F->f].tree;
+        NodeRt& N = it.F->nd[it.t];
+        if (tr.leaf(it.t)) {
+          N.m = N.mc = N.n;
+        } else {
+          const NodeRt &a = it.F->nd[tr.c1[it.t]], &b = it.F->nd[tr.c2[it.t]];
+          N.m = a.kr + b.kr;
+          N.mc = a.kc + b.kc;
+        }
+      }
+      // (a) D of the leaves, B of the sibling pairs: submatrices of F_i
+      std::vector<ExtractJob> ej;
+      for (auto& it : batch) {
+        const ClusterTree& tr = S.fronts[it.F->f].tree;
+        NodeRt& N = it.F->nd[it.t];
+        if (N.extracted) continue;
+        N.extracted = true;
+        if (tr.leaf(it.t)) {
+          N.D = X.A(H.fac, (long long)N.n * N.n);
+          ej.push_back(ExtractJob{iota + tr.lo[it.t], iota + tr.lo[it.t], N.D, N.n, it.F->f, N.n, N.n, 0});
+        } else {
+          const NodeRt &a = it.F->nd[tr.c1[it.t]], &b = it.F->nd[tr.c2[it.t]];
+          N.B12 = X.A(H.fac, (long long)a.kr * b.kc);
+          N.B21 = X.A(H.fac, (long long)b.kr * a.kc);
+          if (a.kr > 0 && b.kc > 0)
+            ej.push_back(ExtractJob{a.Ir, b.Ic, N.B12, a.kr, it.F->f, a.kr, b.kc, 0});
+          if (b.kr > 0 && a.kc > 0)
+            ej.push_back(ExtractJob{b.Ir, a.Ic, N.B21, b.kr, it.F->f, b.kr, a.kc, 0});
+        }
+      }
+      X.launch(ej, [&](const ExtractJob* d, int n) {
+        HssKern<T>::extract(c.ds, c.d_values, X.arena(), d, n, X.s);
+      });
+      // (b) samples of the node before the ID, stored transposed (d x rows)
+      for (auto& it : batch) {
+        const ClusterTree& tr = S.fronts[it.F->f].tree;
+        FrontRt& F = *it.F;
+        NodeRt& N = F.nd[it.t];
+        const int d = F.d, lo = tr.lo[it.t];
+        N.Yr = X.A(H.rnd, (long long)d * N.m);
+        N.Yc = X.A(H.rnd, (long long)d * N.mc);
+        if (tr.leaf(it.t)) {
+          X.copy((T*)F.Sr + lo, F.nf, 1, N.Yr, d, d, N.m);
+          X.copy((T*)F.Sc + lo, F.nf, 1, N.Yc, d, d, N.mc);
+        } else {
+          const NodeRt &a = F.nd[tr.c1[it.t]], &b = F.nd[tr.c2[it.t]];
+          X.copy(a.Srp, d, 0, N.Yr, d, d, a.kr);
+          X.copy(b.Srp, d, 0, (T*)N.Yr + (long long)a.kr * d, d, d, b.kr);
+          X.copy(a.Scp, d, 0, N.Yc, d, d, a.kc);
+          X.copy(b.Scp, d, 0, (T*)N.Yc + (long long)a.kc * d, d, d, b.kc);
+        }
+      }
+      X.flush_copy();
+      for (auto& it : batch) {
+        const ClusterTree& tr = S.fronts[it.F->f].tree;
+        FrontRt& F = *it.F;
+        NodeRt& N = F.nd[it.t];
+        const int d = F.d, lo = tr.lo[it.t];
+        if (tr.leaf(it.t)) {  // S^r - D R, S^c - D^* R (transposed)
+          X.gemm((T*)F.R + lo, F.nf, 1, N.D, N.n, 1, N.Yr, d, d, N.m, N.n, -1.0, 1.0);
+          X.gemm((T*)F.R + lo, F.nf, 1, N.D, N.n, 0, N.Yc, d, d, N.mc, N.n, -1.0, 1.0);
+        } else {  // [S^r_1 - B12 R^r_2; S^r_2 - B21 R^r_1], [S^c_1 - B21^* R^c_2; S^c_2 - B12^* R^c_1]
+          const NodeRt &a = F.nd[tr.c1[it.t]], &b = F.nd[tr.c2[it.t]];
+          X.gemm(b.Rrp, d, 0, N.B12, std::max(a.kr, 1), 1, N.Yr, d, d, a.kr, b.kc, -1.0, 1.0);
+          X.gemm(a.Rrp, d, 0, N.B21, std::max(b.kr, 1), 1, (T*)N.Yr + (long long)a.kr * d, d, d, b.kr,
+                 a.kc, -1.0, 1.0);
+          X.gemm(b.Rcp, d, 0, N.B21, std::max(b.kr, 1), 0, N.Yc, d, d, a.kc, b.kr, -1.0, 1.0);
+          X.gemm(a.Rcp, d, 0, N.B12, std::max(a.kr, 1), 0, (T*)N.Yc + (long long)a.kc * d, d, d, b.kc,
+                 a.kr, -1.0, 1.0);
+        }
+      }
+      X.flush_gemm();
+      // (c) interpolative decompositions of the nodes not yet compressed
+      std::vector<IdJob> ij;
+      std::vector<Item> idn;
+      int maxm = 0;
+      for (auto& it : batch) {
+        FrontRt& F = *it.F;
+        NodeRt& N = F.nd[it.t];
+        if (N.done) continue;
+        const int d = F.d;
+        if (!N.piv_r) {
+          N.piv_r = X.I(H.fac, N.m);
+          N.piv_c = X.I(H.fac, N.mc);
+          N.Xr = X.A(H.fac, (long long)N.m * N.m / 4 + 1);
+          N.Xc = X.A(H.fac, (long long)N.mc * N.mc / 4 + 1);
+        }
+        T* Wr = X.A(H.rnd, (long long)d * N.m);
+        T* Wc = X.A(H.rnd, (long long)d * N.mc);
+        const int slot = (int)idn.size();
+        ij.push_back(IdJob{N.Yr, Wr, N.piv_r, N.Xr, H.d_ranks + 2 * slot, d, N.m});
+        ij.push_back(IdJob{N.Yc, Wc, N.piv_c, N.Xc, H.d_ranks + 2 * slot + 1, d, N.mc});
+        maxm = std::max(maxm, std::max(N.m, N.mc));
+        idn.push_back(it);
+        H.flops += 4.0 * d * (double)N.m * std::min(N.m, d) + 4.0 * d * (double)N.mc * std::min(N.mc, d);
+      }
+      if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during HSS compression");
+      if (!ij.empty()) {
+        if ((int)ij.size() > H.rank_cap) return c.fail(HSSMF_ERR_ARG, "too many IDs in one level");
+        const IdJob* dj = H.ring.put(ij, X.s);
+        if (!dj) return c.fail(HSSMF_ERR_OOM, "job ring");
+        if (HssKern<T>::batched_id(dj, (int)ij.size(), maxm, eps, X.s) < 0)
+          return c.fail(HSSMF_ERR_ARG, "an HSS node is too large for the ID kernel");
+        hssmf_status st = c.cuda_check(cudaMemcpyAsync(H.h_ranks, H.d_ranks, sizeof(int) * ij.size(),
+                                                       cudaMemcpyDeviceToHost, X.s), "ranks");
+        if (st) return st;
+        if ((st = c.cuda_check(cudaStreamSynchronize(X.s), "ID"))) return st;
+        H.ring.off = 0;
+        for (size_t i = 0; i < idn.size(); ++i) {
+          FrontRt& F = *idn[i].F;
+          NodeRt& N = F.nd[idn[i].t];
+          const int kr = H.h_ranks[2 * i], kc = H.h_ranks[2 * i + 1], d = F.d;
+          const bool cap = d >= F.nf;
+          const bool ok_r = kr <= d - p || kr == N.m || cap;
+          const bool ok_c = kc <= d - p || kc == N.mc || cap;
+          if (ok_r && ok_c) {
+            N.done = true;
+            N.kr = kr;
+            N.kc = kc;
+            N.slot = 1;  // newly compressed: skeleton lists still to build
+            c.hss_max_rank = std::max(c.hss_max_rank, std::max(kr, kc));
+          }
+        }
+      }
+      // (d) after the ID: S <- S(J, :), R^r = V^* R, R^c = U^* R, skeleton sets
+      std::vector<IntGatherJob> ig;
+      for (auto& it : batch) {
+        const ClusterTree& tr = S.fronts[it.F->f].tree;
+        FrontRt& F = *it.F;
+        NodeRt& N = F.nd[it.t];
+        if (!N.done) continue;
+        const int d = F.d, lo = tr.lo[it.t];
+        N.Srp = X.A(H.rnd, (long long)d * N.kr);
+        N.Scp = X.A(H.rnd, (long long)d * N.kc);
+        X.copy(N.Yr, d, 0, N.Srp, d, d, N.kr, nullptr, N.piv_r);
+        X.copy(N.Yc, d, 0, N.Scp, d, d, N.kc, nullptr, N.piv_c);
+        T* Rpc = X.A(H.rnd, (long long)d * N.mc);
+        T* Rpr = X.A(H.rnd, (long long)d * N.m);
+        if (tr.leaf(it.t)) {
+          X.copy((T*)F.R + lo, F.nf, 1, Rpc, d, d, N.mc, nullptr, N.piv_c);
+          X.copy((T*)F.R + lo, F.nf, 1, Rpr, d, d, N.m, nullptr, N.piv_r);
+        } else {
+          const NodeRt &a = F.nd[tr.c1[it.t]], &b = F.nd[tr.c2[it.t]];
+          X.copy(a.Rrp, d, 0, Rpc, d, d, N.mc, nullptr, N.piv_c, b.Rrp, d, a.kc);
+          X.copy(a.Rcp, d, 0, Rpr, d, d, N.m, nullptr, N.piv_r, b.Rcp, d, a.kr);
+        }
+        N.Rrp = Rpc;
+        N.Rcp = Rpr;
+        if (N.slot == 1) {
+          N.slot = 0;
+          N.Ir = X.I(H.fac, N.kr);
+          N.Ic = X.I(H.fac, N.kc);
+          if (tr.leaf(it.t)) {
+            if (N.kr) ig.push_back(IntGatherJob{iota + lo, iota + lo, N.piv_r, N.Ir, N.kr, N.m});
+            if (N.kc) ig.push_back(IntGatherJob{iota + lo, iota + lo, N.piv_c, N.Ic, N.kc, N.mc});
+          } else {
+            const NodeRt &a = F.nd[tr.c1[it.t]], &b = F.nd[tr.c2[it.t]];
+            if (N.kr) ig.push_back(IntGatherJob{a.Ir, b.Ir, N.piv_r, N.Ir, N.kr, a.kr});
+            if (N.kc) ig.push_back(IntGatherJob{a.Ic, b.Ic, N.piv_c, N.Ic, N.kc, a.kc});
+          }
+        }
+      }
+      X.flush_copy();
+      for (auto& it : batch) {
+        FrontRt& F = *it.F;
+        NodeRt& N = F.nd[it.t];
+        if (!N.done) continue;
+        const int d = F.d;
+        X.gemm((T*)N.Rrp + (long long)N.kc * d, d, 0, N.Xc, std::max(N.kc, 1), 1, N.Rrp, d, d, N.kc,
+               N.mc - N.kc, 1.0, 1.0);
+        X.gemm((T*)N.Rcp + (long long)N.kr * d, d, 0, N.Xr, std::max(N.kr, 1), 1, N.Rcp, d, d, N.kr,
+               N.m - N.kr, 1.0, 1.0);
+      }
+      X.flush_gemm();
+      X.launch(ig, [&](const IntGatherJob* d, int n) { HssKern<T>::int_gather(d, n, X.s); });
+    }
+    // end of the round: fronts with every non-root node compressed are done
+    std::vector<ExtractJob> ej;
+    std::vector<FrontRt*> next;
+    for (FrontRt* F : todo) {
+      const ClusterTree& tr = S.fronts[F->f].tree;
+      bool all = true;
+      for (int t = 0; t < tr.size(); ++t)
+        if (t != tr.root()) all = all && F->nd[t].done;
+      if (all) {
+        const int r = tr.root();
+        NodeRt& N = F->nd[r];
+        if (tr.leaf(r)) {
+          N.m = N.mc = N.n;
+          N.D = X.A(H.fac, (long long)N.n * N.n);
+          ej.push_back(ExtractJob{iota, iota, N.D, N.n, F->f, N.n, N.n, 0});
+        } else {
+          const NodeRt &a = F->nd[tr.c1[r]], &b = F->nd[tr.c2[r]];
+          N.m = a.kr + b.kr;
+          N.mc = a.kc + b.kc;
+          N.B12 = X.A(H.fac, (long long)a.kr * b.kc);
+          N.B21 = X.A(H.fac, (long long)b.kr * a.kc);
+          if (a.kr > 0 && b.kc > 0) ej.push_back(ExtractJob{a.Ir, b.Ic, N.B12, a.kr, F->f, a.kr, b.kc, 0});
+          if (b.kr > 0 && a.kc > 0) ej.push_back(ExtractJob{b.Ir, a.Ic, N.B21, b.kr, F->f, b.kr, a.kc, 0});
+        }
+        F->compressed = true;
+        c.hss_max_d = std::max(c.hss_max_d, F->d);
+        c.hss_rounds += F->rounds;
+      } else {
+        F->dprev = F->d;
+        F->d = std::min(F->d + c.opts.dd, F->nf);
+        F->rounds++;
+        ensure_cols(X, *F, S.fronts[F->f]);
+        next.push_back(F);
+      }
+    }
+    X.launch(ej, [&](const ExtractJob* d, int n) { HssKern<T>::extract(c.ds, c.d_values, X.arena(), d, n, X.s); });
+    hssmf_status st = c.cuda_check(cudaStreamSynchronize(X.s), "compression round");
+    if (st) return st;
+    H.ring.off = 0;
+    H.rnd.reset();  // the round's scratch is dead
+    todo.swap(next);
+    if (!todo.empty()) sample_fronts(X, todo);
+  }
+  return X.oom ? c.fail(HSSMF_ERR_OOM, "device memory exhausted during HSS compression") : HSSMF_OK;
+}
+
+// ULV solve of F11 (postorder up the F11 tree, root LU, back down), for
+// every listed front: x = F11^-1 b, nrhs[i] columns, in and out with their
+// own leading dimensions (may alias).  Scratch from ``pool``.
+template <typename T>
+void ulv_solve(Ctx<T>& X, const std::vector<FrontRt*>& fs, const std::vector<const T*>& bin,
+               const std::vector<long long>& ldin, const std::vector<T*>& xout,
+               const std::vector<long long>& ldout, const std::vector<int>& nrhs, Pool& pool) {
+  const Symbolic& S = X.c.sym;
+  int maxh = 0;
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    maxh = std::max(maxh, F.height[F.k]);
+    for (int t : F.f11) {
+      NodeRt& N = F.nd[t];
+      N.bt = X.A(pool, (long long)N.m * nrhs[i]);
+      N.bo = X.A(pool, (long long)N.m * nrhs[i]);
+      N.w = X.A(pool, (long long)std::max(N.kc, 1) * nrhs[i]);
+      N.x = X.A(pool, (long long)N.m * nrhs[i]);
+    }
+  }
+  if (X.oom) return;
+  for (int lv = 0; lv <= maxh; ++lv) {
+    std::vector<UlvFwdJob> jobs;
+    for (size_t i = 0; i < fs.size(); ++i) {
+      FrontRt& F = *fs[i];
+      const ClusterTree& tr = S.fronts[F.f].tree;
+      for (int t : F.f11) {
+        if (F.height[t] != lv) continue;
+        NodeRt& N = F.nd[t];
+        UlvFwdJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.Dt = N.Dt;
+        j.is_root = t == F.k;
+        j.piv = j.is_root ? N.lupiv : N.piv_r;
+        j.X = N.Xr;
+        j.Vt = N.Vt;
+        j.leaf = tr.leaf(t);
+        j.m = N.m;
+        j.k = N.kr;
+        j.kc = N.kc;
+        j.mc = N.mc;
+        j.nrhs = nrhs[i];
+        if (j.leaf) {
+          j.bsrc = bin[i] + tr.lo[t];
+          j.ldbsrc = ldin[i];
+        } else {
+          const NodeRt &a = F.nd[tr.c1[t]], &b = F.nd[tr.c2[t]];
+          j.Vloc = N.Vexp;
+          j.B12 = N.B12;
+          j.B21 = N.B21;
+          j.bh1 = (const T*)a.bo + (a.m - a.kr);
+          j.bh2 = (const T*)b.bo + (b.m - b.kr);
+          j.ldbh1 = a.m;
+          j.ldbh2 = b.m;
+          j.wc1 = a.w;
+          j.wc2 = b.w;
+          j.k1 = a.kr;
+          j.k2 = b.kr;
+          j.kc1 = a.kc;
+          j.kc2 = b.kc;
+        }
+        j.bt = N.bt;
+        j.bo = N.bo;
+        j.w = N.w;
+        jobs.push_back(j);
+      }
+    }
+    X.launch(jobs, [&](const UlvFwdJob* d, int n) { HssKern<T>::ulv_fwd(d, n, X.s); });
+  }
+  for (int lv = maxh; lv >= 0; --lv) {
+    std::vector<UlvBwdJob> jobs;
+    for (size_t i = 0; i < fs.size(); ++i) {
+      FrontRt& F = *fs[i];
+      const ClusterTree& tr = S.fronts[F.f].tree;
+      for (int t : F.f11) {
+        if (F.height[t] != lv) continue;
+        NodeRt& N = F.nd[t];
+        if (t == F.k) {
+          if (tr.leaf(t)) X.copy(N.bo, N.m, 0, xout[i] + tr.lo[t], ldout[i], N.m, nrhs[i]);
+          continue;
+        }
+        const int P = tr.parent[t];
+        const NodeRt& PN = F.nd[P];
+        const T* xpar = (const T*)(P == F.k ? PN.bo : PN.x);
+        const int off = (t == tr.c1[P]) ? 0 : F.nd[tr.c1[P]].kr;
+        UlvBwdJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.Dt = N.Dt;
+        j.tau = N.tau;
+        j.x1 = N.bo;
+        j.xh2 = xpar + off;
+        j.ldxh2 = PN.m;
+        if (tr.leaf(t)) {
+          j.out = xout[i] + tr.lo[t];
+          j.ldout = ldout[i];
+        } else {
+          j.out = N.x;
+          j.ldout = N.m;
+        }
+        j.m = N.m;
+        j.k = N.kr;
+        j.nrhs = nrhs[i];
+        jobs.push_back(j);
+      }
+    }
+    X.flush_copy();
+    X.launch(jobs, [&](const UlvBwdJob* d, int n) { HssKern<T>::ulv_bwd(d, n, X.s); });
+  }
+}
+
+// ULV-like factorization of F11 (Section 2.3), then Theta^* Phi and the dense
+// update matrix F22 - Theta^* Phi of every front of the level (Section 4.4).
+template <typename T>
+hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
+  hssmf_ctx& c = X.c;
+  HssState& H = X.H;
+  const Symbolic& S = c.sym;
+  // explicit interpolative bases U = Pi_r [I; E_r], V = Pi_c [I; E_c]
+  std::vector<BasisJob> bj;
+  for (FrontRt* F : fs) {
+    const ClusterTree& tr = S.fronts[F->f].tree;
+    for (int t = 0; t < tr.size(); ++t) {
+      if (t == tr.root()) continue;
+      NodeRt& N = F->nd[t];
+      N.Uexp = X.A(H.fac, (long long)N.m * N.kr);
+      N.Vexp = X.A(H.fac, (long long)N.mc * N.kc);
+      if (N.kr) bj.push_back(BasisJob{N.piv_r, N.Xr, N.Uexp, std::max(N.m, 1), N.m, N.kr});
+      if (N.kc) bj.push_back(BasisJob{N.piv_c, N.Xc, N.Vexp, std::max(N.mc, 1), N.mc, N.kc});
+    }
+  }
+  X.launch(bj, [&](const BasisJob* d, int n) { HssKern<T>::basis(d, n, X.s); });
+  // ULV, bottom-up over the F11 trees
+  int maxh = 0;
+  for (FrontRt* F : fs) maxh = std::max(maxh, F->height[F->k]);
+  for (int lv = 0; lv <= maxh; ++lv) {
+    std::vector<std::pair<FrontRt*, int>> items;
+    for (FrontRt* F : fs)
+      for (int t : F->f11)
+        if (F->height[t] == lv) items.push_back({F, t});
+    if (items.empty()) continue;
+    // merged diagonal block [[Dh1, B12 Vh2^T], [B21 Vh1^T, Dh2]] (leaf: D)
+    std::vector<T*> Dm(items.size());
+    for (size_t i = 0; i < items.size(); ++i) {
+      FrontRt& F = *items[i].first;
+      const int t = items[i].second;
+      const ClusterTree& tr = S.fronts[F.f].tree;
+      NodeRt& N = F.nd[t];
+      const int m = N.m;
+      const bool root = t == F.k;
+      Dm[i] = X.A(root ? H.fac : H.lvl, (long long)m * m);
+      if (tr.leaf(t)) {
+        X.copy(N.D, m, 0, Dm[i], m, m, m);
+      } else {
+        const NodeRt &a = F.nd[tr.c1[t]], &b = F.nd[tr.c2[t]];
+        const long long oa = (a.m - a.kr) + (long long)(a.m - a.kr) * a.m;
+        const long long ob = (b.m - b.kr) + (long long)(b.m - b.kr) * b.m;
+        X.copy((const T*)a.Dt + oa, a.m, 0, Dm[i], m, a.kr, a.kr);
+        X.copy((const T*)b.Dt + ob, b.m, 0, Dm[i] + a.kr + (long long)a.kr * m, m, b.kr, b.kr);
+      }
+    }
+    X.flush_copy();
+    for (size_t i = 0; i < items.size(); ++i) {
+      FrontRt& F = *items[i].first;
+      const int t = items[i].second;
+      const ClusterTree& tr = S.fronts[F.f].tree;
+      if (tr.leaf(t)) continue;
+      NodeRt& N = F.nd[t];
+      const NodeRt &a = F.nd[tr.c1[t]], &b = F.nd[tr.c2[t]];
+      const int m = N.m;
+      const T* Vh1 = (const T*)a.Vt + (a.m - a.kr);
+      const T* Vh2 = (const T*)b.Vt + (b.m - b.kr);
+      X.gemm(N.B12, std::max(a.kr, 1), 0, Vh2, b.m, 1, Dm[i] + (long long)a.kr * m, m, a.kr, b.kr, b.kc, 1.0, 0.0);
+      X.gemm(N.B21, std::max(b.kr, 1), 0, Vh1, a.m, 1, Dm[i] + a.kr, m, b.kr, a.kr, a.kc, 1.0, 0.0);
+    }
+    X.flush_gemm();
+    // Omega: rows piv[k:] minus E rows piv[:k] on top, rows piv[:k] below; root: LU
+    std::vector<LuJob> lu;
+    for (size_t i = 0; i < items.size(); ++i) {
+      FrontRt& F = *items[i].first;
+      const int t = items[i].second;
+      NodeRt& N = F.nd[t];
+      const int m = N.m, k = N.kr;
+      if (t == F.k) {
+        N.Dt = Dm[i];
+        N.lupiv = X.I(H.fac, m);
+        if (m > 0) lu.push_back(LuJob{N.Dt, N.lupiv, m, 0});
+        continue;
+      }
+      N.Dt = X.A(H.fac, (long long)m * m);
+      X.copy(Dm[i], m, 0, N.Dt, m, m - k, m, N.piv_r + k);
+      X.copy(Dm[i], m, 0, (T*)N.Dt + (m - k), m, k, m, N.piv_r);
+    }
+    X.flush_copy();
+    for (size_t i = 0; i < items.size(); ++i) {
+      FrontRt& F = *items[i].first;
+      const int t = items[i].second;
+      if (t == F.k) continue;
+      NodeRt& N = F.nd[t];
+      const int m = N.m, k = N.kr;
+      X.gemm(N.Xr, std::max(k, 1), 1, (const T*)N.Dt + (m - k), m, 0, N.Dt, m, m - k, m, k, -1.0, 1.0);
+    }
+    X.flush_gemm();
+    // V merged: leaf V_t; non-leaf diag(Vh1, Vh2) V_t
+    for (size_t i = 0; i < items.size(); ++i) {
+      FrontRt& F = *items[i].first;
+      const int t = items[i].second;
+      const ClusterTree& tr = S.fronts[F.f].tree;
+      if (t == F.k) continue;
+      NodeRt& N = F.nd[t];
+      N.Vt = X.A(H.fac, (long long)N.m * std::max(N.kc, 1));
+      if (tr.leaf(t)) {
+        X.copy(N.Vexp, N.mc, 0, N.Vt, N.m, N.m, N.kc);
+      } else {
+        const NodeRt &a = F.nd[tr.c1[t]], &b = F.nd[tr.c2[t]];
+        const T* Vh1 = (const T*)a.Vt + (a.m - a.kr);
+        const T* Vh2 = (const T*)b.Vt + (b.m - b.kr);
+        X.gemm(Vh1, a.m, 0, N.Vexp, std::max(N.mc, 1), 0, N.Vt, N.m, a.kr, N.kc, a.kc, 1.0, 0.0);
+        X.gemm(Vh2, b.m, 0, (const T*)N.Vexp + a.kc, std::max(N.mc, 1), 0, (T*)N.Vt + a.kr, N.m, b.kr,
+               N.kc, b.kc, 1.0, 0.0);
+      }
+    }
+    X.flush_copy();
+    X.flush_gemm();
+    std::vector<LqJob> lq;
+    for (size_t i = 0; i < items.size(); ++i) {
+      FrontRt& F = *items[i].first;
+      const int t = items[i].second;
+      if (t == F.k) continue;
+      NodeRt& N = F.nd[t];
+      N.tau = X.A(H.fac, std::max(N.m - N.kr, 1));
+      if (N.m - N.kr > 0) lq.push_back(LqJob{N.Dt, N.Vt, N.tau, N.m, N.kr, N.kc, 0});
+    }
+    X.launch(lq, [&](const LqJob* d, int n) { HssKern<T>::lq(d, n, X.s); });
+    X.launch(lu, [&](const LuJob* d, int n) { HssKern<T>::lu(d, n, c.d_status, X.s); });
+  }
+  if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during the ULV factorization");
+  // nested bases U^big, V^big of every non-root node, bottom-up
+  int th = 0;
+  for (FrontRt* F : fs) th = std::max(th, F->tree_h);
+  for (int lv = 0; lv < th; ++lv) {
+    for (FrontRt* F : fs) {
+      const ClusterTree& tr = S.fronts[F->f].tree;
+      for (int t = 0; t < tr.size(); ++t) {
+        if (t == tr.root() || F->height[t] != lv) continue;
+        NodeRt& N = F->nd[t];
+        if (tr.leaf(t)) {
+          N.Ubig = N.Uexp;
+          N.Vbig = N.Vexp;
+          continue;
+        }
+        const NodeRt &a = F->nd[tr.c1[t]], &b = F->nd[tr.c2[t]];
+        N.Ubig = X.A(H.fac, (long long)N.n * std::max(N.kr, 1));
+        N.Vbig = X.A(H.fac, (long long)N.n * std::max(N.kc, 1));
+        X.gemm(a.Ubig, a.n, 0, N.Uexp, std::max(N.m, 1), 0, N.Ubig, N.n, a.n, N.kr, a.kr, 1.0, 0.0);
+        X.gemm(b.Ubig, b.n, 0, (const T*)N.Uexp + a.kr, std::max(N.m, 1), 0, (T*)N.Ubig + a.n, N.n, b.n,
+               N.kr, b.kr, 1.0, 0.0);
+        X.gemm(a.Vbig, a.n, 0, N.Vexp, std::max(N.mc, 1), 0, N.Vbig, N.n, a.n, N.kc, a.kc, 1.0, 0.0);
+        X.gemm(b.Vbig, b.n, 0, (const T*)N.Vexp + a.kc, std::max(N.mc, 1), 0, (T*)N.Vbig + a.n, N.n, b.n,
+               N.kc, b.kc, 1.0, 0.0);
+      }
+    }
+    X.flush_gemm();
+  }
+  // Z = F11^-1 U^big_k for fronts with an update block
+  std::vector<FrontRt*> sf;
+  std::vector<const T*> bin;
+  std::vector<long long> ldin, ldout;
+  std::vector<T*> xout;
+  std::vector<int> nr;
+  for (FrontRt* F : fs) {
+    if (F->nu == 0 || F->nd[F->k].kr == 0) continue;
+    F->Z = X.A(H.fac, (long long)F->ns * F->nd[F->k].kr);
+    sf.push_back(F);
+    bin.push_back((const T*)F->nd[F->k].Ubig);
+    ldin.push_back(F->ns);
+    xout.push_back((T*)F->Z);
+    ldout.push_back(F->ns);
+    nr.push_back(F->nd[F->k].kr);
+  }
+  if (!sf.empty()) ulv_solve(X, sf, bin, ldin, xout, ldout, nr, H.lvl);
+  // W = V^big_k^* Z, Theta^* = U^big_q B_qk W, Phi^* = V^big_q B_kq^*
+  std::vector<T*> Wk(fs.size()), G2(fs.size()), Th(fs.size()), Ph(fs.size());
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    if (F.nu == 0) continue;
+    const NodeRt &K = F.nd[F.k], &Q = F.nd[F.q], &Rt = F.nd[F.root];
+    const int r = K.kr;
+    Wk[i] = X.A(H.lvl, (long long)std::max(K.kc, 1) * std::max(r, 1));
+    G2[i] = X.A(H.lvl, (long long)std::max(Q.kr, 1) * std::max(r, 1));
+    Th[i] = X.A(H.lvl, (long long)F.nu * std::max(r, 1));
+    Ph[i] = X.A(H.lvl, (long long)F.nu * std::max(r, 1));
+    if (r > 0) X.gemm(K.Vbig, F.ns, 1, F.Z, F.ns, 0, Wk[i], std::max(K.kc, 1), K.kc, r, F.ns, 1.0, 0.0);
+  }
+  X.flush_gemm();
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    if (F.nu == 0) continue;
+    const NodeRt &K = F.nd[F.k], &Q = F.nd[F.q], &Rt = F.nd[F.root];
+    const int r = K.kr;
+    X.gemm(Rt.B21, std::max(Q.kr, 1), 0, Wk[i], std::max(K.kc, 1), 0, G2[i], std::max(Q.kr, 1), Q.kr, r,
+           K.kc, 1.0, 0.0);
+    X.gemm(Q.Vbig, F.nu, 0, Rt.B12, std::max(K.kr, 1), 1, Ph[i], F.nu, F.nu, r, Q.kc, 1.0, 0.0);
+  }
+  X.flush_gemm();
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    if (F.nu == 0) continue;
+    const NodeRt &K = F.nd[F.k], &Q = F.nd[F.q];
+    X.gemm(Q.Ubig, F.nu, 0, G2[i], std::max(Q.kr, 1), 0, Th[i], F.nu, F.nu, K.kr, Q.kr, 1.0, 0.0);
+  }
+  X.flush_gemm();
+  // dense F22 (HSS expansion) into the update matrix, then -= Theta^* Phi
+  struct Blk {
+    FrontRt* F;
+    int t;
+    T* t1;
+    T* t2;
+  };
+  std::vector<Blk> blks;
+  for (FrontRt* F : fs) {
+    if (F->nu == 0) continue;
+    const ClusterTree& tr = S.fronts[F->f].tree;
+    T* Ui = X.arena() + c.fronts_host[F->f].u_off;
+    for (int t = 0; t < tr.size(); ++t) {
+      if (t == tr.root() || tr.lo[t] < F->ns) continue;  // F22 subtree only
+      NodeRt& N = F->nd[t];
+      const long long o = (tr.lo[t] - F->ns) * (1LL + F->nu);
+      if (tr.leaf(t)) {
+        X.copy(N.D, N.n, 0, Ui + o, F->nu, N.n, N.n);
+        continue;
+      }
+      const NodeRt &a = F->nd[tr.c1[t]], &b = F->nd[tr.c2[t]];
+      Blk bk{F, t, X.A(H.lvl, (long long)std::max(a.kr, 1) * b.n), X.A(H.lvl, (long long)std::max(b.kr, 1) * a.n)};
+      X.gemm(N.B12, std::max(a.kr, 1), 0, b.Vbig, b.n, 1, bk.t1, std::max(a.kr, 1), a.kr, b.n, b.kc, 1.0, 0.0);
+      X.gemm(N.B21, std::max(b.kr, 1), 0, a.Vbig, a.n, 1, bk.t2, std::max(b.kr, 1), b.kr, a.n, a.kc, 1.0, 0.0);
+      blks.push_back(bk);
+    }
+  }
+  X.flush_copy();
+  X.flush_gemm();
+  for (auto& bk : blks) {
+    FrontRt& F = *bk.F;
+    const ClusterTree& tr = S.fronts[F.f].tree;
+    T* Ui = X.arena() + c.fronts_host[F.f].u_off;
+    const int c1 = tr.c1[bk.t], c2 = tr.c2[bk.t];
+    const NodeRt &a = F.nd[c1], &b = F.nd[c2];
+    const long long r1 = tr.lo[c1] - F.ns, r2 = tr.lo[c2] - F.ns;
+    X.gemm(a.Ubig, a.n, 0, bk.t1, std::max(a.kr, 1), 0, Ui + r1 + r2 * F.nu, F.nu, a.n, b.n, a.kr, 1.0, 0.0);
+    X.gemm(b.Ubig, b.n, 0, bk.t2, std::max(b.kr, 1), 0, Ui + r2 + r1 * F.nu, F.nu, b.n, a.n, b.kr, 1.0, 0.0);
+  }
+  X.flush_gemm();
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    if (F.nu == 0) continue;
+    T* Ui = X.arena() + c.fronts_host[F.f].u_off;
+    X.gemm(Th[i], F.nu, 0, Ph[i], F.nu, 1, Ui, F.nu, F.nu, F.nu, F.nd[F.k].kr, -1.0, 1.0);
+  }
+  X.flush_gemm();
+  return X.oom ? c.fail(HSSMF_ERR_OOM, "device memory exhausted in the HSS Schur update") : HSSMF_OK;
+}
+
+std::vector<FrontRt*> level_fronts(HssState& H, const LevelPlan& L) {
+  std::vector<FrontRt*> fs;
+  for (int f : L.hss) fs.push_back(&H.fronts[H.index[f]]);
+  return fs;
+}
+
+}  // namespace
+
+void hss_begin_factor(hssmf_ctx& c) {
+  c.hss_max_rank = c.hss_max_d = c.hss_rounds = 0;
+  c.hss_flops = c.hss_bytes = 0.0;
+  if (!c.hss) return;
+  c.hss->fac.reset();
+  c.hss->sol.reset();
+  c.hss->sol_nrhs = -1;
+  c.hss->flops = 0.0;
+}
+
+template <typename T>
+hssmf_status hss_factor_level(hssmf_ctx& c, int level) {
+  if (!c.hss) return c.fail(HSSMF_ERR_ARG, "internal: no HSS state");
+  Ctx<T> X(c);
+  HssState& H = X.H;
+  H.lvl.reset();
+  std::vector<FrontRt*> fs = level_fronts(H, c.plan[level]);
+  hssmf_status st = compress_level(X, fs);
+  if (st) return st;
+  if ((st = factor_ulv_schur(X, fs))) return st;
+  if ((st = c.cuda_check(cudaStreamSynchronize(c.stream), "HSS level"))) return st;
+  H.ring.off = 0;
+  c.hss_flops = H.flops;
+  c.hss_bytes = (double)H.fac.used;
+  return HSSMF_OK;
+}
+
+template <typename T>
+hssmf_status hss_solve_fwd_level(hssmf_ctx& c, int level, T* W, int nrhs, int transpose) {
+  if (transpose) return c.fail(HSSMF_ERR_ARG, "solve_T with HSS fronts is not available yet");
+  Ctx<T> X(c);
+  HssState& H = X.H;
+  std::vector<FrontRt*> fs = level_fronts(H, c.plan[level]);
+  // scratch for this level is taken from the solve pool; the pool is reset
+  // at the first (bottom) HSS level of every solve
+  if (level == c.hss_first_level) H.sol.reset();
+  std::vector<const T*> bin;
+  std::vector<T*> xout;
+  std::vector<long long> ld;
+  std::vector<int> nr;
+  for (FrontRt* F : fs) {
+    const DFront& d = c.fronts_host[F->f];
+    bin.push_back(W + d.w_off);
+    xout.push_back(W + d.w_off);
+    ld.push_back(d.nf);
+    nr.push_back(nrhs);
+  }
+  ulv_solve(X, fs, bin, ld, xout, ld, nr, H.sol);
+  // b_u -= U^big_q B_qk (V^big_k)^* y
+  std::vector<T*> t1(fs.size()), t2(fs.size());
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    if (F.nu == 0) continue;
+    const DFront& d = c.fronts_host[F.f];
+    const NodeRt &K = F.nd[F.k], &Q = F.nd[F.q];
+    t1[i] = X.A(H.sol, (long long)std::max(K.kc, 1) * nrhs);
+    t2[i] = X.A(H.sol, (long long)std::max(Q.kr, 1) * nrhs);
+    X.gemm(K.Vbig, F.ns, 1, W + d.w_off, d.nf, 0, t1[i], std::max(K.kc, 1), K.kc, nrhs, F.ns, 1.0, 0.0);
+  }
+  X.flush_gemm();
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    if (F.nu == 0) continue;
+    const NodeRt &K = F.nd[F.k], &Q = F.nd[F.q], &Rt = F.nd[F.root];
+    X.gemm(Rt.B21, std::max(Q.kr, 1), 0, t1[i], std::max(K.kc, 1), 0, t2[i], std::max(Q.kr, 1), Q.kr, nrhs,
+           K.kc, 1.0, 0.0);
+  }
+  X.flush_gemm();
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    if (F.nu == 0) continue;
+    const DFront& d = c.fronts_host[F.f];
+    const NodeRt& Q = F.nd[F.q];
+    X.gemm(Q.Ubig, F.nu, 0, t2[i], std::max(Q.kr, 1), 0, W + d.w_off + F.ns, d.nf, F.nu, nrhs, Q.kr, -1.0, 1.0);
+  }
+  X.flush_gemm();
+  return X.oom ? c.fail(HSSMF_ERR_OOM, "device memory exhausted in the HSS solve") : HSSMF_OK;
+}
+
+template <typename T>
+hssmf_status hss_solve_bwd_level(hssmf_ctx& c, int level, T* W, T* xp, int nrhs, int transpose) {
+  if (transpose) return c.fail(HSSMF_ERR_ARG, "solve_T with HSS fronts is not available yet");
+  Ctx<T> X(c);
+  HssState& H = X.H;
+  std::vector<FrontRt*> fs = level_fronts(H, c.plan[level]);
+  // x_s = y - Z B_kq (V^big_q)^* x_u
+  std::vector<T*> t3(fs.size()), t4(fs.size());
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    if (F.nu == 0 || !F.Z) continue;
+    const DFront& d = c.fronts_host[F.f];
+    const NodeRt &K = F.nd[F.k], &Q = F.nd[F.q];
+    t3[i] = X.A(H.sol, (long long)std::max(Q.kc, 1) * nrhs);
+    t4[i] = X.A(H.sol, (long long)std::max(K.kr, 1) * nrhs);
+    X.gemm(Q.Vbig, F.nu, 1, W + d.w_off + F.ns, d.nf, 0, t3[i], std::max(Q.kc, 1), Q.kc, nrhs, F.nu, 1.0, 0.0);
+  }
+  X.flush_gemm();
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    if (F.nu == 0 || !F.Z) continue;
+    const NodeRt &K = F.nd[F.k], &Q = F.nd[F.q], &Rt = F.nd[F.root];
+    X.gemm(Rt.B12, std::max(K.kr, 1), 0, t3[i], std::max(Q.kc, 1), 0, t4[i], std::max(K.kr, 1), K.kr, nrhs,
+           Q.kc, 1.0, 0.0);
+  }
+  X.flush_gemm();
+  for (size_t i = 0; i < fs.size(); ++i) {
+    FrontRt& F = *fs[i];
+    if (F.nu == 0 || !F.Z) continue;
+    const DFront& d = c.fronts_host[F.f];
+    const NodeRt& K = F.nd[F.k];
+    X.gemm(F.Z, F.ns, 0, t4[i], std::max(K.kr, 1), 0, W + d.w_off, d.nf, F.ns, nrhs, K.kr, -1.0, 1.0);
+  }
+  X.flush_gemm();
+  for (FrontRt* F : fs) {
+    const DFront& d = c.fronts_host[F->f];
+    X.copy(W + d.w_off, d.nf, 0, xp + d.sep_begin, c.sym.n, F->ns, nrhs);
+  }
+  X.flush_copy();
+  return X.oom ? c.fail(HSSMF_ERR_OOM, "device memory exhausted in the HSS solve") : HSSMF_OK;
+}
 
 template hssmf_status hss_factor_level<double>(hssmf_ctx&, int);
 template hssmf_status hss_factor_level<float>(hssmf_ctx&, int);

@@ -10,6 +10,7 @@ namespace hssmf {
 hssmf_status hss_prepare(hssmf_ctx& c);       // host-side plan after analyze
 hssmf_status hss_device_init(hssmf_ctx& c);   // device buffers at the first factor
 void hss_release(hssmf_ctx& c);
+void hss_begin_factor(hssmf_ctx& c);           // start of every numerical factorization
 template <typename T>
 hssmf_status hss_factor_level(hssmf_ctx& c, int level);
 template <typename T>

@@ -1,0 +1,139 @@
+// Job descriptors and launchers of the HSS-front kernels.
+#pragma once
+#include "kernels.h"
+
+namespace hssmf {
+
+struct CopyJob {  // dst(i, j) = src'(rmap[i], cmap[j]); source columns >= split come from src2
+  const void* src;
+  const void* src2;  // second source (columns split.. of the concatenation), lds2
+  long long lds2;
+  int split, pad2;
+  void* dst;
+  const int* rmap;  // nullptr: identity
+  const int* cmap;  // nullptr: identity
+  long long lds, ldd;
+  int rows, cols;
+  int src_trans;  // src'(a, b) = src[b + a * lds] instead of src[a + b * lds]
+  int scale_neg;  // 1: dst = -src'
+};
+
+struct IntGatherJob {  // out[i] = cat(a, b)[idx[i]], cat(a, b)[p] = p < split ? a[p] : b[p - split]
+  const int* a;
+  const int* b;
+  const int* idx;
+  int* out;
+  int n, split;
+};
+
+struct PhiloxJob {  // out(i, c) = G(seed, gidx[i], c), c in [c0, c1)
+  const int* gidx;
+  void* out;
+  long long ld;
+  int rows, c0, c1, pad;
+};
+
+struct SampleAJob {  // Sr(:, c) = A_i R(:, c), Sc(:, c) = A_i^T R(:, c), c in [c0, c1)
+  void* Sr;
+  void* Sc;
+  const void* R;
+  long long ld;
+  int front, c0, c1, pad;
+};
+
+struct ExtractJob {  // out(i, j) = F_front(rows[i], cols[j]) from A_i and the children's updates
+  const int* rows;
+  const int* cols;
+  void* out;
+  long long ld;
+  int front, nr, nc, pad;
+};
+
+struct IdJob {  // ID of the columns of Y (d x m): rank, piv, X = R1^-1 R2 (k x (m-k), ld k)
+  const void* Y;
+  void* W;  // d x m work copy
+  int* piv;
+  void* X;
+  int* rank;
+  int d, m;
+};
+
+struct BasisJob {  // out (m x k, ld ldo) = Pi [I; X^T]
+  const int* piv;
+  const void* X;
+  void* out;
+  long long ldo;
+  int m, k;
+};
+
+struct LqJob {  // LQ of the top m-k rows of Dt (m x m): Dt <- Dt Q, V <- Q^T V; taus
+  void* Dt;
+  void* V;
+  void* tau;
+  int m, k, kc, pad;
+};
+
+struct LuJob {  // in-place partial-pivoting LU of A (m x m, ld m)
+  void* A;
+  int* piv;
+  int m, pad;
+};
+
+// Forward ULV step of one HSS node (one CTA per job, all nrhs columns):
+//   b_t   = leaf: bsrc rows; non-leaf: [bh1 - B12 wc2; bh2 - B21 wc1]
+//   bo    = Omega b_t (rows piv[k:] minus E rows piv[:k]; then rows piv[:k])
+//   x1    = L^-1 bo[0:m-k], bhat = bo[m-k:] - D21 x1 (one column sweep of Dt)
+//   w     = V_t^T [wc1; wc2] + Vt_top^T x1
+// At the root of the F11 tree: x1 = LU^-1 b_t (m rows).
+struct UlvFwdJob {
+  const void* Dt;     // m x m, ld m: [L 0; D21 Dhat] (root: LU factors)
+  const int* piv;     // Pi (m); root: LU row interchanges
+  const void* X;      // k x (m - k), ld k: E = X^T
+  const void* Vt;     // Q^T V_merged (m x kc, ld m)
+  const void* Vloc;   // V_t explicit (mc x kc, ld mc), non-leaf only
+  const void* B12;    // k1 x kc2, ld k1
+  const void* B21;    // k2 x kc1, ld k2
+  const void* bsrc;   // leaf: m x nrhs, ld ldbsrc
+  const void* bh1;    // non-leaf: children's bhat (k1 x nrhs, ld k1) and (k2 x nrhs, ld k2)
+  const void* bh2;
+  const void* wc1;    // children's w (kc1 x nrhs, ld kc1) and (kc2 x nrhs, ld kc2)
+  const void* wc2;
+  void* bt;           // scratch m x nrhs, ld m
+  void* bo;           // out m x nrhs, ld m: [x1; bhat] (root: the solution)
+  void* w;            // out kc x nrhs, ld kc
+  long long ldbsrc;
+  int m, k, kc, mc, k1, k2, kc1, kc2, leaf, is_root, ldbh1, ldbh2, nrhs, pad;
+};
+
+// Backward ULV step: x_t = Q [x1; xhat2] with Q the product of the LQ
+// reflectors stored in the rows of Dt; x1 = bo[0:m-k] of the forward job.
+struct UlvBwdJob {
+  const void* Dt;
+  const void* tau;
+  const void* x1;   // (m - k) x nrhs, ld m
+  const void* xh2;  // k x nrhs, ld ldxh2 (slice of the parent's x)
+  void* out;        // m x nrhs, ld ldout
+  long long ldxh2, ldout;
+  int m, k, nrhs, pad;
+};
+
+template <typename T>
+struct HssKern {
+  static void copy(const CopyJob* jobs, int njobs, cudaStream_t s);
+  static void int_gather(const IntGatherJob* jobs, int njobs, cudaStream_t s);
+  static void philox(const PhiloxJob* jobs, int njobs, int max_rows, unsigned long long seed,
+                     cudaStream_t s);
+  static void sample_a(const DevSym& ds, const double* values, const SampleAJob* jobs, int njobs,
+                       int max_rows, cudaStream_t s);
+  static void extract(const DevSym& ds, const double* values, const T* arena, const ExtractJob* jobs,
+                      int njobs, cudaStream_t s);
+  // returns -1 if max_m exceeds the shared-memory bound of the kernel
+  static int batched_id(const IdJob* jobs, int njobs, int max_m, double eps, cudaStream_t s);
+  static void basis(const BasisJob* jobs, int njobs, cudaStream_t s);
+  static void lq(const LqJob* jobs, int njobs, cudaStream_t s);
+  static void lu(const LuJob* jobs, int njobs, unsigned* status, cudaStream_t s);
+  static void ulv_fwd(const UlvFwdJob* jobs, int njobs, cudaStream_t s);
+  static void ulv_bwd(const UlvBwdJob* jobs, int njobs, cudaStream_t s);
+};
+
+}  // namespace hssmf

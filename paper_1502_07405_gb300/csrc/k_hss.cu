@@ -1,0 +1,672 @@
+// Kernels of the HSS frontal matrices (Sections 2.2, 2.3, 4.3-4.5).
+#include <algorithm>
+#include <cmath>
+
+#include "hss_kernels.h"
+
+namespace hssmf {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v);
+template <>
+__device__ __forceinline__ double wsum<double>(double v) { return warp_sum(v); }
+template <>
+__device__ __forceinline__ float wsum<float>(float v) { return warp_sumf(v); }
+
+// block-wide sum of a double, result in every thread (blockDim multiple of 32)
+__device__ double block_sum_d(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += sh[w];
+  __syncthreads();
+  return s;
+}
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, Weyl key schedule.
+__device__ __forceinline__ void philox4x32_10(unsigned c[4], unsigned k0, unsigned k1) {
+  const unsigned M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    unsigned hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    unsigned hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    unsigned n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// G(seed, g, c) = sqrt(-2 ln u1) cos(2 pi u2), u = (x + 0.5) 2^-32, FP64.
+__device__ __forceinline__ double gauss(unsigned long long seed, unsigned g, unsigned c) {
+  unsigned ctr[4] = {g, c, 0u, 0u};
+  philox4x32_10(ctr, (unsigned)(seed & 0xFFFFFFFFull), (unsigned)(seed >> 32));
+  const double s = 2.3283064365386963e-10;  // 2^-32
+  double u1 = ((double)ctr[0] + 0.5) * s;
+  double u2 = ((double)ctr[1] + 0.5) * s;
+  return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Gather/transposing copies.  Grid (job, 32 chunks).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_copy(const CopyJob* __restrict__ jobs) {
+  const CopyJob jb = jobs[blockIdx.x];
+  const T* src = (const T*)jb.src;
+  T* dst = (T*)jb.dst;
+  const long long tot = (long long)jb.rows * jb.cols;
+  for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.y * blockDim.x) {
+    int i = (int)(e % jb.rows), j = (int)(e / jb.rows);
+    int si = jb.rmap ? jb.rmap[i] : i;
+    int sj = jb.cmap ? jb.cmap[j] : j;
+    const T* sp = src;
+    long long lds = jb.lds;
+    if (jb.src2 && sj >= jb.split) {
+      sp = (const T*)jb.src2;
+      lds = jb.lds2;
+      sj -= jb.split;
+    }
+    T v = jb.src_trans ? sp[sj + (long long)si * lds] : sp[si + (long long)sj * lds];
+    dst[i + (long long)j * jb.ldd] = jb.scale_neg ? -v : v;
+  }
+}
+
+template <typename T>
+void HssKern<T>::copy(const CopyJob* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_copy<T><<<dim3(njobs, 32), 256, 0, s>>>(jobs);
+  count_launch();
+}
+
+__global__ void k_int_gather(const IntGatherJob* __restrict__ jobs) {
+  const IntGatherJob jb = jobs[blockIdx.x];
+  for (int i = threadIdx.x; i < jb.n; i += blockDim.x) {
+    int p = jb.idx[i];
+    jb.out[i] = p < jb.split ? jb.a[p] : jb.b[p - jb.split];
+  }
+}
+
+template <typename T>
+void HssKern<T>::int_gather(const IntGatherJob* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_int_gather<<<njobs, 128, 0, s>>>(jobs);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Columns of the random matrix R for a list of global rows (Section 2.2.2,
+// Section 4.3: every entry depends only on its global row and column).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_philox(const PhiloxJob* __restrict__ jobs, unsigned long long seed) {
+  const PhiloxJob jb = jobs[blockIdx.x];
+  const int i = blockIdx.y * blockDim.x + threadIdx.x;
+  if (i >= jb.rows) return;
+  const unsigned g = (unsigned)jb.gidx[i];
+  T* out = (T*)jb.out;
+  for (int c = jb.c0; c < jb.c1; ++c) out[i + (long long)c * jb.ld] = T(gauss(seed, g, (unsigned)c));
+}
+
+template <typename T>
+void HssKern<T>::philox(const PhiloxJob* jobs, int njobs, int max_rows, unsigned long long seed,
+                        cudaStream_t s) {
+  if (njobs <= 0 || max_rows <= 0) return;
+  k_philox<T><<<dim3(njobs, (max_rows + 127) / 128), 128, 0, s>>>(jobs, seed);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Original-entry part of the samples (eq. FtimesR): S^r = A_i R, S^c = A_i^T R
+// over the local sparse rows of front i; A_i^T uses the transposed entries.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_sample_a(const DFront* __restrict__ fr, const int* __restrict__ ints,
+                           const int* __restrict__ tpos, const double* __restrict__ values,
+                           const SampleAJob* __restrict__ jobs) {
+  const SampleAJob jb = jobs[blockIdx.x];
+  const DFront f = fr[jb.front];
+  const int r = blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= f.nf) return;
+  const int* arow = ints + f.arow_off;
+  const int nnz_f = arow[f.nf];
+  const int* acol = arow + f.nf + 1;
+  const int* aval = acol + nnz_f;
+  const T* R = (const T*)jb.R;
+  T* Sr = (T*)jb.Sr;
+  T* Sc = (T*)jb.Sc;
+  const int p0 = arow[r], p1 = arow[r + 1];
+  for (int c = jb.c0; c < jb.c1; ++c) {
+    T sr = T(0), sc = T(0);
+    for (int p = p0; p < p1; ++p) {
+      T rv = R[acol[p] + (long long)c * jb.ld];
+      sr += T(values[aval[p]]) * rv;
+      sc += T(values[tpos[aval[p]]]) * rv;
+    }
+    Sr[r + (long long)c * jb.ld] = sr;
+    Sc[r + (long long)c * jb.ld] = sc;
+  }
+}
+
+template <typename T>
+void HssKern<T>::sample_a(const DevSym& ds, const double* values, const SampleAJob* jobs, int njobs,
+                          int max_rows, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_sample_a<T><<<dim3(njobs, (max_rows + 127) / 128), 128, 0, s>>>(ds.fronts, ds.ints, ds.tpos,
+                                                                    values, jobs);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Element extraction from a front (Sections 4.3 and 4.5): entries of A_i plus
+// the children's update matrices at their positions.  Grid (job, 16 chunks).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_extract(const DFront* __restrict__ fr, const int* __restrict__ ints,
+                          const double* __restrict__ values, const T* __restrict__ ar,
+                          const ExtractJob* __restrict__ jobs) {
+  const ExtractJob jb = jobs[blockIdx.x];
+  const DFront f = fr[jb.front];
+  const int* arow = ints + f.arow_off;
+  const int nnz_f = arow[f.nf];
+  const int* acol = arow + f.nf + 1;
+  const int* aval = acol + nnz_f;
+  T* out = (T*)jb.out;
+  const long long tot = (long long)jb.nr * jb.nc;
+  for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.y * blockDim.x) {
+    int i = (int)(e % jb.nr), j = (int)(e / jb.nr);
+    int r = jb.rows[i], c = jb.cols[j];
+    T v = T(0);
+    for (int p = arow[r]; p < arow[r + 1]; ++p)
+      if (acol[p] == c) {
+        v = T(values[aval[p]]);
+        break;
+      }
+    for (int k = 0; k < f.nchild; ++k) {
+      const int* inv = ints + f.inv_off + (long long)k * f.nf;
+      int ir = inv[r], ic = inv[c];
+      if (ir >= 0 && ic >= 0) {
+        const DFront ch = fr[k == 0 ? f.child0 : f.child1];
+        v += ar[ch.u_off + ir + (long long)ic * ch.u_ld];
+      }
+    }
+    out[i + (long long)j * jb.ld] = v;
+  }
+}
+
+template <typename T>
+void HssKern<T>::extract(const DevSym& ds, const double* values, const T* arena,
+                         const ExtractJob* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_extract<T><<<dim3(njobs, 16), 256, 0, s>>>(ds.fronts, ds.ints, values, arena, jobs);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Interpolative decomposition by column-pivoted Householder QR (Section 2.2;
+// rank rule of Section 5.3).  One CTA per job.  Y (d x m) is copied to W;
+// column norms (FP64) are recomputed from the trailing rows after every
+// step; the pivot is the first column of largest norm; the rank is the first
+// i with |R_{i+1,i+1}| <= eps |R_11|.  Then X = R1^-1 R2 by back
+// substitution, one warp per column.
+// ---------------------------------------------------------------------------
+constexpr int ID_THREADS = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(ID_THREADS) k_cpqr_id(const IdJob* __restrict__ jobs, double eps) {
+  const IdJob jb = jobs[blockIdx.x];
+  const int d = jb.d, m = jb.m;
+  const long long ld = d;
+  const T* Y = (const T*)jb.Y;
+  T* W = (T*)jb.W;
+  extern __shared__ double smem[];
+  double* cn = smem;              // m column norms^2
+  int* perm = (int*)(smem + m);   // m
+  __shared__ double s_bv[ID_THREADS / 32];
+  __shared__ int s_bi[ID_THREADS / 32];
+  __shared__ double s_best;
+  __shared__ int s_bidx;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < m; j += nw) {
+    double s = 0.0;
+    for (int r = lane; r < d; r += 32) {
+      T v = Y[r + j * ld];
+      W[r + j * ld] = v;
+      s += (double)v * (double)v;
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      cn[j] = s;
+      perm[j] = j;
+    }
+  }
+  __syncthreads();
+  const int kmax = min(d, m);
+  int k = kmax;
+  double r11 = 0.0;
+  for (int i = 0; i < kmax; ++i) {
+    double bv = -1.0;
+    int bi = m;
+    for (int j = i + threadIdx.x; j < m; j += blockDim.x) {
+      double v = cn[j];
+      if (v > bv) { bv = v; bi = j; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = s_bv[0];
+      int ix = s_bi[0];
+      for (int w = 1; w < nw; ++w)
+        if (s_bv[w] > b || (s_bv[w] == b && s_bi[w] < ix)) { b = s_bv[w]; ix = s_bi[w]; }
+      s_best = b;
+      s_bidx = ix;
+    }
+    __syncthreads();
+    const double nrm = sqrt(fmax(s_best, 0.0));
+    const int p = s_bidx;
+    if (i == 0) {
+      r11 = nrm;
+      if (!(r11 > 0.0)) { k = 0; break; }
+    } else if (!(nrm > eps * r11)) {
+      k = i;
+      break;
+    }
+    if (p != i) {
+      for (int r = threadIdx.x; r < d; r += blockDim.x) {
+        T t = W[r + i * ld];
+        W[r + i * ld] = W[r + p * ld];
+        W[r + p * ld] = t;
+      }
+      if (threadIdx.x == 0) {
+        double t = cn[i]; cn[i] = cn[p]; cn[p] = t;
+        int q = perm[i]; perm[i] = perm[p]; perm[p] = q;
+      }
+    }
+    __syncthreads();
+    const T alpha = W[i + i * ld];
+    const T beta = alpha >= T(0) ? T(-nrm) : T(nrm);
+    const T tau = (beta - alpha) / beta;
+    const T scl = T(1) / (alpha - beta);
+    for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) W[r + i * ld] *= scl;
+    __syncthreads();
+    for (int j = i + 1 + wid; j < m; j += nw) {
+      T* wj = W + j * ld;
+      T s = T(0);
+      for (int r = i + 1 + lane; r < d; r += 32) s += W[r + i * ld] * wj[r];
+      s = wsum<T>(s) + wj[i];
+      const T fct = tau * s;
+      double nn = 0.0;
+      for (int r = i + 1 + lane; r < d; r += 32) {
+        T v = wj[r] - fct * W[r + i * ld];
+        wj[r] = v;
+        nn += (double)v * (double)v;
+      }
+      nn = warp_sum(nn);
+      __syncwarp();
+      if (lane == 0) {
+        wj[i] -= fct;
+        cn[j] = nn;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) W[i + i * ld] = beta;
+    __syncthreads();
+  }
+  // X = R1^-1 R2 (k x (m - k), ld k)
+  T* X = (T*)jb.X;
+  for (int j = k + wid; j < m; j += nw) {
+    T* x = X + (long long)(j - k) * k;
+    for (int r = k - 1; r >= 0; --r) {
+      T s = T(0);
+      for (int c = r + 1 + lane; c < k; c += 32) s += W[r + c * ld] * x[c];
+      s = wsum<T>(s);
+      if (lane == 0) x[r] = (W[r + j * ld] - s) / W[r + r * ld];
+      __syncwarp();
+    }
+  }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) jb.piv[j] = perm[j];
+  if (threadIdx.x == 0) *jb.rank = k;
+}
+
+template <typename T>
+int HssKern<T>::batched_id(const IdJob* jobs, int njobs, int max_m, double eps, cudaStream_t s) {
+  if (njobs <= 0) return 0;
+  const size_t smem = 12 * (size_t)std::max(max_m, 1);  // m norms (double) + m pivots (int)
+  if (smem > 200 * 1024) return -1;                       // m above 17066 is not supported
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cpqr_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_cpqr_id<T><<<njobs, ID_THREADS, smem, s>>>(jobs, eps);
+  count_launch();
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Explicit interpolative basis Pi [I; X^T] (eq. UVstructure).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_basis(const BasisJob* __restrict__ jobs) {
+  const BasisJob jb = jobs[blockIdx.x];
+  const T* X = (const T*)jb.X;
+  T* out = (T*)jb.out;
+  const long long tot = (long long)jb.m * jb.k;
+  for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.y * blockDim.x) {
+    int j = (int)(e % jb.m), c = (int)(e / jb.m);  // j: position in pivoted order
+    T v = j < jb.k ? T(j == c ? 1 : 0) : X[c + (long long)(j - jb.k) * jb.k];
+    out[jb.piv[j] + (long long)c * jb.ldo] = v;
+  }
+}
+
+template <typename T>
+void HssKern<T>::basis(const BasisJob* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_basis<T><<<dim3(njobs, 8), 256, 0, s>>>(jobs);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// LQ of the top m - k rows of Dt (Section 2.3 ULV step): Householder
+// reflectors H_i from the rows (LAPACK larfg convention, v stored in the
+// zeroed part of row i), applied from the right to the rows below and from
+// the left to V.  One CTA per job.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_lq(const LqJob* __restrict__ jobs) {
+  const LqJob jb = jobs[blockIdx.x];
+  const int m = jb.m, nk = jb.m - jb.k, kc = jb.kc;
+  T* D = (T*)jb.Dt;
+  T* V = (T*)jb.V;
+  T* tau = (T*)jb.tau;
+  __shared__ double sh[33];
+  for (int i = 0; i < nk; ++i) {
+    double part = 0.0;
+    for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) {
+      double v = (double)D[i + (long long)c * m];
+      part += v * v;
+    }
+    const double xn2 = block_sum_d(part, sh);
+    const T alpha = D[i + (long long)i * m];
+    T t = T(0), beta = alpha, scl = T(0);
+    if (xn2 > 0.0) {
+      double b = sqrt((double)alpha * (double)alpha + xn2);
+      beta = alpha >= T(0) ? T(-b) : T(b);
+      t = (beta - alpha) / beta;
+      scl = T(1) / (alpha - beta);
+    }
+    __syncthreads();
+    for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) D[i + (long long)c * m] *= scl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      D[i + (long long)i * m] = beta;
+      tau[i] = t;
+    }
+    if (t != T(0)) {
+      // rows r > i:  row_r[i:m] -= t (row_r[i:m] . v) v^T, v = [1, D[i, i+1:m]]
+      for (int r = i + 1 + threadIdx.x; r < m; r += blockDim.x) {
+        T s = D[r + (long long)i * m];
+        for (int c = i + 1; c < m; ++c) s += D[r + (long long)c * m] * D[i + (long long)c * m];
+        const T f = t * s;
+        D[r + (long long)i * m] -= f;
+        for (int c = i + 1; c < m; ++c) D[r + (long long)c * m] -= f * D[i + (long long)c * m];
+      }
+      // V rows i..m-1:  V -= t v (v^T V)
+      for (int c = threadIdx.x; c < kc; c += blockDim.x) {
+        T s = V[i + (long long)c * m];
+        for (int r = i + 1; r < m; ++r) s += D[i + (long long)r * m] * V[r + (long long)c * m];
+        const T f = t * s;
+        V[i + (long long)c * m] -= f;
+        for (int r = i + 1; r < m; ++r) V[r + (long long)c * m] -= f * D[i + (long long)r * m];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void HssKern<T>::lq(const LqJob* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_lq<T><<<njobs, 256, 0, s>>>(jobs);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Small dense LU with partial pivoting (root of the F11 tree).  One CTA.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_lu_small(const LuJob* __restrict__ jobs, unsigned* status) {
+  const LuJob jb = jobs[blockIdx.x];
+  const int m = jb.m;
+  T* A = (T*)jb.A;
+  __shared__ double s_v[8];
+  __shared__ int s_i[8];
+  __shared__ int s_p;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < m; ++j) {
+    double bv = -1.0;
+    int bi = m;
+    for (int r = j + threadIdx.x; r < m; r += blockDim.x) {
+      double a = fabs((double)A[r + (long long)j * m]);
+      if (a > bv) { bv = a; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_v[wid] = bv; s_i[wid] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = s_v[0];
+      int ix = s_i[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (s_v[w] > b || (s_v[w] == b && s_i[w] < ix)) { b = s_v[w]; ix = s_i[w]; }
+      if (!(b > 0.0) || !isfinite(b)) {
+        atomicOr(status, b == 0.0 ? ST_ZERO_PIVOT : ST_NONFINITE);
+        ix = j;
+      }
+      s_p = ix;
+      jb.piv[j] = ix;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j)
+      for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        T t = A[j + (long long)c * m];
+        A[j + (long long)c * m] = A[p + (long long)c * m];
+        A[p + (long long)c * m] = t;
+      }
+    __syncthreads();
+    const T dj = A[j + (long long)j * m];
+    const T inv = dj != T(0) ? T(1) / dj : T(0);
+    for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) {
+      T l = A[r + (long long)j * m] * inv;
+      A[r + (long long)j * m] = l;
+      for (int c = j + 1; c < m; ++c) A[r + (long long)c * m] -= l * A[j + (long long)c * m];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void HssKern<T>::lu(const LuJob* jobs, int njobs, unsigned* status, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_lu_small<T><<<njobs, 256, 0, s>>>(jobs, status);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// ULV forward step of one node (see UlvFwdJob).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_ulv_fwd(const UlvFwdJob* __restrict__ jobs) {
+  const UlvFwdJob jb = jobs[blockIdx.x];
+  const int nrhs = jb.nrhs;
+  const int m = jb.m, k = jb.k, nk = jb.m - jb.k;
+  const T* Dt = (const T*)jb.Dt;
+  const T* X = (const T*)jb.X;
+  const T* Vt = (const T*)jb.Vt;
+  const T* Vloc = (const T*)jb.Vloc;
+  const T* B12 = (const T*)jb.B12;
+  const T* B21 = (const T*)jb.B21;
+  const T* bsrc = (const T*)jb.bsrc;
+  const T* bh1 = (const T*)jb.bh1;
+  const T* bh2 = (const T*)jb.bh2;
+  const T* wc1 = (const T*)jb.wc1;
+  const T* wc2 = (const T*)jb.wc2;
+  for (int j = 0; j < nrhs; ++j) {
+    T* bt = (T*)jb.bt + (long long)j * m;
+    T* bo = (T*)jb.bo + (long long)j * m;
+    if (jb.leaf) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) bt[i] = bsrc[i + j * jb.ldbsrc];
+    } else {
+      for (int i = threadIdx.x; i < jb.k1; i += blockDim.x) {
+        T s = bh1[i + (long long)j * jb.ldbh1];
+        for (int c = 0; c < jb.kc2; ++c) s -= B12[i + (long long)c * jb.k1] * wc2[c + (long long)j * jb.kc2];
+        bt[i] = s;
+      }
+      for (int i = threadIdx.x; i < jb.k2; i += blockDim.x) {
+        T s = bh2[i + (long long)j * jb.ldbh2];
+        for (int c = 0; c < jb.kc1; ++c) s -= B21[i + (long long)c * jb.k2] * wc1[c + (long long)j * jb.kc1];
+        bt[jb.k1 + i] = s;
+      }
+    }
+    __syncthreads();
+    if (jb.is_root) {  // LU solve with interchanges
+      if (threadIdx.x == 0)
+        for (int i = 0; i < m; ++i) {
+          int p = jb.piv[i];
+          if (p != i) { T t = bt[i]; bt[i] = bt[p]; bt[p] = t; }
+        }
+      __syncthreads();
+      for (int c = 0; c < m; ++c) {
+        const T xc = bt[c];
+        for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) bt[r] -= Dt[r + (long long)c * m] * xc;
+        __syncthreads();
+      }
+      for (int c = m - 1; c >= 0; --c) {
+        const T xc = bt[c] / Dt[c + (long long)c * m];
+        __syncthreads();
+        if (threadIdx.x == 0) bt[c] = xc;
+        for (int r = threadIdx.x; r < c; r += blockDim.x) bt[r] -= Dt[r + (long long)c * m] * xc;
+        __syncthreads();
+      }
+      for (int i = threadIdx.x; i < m; i += blockDim.x) bo[i] = bt[i];
+      __syncthreads();
+      continue;
+    }
+    // bo = Omega bt
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+      T s = bt[jb.piv[k + i]];
+      for (int c = 0; c < k; ++c) s -= X[c + (long long)i * k] * bt[jb.piv[c]];
+      bo[i] = s;
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) bo[nk + i] = bt[jb.piv[i]];
+    __syncthreads();
+    // x1 = L^-1 bo[0:nk]; bhat = bo[nk:] - D21 x1  (one column sweep)
+    for (int c = 0; c < nk; ++c) {
+      const T xc = bo[c] / Dt[c + (long long)c * m];
+      __syncthreads();
+      if (threadIdx.x == 0) bo[c] = xc;
+      for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) bo[r] -= Dt[r + (long long)c * m] * xc;
+      __syncthreads();
+    }
+    // w = V_t^T [wc1; wc2] + Vt_top^T x1
+    T* w = (T*)jb.w + (long long)j * jb.kc;
+    for (int c = threadIdx.x; c < jb.kc; c += blockDim.x) {
+      T s = T(0);
+      if (!jb.leaf) {
+        for (int r = 0; r < jb.kc1; ++r) s += Vloc[r + (long long)c * jb.mc] * wc1[r + (long long)j * jb.kc1];
+        for (int r = 0; r < jb.kc2; ++r)
+          s += Vloc[jb.kc1 + r + (long long)c * jb.mc] * wc2[r + (long long)j * jb.kc2];
+      }
+      for (int r = 0; r < nk; ++r) s += Vt[r + (long long)c * m] * bo[r];
+      w[c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void HssKern<T>::ulv_fwd(const UlvFwdJob* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_ulv_fwd<T><<<njobs, 256, 0, s>>>(jobs);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// ULV backward step of one node: out = Q [x1; xhat2].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_ulv_bwd(const UlvBwdJob* __restrict__ jobs) {
+  const UlvBwdJob jb = jobs[blockIdx.x];
+  const int nrhs = jb.nrhs;
+  const int m = jb.m, nk = jb.m - jb.k;
+  const T* Dt = (const T*)jb.Dt;
+  const T* tau = (const T*)jb.tau;
+  const T* x1 = (const T*)jb.x1;
+  const T* xh2 = (const T*)jb.xh2;
+  __shared__ double sh[33];
+  for (int j = 0; j < nrhs; ++j) {
+    T* x = (T*)jb.out + (long long)j * jb.ldout;
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) x[i] = x1[i + (long long)j * m];
+    for (int i = threadIdx.x; i < jb.k; i += blockDim.x) x[nk + i] = xh2[i + (long long)j * jb.ldxh2];
+    __syncthreads();
+    for (int i = nk - 1; i >= 0; --i) {
+      const T t = tau[i];
+      if (t == T(0)) continue;  // uniform across the block
+      const double xi = (double)x[i];  // read before the reduction's barriers
+      double part = 0.0;
+      for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x)
+        part += (double)Dt[i + (long long)c * m] * (double)x[c];
+      const double s = block_sum_d(part, sh) + xi;
+      const T f = t * T(s);
+      if (threadIdx.x == 0) x[i] -= f;
+      for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) x[c] -= f * Dt[i + (long long)c * m];
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+void HssKern<T>::ulv_bwd(const UlvBwdJob* jobs, int njobs, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_ulv_bwd<T><<<njobs, 256, 0, s>>>(jobs);
+  count_launch();
+}
+
+template struct HssKern<double>;
+template struct HssKern<float>;
+
+}  // namespace hssmf

@@ -298,6 +298,7 @@ hssmf_status hssmf_ctx::factor_impl() {
   T* ar = static_cast<T*>(d_arena);
   hssmf_status st;
   dense_flops = 0.0;
+  hss_begin_factor(*this);
   for (size_t h = 0; h < plan.size(); ++h) {
     const LevelPlan& L = plan[h];
     // dense fronts: assembly, then the blocked partial LU

@@ -76,7 +76,7 @@ struct hssmf_ctx {
   hssmf_stats stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double dense_flops = 0.0, hss_flops = 0.0, factor_bytes_dense = 0.0, hss_bytes = 0.0;
-  int hss_max_rank = 0, hss_max_d = 0, hss_rounds = 0;
+  int hss_max_rank = 0, hss_max_d = 0, hss_rounds = 0, hss_first_level = -1;
   int factor_launches = 0;
   int last_iters = 0;
   double last_relres = 0.0;
