@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the HSS-structured multifrontal solver on one GB300 (or N
+independent replicas on N GPUs).
+
+Metric: factor + solve time to a true relative residual of 1e-10 on the 3D
+7-point Poisson problem on a 64^3 grid (n = 262144), HSS compression on
+fronts with n_f >= 1024 at relative tolerance 1e-4, d0 = 128 and dd = 64
+sample columns, one right-hand side uniform on [-1, 1] (seed 1), sampling
+matrix from seed 0.  Two forms are timed on the same GPU: the mixed form
+(FP32 fronts, sampling, ID and ULV preconditioning FP64 GMRES(30); the
+headline ``value``) and the plain FP64 form (``fp64_ms_per_step``).
+
+One step = hssmf_factor + hssmf_solve (GMRES to 1e-10) on device-resident
+inputs; the factor storage (GBs) is far larger than L2, so no flush is
+needed.  ``e2e`` repeats the step through the C ABI with host buffers
+(values, right-hand side and solution copied inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own system on its own GPU
+(replicas: the method has no data-parallel exchange at this size); the
+reported time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(dims=(64, 64, 64), hss_min_front=1024, hss_tol=1e-4, d0=128, dd=64, seed=0,
+                rhs_seed=1, nrhs=1)
+WORKLOAD_NAME = ("3D 7-point Poisson 64^3 (n=262144), geometric ND (8^3 leaves), HSS on fronts >= 1024, "
+                 "eps=1e-4, d0=128, dd=64, 1 RHS U[-1,1] seed 1, GMRES(30) to rel. residual 1e-10")
+CPU_SAMPLE_SIDE = 32  # oracle sample: the same problem family on a 32^3 grid
+METRIC = "factor+solve time to rel. residual 1e-10 (mixed FP32/FP64 vs FP64), 1 GB300"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax = max(smax, float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _problem():
+    import problems
+    A = problems.grid_poisson(WORKLOAD["dims"])
+    b = problems.rhs_uniform(A.n, WORKLOAD["nrhs"], WORKLOAD["rhs_seed"])
+    return A, b
+
+
+def _solver(A, precision):
+    import paper_1502_07405_gb300 as P
+    o = P.Options.defaults(hss_min_front=WORKLOAD["hss_min_front"], hss_tol=WORKLOAD["hss_tol"],
+                           d0=WORKLOAD["d0"], dd=WORKLOAD["dd"], seed=WORKLOAD["seed"],
+                           precision=precision)
+    s = P.Solver(o)
+    s.analyze_grid(WORKLOAD["dims"], A.rowptr, A.colind)
+    return s
+
+
+def _time_steps(s, vals, bt, steps, warmup, ws):
+    """CUDA-event timing of factor + solve on the default stream (the
+    solver's stream); returns per-step ms (max over ranks)."""
+    import torch
+    for _ in range(warmup):
+        s.factor(vals)
+        s.solve(bt)
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(steps):
+        _barrier(ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.factor(vals)
+        x = s.solve(bt)
+        e1.record()
+        torch.cuda.synchronize()
+        out.append(_barrier_max(e0.elapsed_time(e1), ws))
+    return out, x
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    A, b = _problem()
+    vals = torch.tensor(A.values, device="cuda")
+    bt = torch.tensor(np.ascontiguousarray(b[:, 0]), device="cuda")
+    if args.form == "fp64":  # profiling of the plain FP64 form alone
+        s64 = _solver(A, 0)
+        t64, _ = _time_steps(s64, vals, bt, args.steps, args.warmup, ws)
+        if rank == 0:
+            print(json.dumps({"form": "fp64", "ms_per_step": t64, "stats": s64.get_stats()}), flush=True)
+        s64.close()
+        return
+    # mixed form (headline) -------------------------------------------------
+    s = _solver(A, 1)
+    clocks = Clocks(local)
+    for _ in range(args.warmup):
+        s.factor(vals)
+        s.solve(bt)
+    torch.cuda.synchronize()
+    clocks.start()
+    times, x = _time_steps(s, vals, bt, args.steps, 0, ws)
+    clk = clocks.stop()
+    st = s.get_stats()
+    xr = x.cpu().numpy()
+    relres = float(np.linalg.norm(b[:, 0] - A.to_scipy() @ xr) / np.linalg.norm(b[:, 0]))
+    if args.form == "mixed":  # profiling of the mixed form alone
+        if rank == 0:
+            print(json.dumps({"form": "mixed", "ms_per_step": times, "relres": relres,
+                              "stats": st}), flush=True)
+        s.close()
+        return
+    # one profiled step for the phase split and the dominant kernel
+    s.set_profiling(True)
+    s.factor(vals)
+    s.solve(bt)
+    torch.cuda.synchronize()
+    phases = s.get_phase_times()
+    stp = s.get_stats()
+    s.set_profiling(False)
+    # e2e through the C ABI with host buffers --------------------------------
+    vals_h = np.ascontiguousarray(A.values)
+    b_h = np.asfortranarray(b)
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 3))):
+        _barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.factor(vals_h)
+        xh = s.solve(b_h)
+        e2e_t.append(_barrier_max((time.perf_counter() - t0) * 1e3, ws))
+    s.close()
+    # plain FP64 form ---------------------------------------------------------
+    s64 = _solver(A, 0)
+    t64, x64 = _time_steps(s64, vals, bt, max(1, min(args.steps, 3)), 1, ws)
+    st64 = s64.get_stats()
+    s64.close()
+    ms = float(np.median(times))
+    # roofline of the dominant kernel: the interpolative decomposition
+    hbm, src = _peaks()
+    t_id = phases["id"]
+    achieved = stp["id_bytes"] / (t_id * 1e-3) / 1e9 if t_id > 0 else 0.0
+    roof = {"kernel": "k_cpqr_id / k_cpqr_id_cluster (interpolative decomposition, Section 2.2)",
+            "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 5), "traffic": None, "peak_source": src,
+            "launches": stp["id_launches"],
+            "alg_bytes_per_launch": stp["id_bytes"] / max(stp["id_launches"], 1),
+            "avg_launch_ms": t_id / max(stp["id_launches"], 1),
+            "share_of_factor": round(t_id / max(stp["t_factor_ms"], 1e-9), 3)}
+    line = {
+        "metric": METRIC, "value": round(ms, 2), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 factor + f64 GMRES", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "form": "mixed (FP32 HSS factorization preconditioning FP64 GMRES)",
+                   "l2": "no flush: factor storage and inputs are GBs, far larger than L2",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "fp64_ms_per_step": round(float(np.median(t64)), 2),
+        "mixed_over_fp64_speedup": round(float(np.median(t64)) / ms, 3),
+        "iterations": st["iterations"], "relres": relres, "fp64_iterations": st64["iterations"],
+        "factor_ms": round(st["t_factor_ms"], 2), "solve_ms": round(st["t_solve_ms"], 2),
+        "max_hss_rank": st["max_rank"], "max_d": st["max_d"], "hss_fronts": st["n_hss_fronts"],
+        "factor_flops": st["factor_flops"], "phases_ms": {k: round(v, 2) for k, v in phases.items()},
+        "gpu_launches": st["gpu_launches"],
+        "e2e": {"value": round(float(np.median(e2e_t)), 2), "unit": "ms",
+                "h2d_bytes_per_step": int(A.values.nbytes + b.nbytes),
+                "d2h_bytes_per_step": int(b.nbytes)},
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if ws > 1:
+        line["systems_per_s"] = round(ws / (ms * 1e-3), 4)
+    if rank == 0:
+        if ws == 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(st["factor_flops"])
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _oracle_step(side):
+    """Oracle factor + GMRES on a side^3 grid with the workload's settings."""
+    import problems
+    from oracle import krylov, multifrontal as mf
+    dims = (side,) * 3
+    A = problems.grid_poisson(dims).to_scipy()
+    b = problems.rhs_uniform(A.shape[0], 1, WORKLOAD["rhs_seed"])[:, 0]
+    t0 = time.perf_counter()
+    fz = mf.factor(A, dims, mf.Options(hss_tol=WORKLOAD["hss_tol"], d0=WORKLOAD["d0"], dd=WORKLOAD["dd"],
+                                        hss_min_front=WORKLOAD["hss_min_front"], seed=WORKLOAD["seed"]))
+    x, its, rel = krylov.gmres(A, lambda v: mf.apply_inverse(fz, v), b, rtol=1e-10)
+    return time.perf_counter() - t0, rel
+
+
+def _flops_at(side):
+    """Library factor flops on a side^3 grid (same settings), for scaling."""
+    import paper_1502_07405_gb300 as P
+    import problems
+    A = problems.grid_poisson((side,) * 3)
+    s = P.Solver(P.Options.defaults(hss_min_front=WORKLOAD["hss_min_front"], hss_tol=WORKLOAD["hss_tol"],
+                                    d0=WORKLOAD["d0"], dd=WORKLOAD["dd"], maxit=0))
+    s.analyze_grid((side,) * 3, A.rowptr, A.colind)
+    s.factor(A.values)
+    f = s.get_stats()["factor_flops"]
+    s.close()
+    return f
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(full_flops):
+    t, rel = _oracle_step(CPU_SAMPLE_SIDE)
+    f_sample = _flops_at(CPU_SAMPLE_SIDE)
+    scale = full_flops / f_sample if f_sample > 0 else float("nan")
+    return {"value": round(t * 1e3 * scale, 1), "unit": "ms", "cores": _cores(), "kind": "oracle",
+            "sample": (f"oracle (numpy FP64) factor + GMRES on the 32^3 grid with the same settings "
+                       f"({t:.1f} s, rel. residual {rel:.1e}), scaled to 64^3 by the library's factor-flop "
+                       f"ratio {scale:.1f}"),
+            "sample_seconds": round(t, 2)}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    # warm-up steps on a tiny grid (the oracle has no state to warm)
+    for _ in range(args.warmup):
+        _oracle_step(8)
+    full = None
+    try:
+        full = _flops_at(WORKLOAD["dims"][0])
+        f_sample = _flops_at(CPU_SAMPLE_SIDE)
+        scale = full / f_sample
+    except Exception as e:  # no GPU: report the unscaled sample time
+        scale, f_sample = 1.0, None
+    times = []
+    for _ in range(args.steps):
+        t, rel = _oracle_step(CPU_SAMPLE_SIDE)
+        times.append(t * 1e3 * scale)
+    times.sort()
+    ms = times[len(times) // 2]
+    line = {"impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": "ms", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "form": "CPU oracle (numpy FP64)"},
+            "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": _cores(), "kind": "oracle",
+                             "sample": (f"oracle factor + GMRES on the 32^3 grid, same settings, scaled to "
+                                        f"64^3 by the library's factor-flop ratio {scale:.1f}")},
+            "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--form", choices=["both", "mixed", "fp64"], default="both",
+                    help="forms to time (profiling runs use one)")
+    ap.add_argument("--small", action="store_true",
+                    help="32^3 grid instead of 64^3 (profiling captures only; not a bench line)")
+    args = ap.parse_args()
+    if args.small:
+        WORKLOAD["dims"] = (32, 32, 32)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -84,6 +84,9 @@ typedef struct {
   double t_factor_ms;    /* device time of the last factor (CUDA events) */
   double t_solve_ms;     /* device time of the last solve (CUDA events) */
   int gpu_launches;      /* kernels launched by the last factor + solve */
+  int id_launches;       /* interpolative-decomposition kernel launches of the last factor */
+  double id_bytes;       /* their algorithmic bytes: sum of m d + k (m - k) elements */
+  double id_flops;       /* their algorithmic flops: sum of 4mdk - 2k^2(m + d) + 4k^3/3 */
 } hssmf_stats;
 
 /* Fill *opts with the defaults named above (hss_tol 1e-4, d0 128, dd 64,
@@ -141,6 +144,39 @@ hssmf_status hssmf_get_symbolic(const hssmf_ctx* ctx, int* perm, int* sep_begin,
 
 /* I^upd of front f (ascending new indices) into upd[n_upd[f]]. */
 hssmf_status hssmf_get_upd(const hssmf_ctx* ctx, int f, int* upd);
+
+/* Per-phase device times of the last factor + solve (CUDA events, ms), in
+ * this order: 0 dense-front assembly and partial LU, 1 sampling (R, A_i R,
+ * child-update GEMMs), 2 element extraction, 3 pre-ID sample updates,
+ * 4 interpolative decompositions, 5 post-ID updates, 6 ULV factorization,
+ * 7 nested bases, Theta^* Phi and update matrices, 8 multifrontal solve
+ * (all preconditioner applications), 9 outer-iteration kernels.  Writes
+ * min(n, 10) values; phase timing is recorded only after
+ * hssmf_set_profiling(ctx, 1). */
+hssmf_status hssmf_get_phase_times(const hssmf_ctx* ctx, double* ms, int n);
+hssmf_status hssmf_set_profiling(hssmf_ctx* ctx, int on);
+
+/* Kernel-level entry point: a batch of interpolative decompositions
+ * (Section 2.2, ID definitions; rank rule of Section 5.3).  Job j selects
+ * columns of Y_j (d_j x m_j, column-major, leading dimension d_j, device
+ * memory at Y + y_off[j] elements, arithmetic T = double for prec 0, float
+ * for prec 1) by column-pivoted Householder QR with column norms recomputed
+ * from the trailing rows at every step (FP64) and the first largest norm
+ * winning; the rank k_j is the first i with |R_{i+1,i+1}| <= eps |R_11|
+ * (0 if R_11 = 0), else min(d_j, m_j).  Outputs: rank_host[j];
+ * piv + p_off[j] (m_j ints, device): the k_j skeleton columns first, in
+ * pivot order; X + x_off[j] (device, k_j x (m_j - k_j), leading dimension
+ * k_j, room for m_j * m_j / 4 + 1 elements): X = R1^-1 R2 for the
+ * non-skeleton columns in the order piv[k_j:], so Y ~ Y(:, piv[:k]) [I X]
+ * and the interpolative basis is Pi [I; X^T].  y_off, m, d, p_off, x_off
+ * are host arrays.  use_cluster = 0 runs every job on one CTA; 1..8 on a
+ * thread-block cluster of 8 CTAs, 16 on a cluster of 16 CTAs (where the
+ * device can schedule it, else 8).  Y is not modified.  Synchronizes the
+ * stream. */
+hssmf_status hssmf_batched_id(int prec, int njobs, const void* Y, const long long* y_off,
+                              const int* m, const int* d, double eps, int* rank_host, int* piv,
+                              const long long* p_off, void* X, const long long* x_off,
+                              int use_cluster, void* cuda_stream);
 
 const char* hssmf_last_error(const hssmf_ctx* ctx);
 void hssmf_destroy(hssmf_ctx* ctx);

@@ -60,7 +60,8 @@ class Stats(C.Structure):
                 ("relres", C.c_double), ("factor_flops", C.c_double),
                 ("factor_bytes", C.c_double), ("t_analyze_ms", C.c_double),
                 ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double),
-                ("gpu_launches", C.c_int)]
+                ("gpu_launches", C.c_int), ("id_launches", C.c_int), ("id_bytes", C.c_double),
+                ("id_flops", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -79,12 +80,15 @@ lib.hssmf_solve_T.argtypes = [_P, _P, _P, _I, _I]
 lib.hssmf_get_stats.argtypes = [_P, C.POINTER(Stats)]
 lib.hssmf_get_symbolic.argtypes = [_P, _IP, _IP, _IP, _IP, _IP]
 lib.hssmf_get_upd.argtypes = [_P, _I, _IP]
+lib.hssmf_get_phase_times.argtypes = [_P, C.POINTER(C.c_double), _I]
+lib.hssmf_set_profiling.argtypes = [_P, _I]
 lib.hssmf_last_error.argtypes = [_P]
 lib.hssmf_last_error.restype = C.c_char_p
 lib.hssmf_destroy.argtypes = [_P]
 lib.hssmf_destroy.restype = None
 for _f in ("hssmf_create", "hssmf_analyze_grid", "hssmf_factor", "hssmf_solve", "hssmf_solve_T",
-           "hssmf_get_stats", "hssmf_get_symbolic", "hssmf_get_upd"):
+           "hssmf_get_stats", "hssmf_get_symbolic", "hssmf_get_upd", "hssmf_get_phase_times",
+           "hssmf_set_profiling"):
     getattr(lib, _f).restype = C.c_int
 
 
@@ -192,6 +196,17 @@ class Solver:
         s = Stats()
         self._check(lib.hssmf_get_stats(self._h, C.byref(s)))
         return s.as_dict()
+
+    PHASES = ("dense", "sample", "extract", "pre_id", "id", "post_id", "ulv", "schur", "solve",
+              "outer")
+
+    def set_profiling(self, on=True):
+        self._check(lib.hssmf_set_profiling(self._h, int(bool(on))))
+
+    def get_phase_times(self):
+        buf = (C.c_double * len(self.PHASES))()
+        self._check(lib.hssmf_get_phase_times(self._h, buf, len(self.PHASES)))
+        return dict(zip(self.PHASES, list(buf)))
 
     def get_symbolic(self, n_fronts):
         perm = np.zeros(self.n, dtype=np.int32)

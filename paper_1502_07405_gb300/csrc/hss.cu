@@ -31,6 +31,11 @@ namespace hssmf {
 namespace {
 
 constexpr size_t ALIGN = 256;
+// IDs with d * m at least this large run on a thread-block cluster
+// (measured on GB300: one CTA is fastest for nodes of <= 256 columns, 8-CTA
+// clusters for d * m up to ~1M, 16-CTA clusters beyond)
+constexpr long long kClusterIdWork = 64 * 1024;
+constexpr long long kClusterIdWork16 = 1024 * 1024;  // ... and on 16 CTAs from this size
 
 struct Pool {  // device bump allocator over large chunks
   std::vector<std::pair<char*, size_t>> chunks;
@@ -347,6 +352,7 @@ void sample_fronts(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     }
     sj.push_back(SampleAJob{F->Sr, F->Sc, F->R, F->nf, F->f, c0, c1, 0});
   }
+  X.c.prof.mark(PH_SAMPLE, X.s);
   X.launch(pj, [&](const PhiloxJob* d, int n) { HssKern<T>::philox(d, n, max_rows, c.opts.seed, X.s); });
   X.launch(sj, [&](const SampleAJob* d, int n) { HssKern<T>::sample_a(c.ds, c.d_values, d, n, max_nf, X.s); });
   for (int k = 0; k < 2; ++k) {  // one launch per child slot: deterministic order of the sums
@@ -442,6 +448,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           N.mc = a.kc + b.kc;
         }
       }
+      c.prof.mark(PH_EXTRACT, X.s);
       // (a) D of the leaves, B of the sibling pairs: submatrices of F_i
       std::vector<ExtractJob> ej;
       for (auto& it : batch) {
@@ -465,6 +472,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       X.launch(ej, [&](const ExtractJob* d, int n) {
         HssKern<T>::extract(c.ds, c.d_values, X.arena(), d, n, X.s);
       });
+      c.prof.mark(PH_PREID, X.s);
       // (b) samples of the node before the ID, stored transposed (d x rows)
       for (auto& it : batch) {
         const ClusterTree& tr = S.fronts[it.F->f].tree;
@@ -504,6 +512,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         }
       }
       X.flush_gemm();
+      c.prof.mark(PH_ID, X.s);
       // (c) interpolative decompositions of the nodes not yet compressed
       std::vector<IdJob> ij;
       std::vector<Item> idn;
@@ -531,19 +540,53 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during HSS compression");
       if (!ij.empty()) {
         if ((int)ij.size() > H.rank_cap) return c.fail(HSSMF_ERR_ARG, "too many IDs in one level");
-        const IdJob* dj = H.ring.put(ij, X.s);
-        if (!dj) return c.fail(HSSMF_ERR_OOM, "job ring");
-        if (HssKern<T>::batched_id(dj, (int)ij.size(), maxm, eps, X.s) < 0)
-          return c.fail(HSSMF_ERR_ARG, "an HSS node is too large for the ID kernel");
+        // large IDs on thread-block clusters (16 CTAs for the largest), small
+        // ones on one CTA each
+        std::vector<IdJob> tier[3];
+        int tm[3] = {0, 0, 0}, td[3] = {0, 0, 0};
+        for (const IdJob& j : ij) {
+          const long long w = (long long)j.d * j.m;
+          const int t = (w >= kClusterIdWork16 && j.m > 256) ? 2 : (w >= kClusterIdWork && j.m > 256) ? 1 : 0;
+          tier[t].push_back(j);
+          tm[t] = std::max(tm[t], j.m);
+          td[t] = std::max(td[t], j.d);
+        }
+        for (int t = 2; t >= 1; --t) {
+          if (tier[t].empty()) continue;
+          const int bk = std::max(std::min(tm[t], td[t]), 1);
+          double* rdiag = (double*)H.rnd.alloc(sizeof(double) * tier[t].size() * bk);
+          int* order = (int*)H.rnd.alloc(sizeof(int) * tier[t].size() * std::max(tm[t], 1));
+          const IdJob* dj = H.ring.put(tier[t], X.s);
+          if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
+          if (HssKern<T>::batched_id_cluster(dj, (int)tier[t].size(), tm[t], td[t], eps, rdiag, order, X.s,
+                                             t == 2 ? 16 : 8) < 0) {
+            tier[0].insert(tier[0].end(), tier[t].begin(), tier[t].end());  // one CTA per job
+            tm[0] = std::max(tm[0], tm[t]);
+            td[0] = std::max(td[0], td[t]);
+          }
+        }
+        if (!tier[0].empty()) {
+          const IdJob* dj = H.ring.put(tier[0], X.s);
+          if (!dj) return c.fail(HSSMF_ERR_OOM, "job ring");
+          if (HssKern<T>::batched_id(dj, (int)tier[0].size(), tm[0], td[0], eps, X.s) < 0)
+            return c.fail(HSSMF_ERR_ARG, "an HSS node is too large for the ID kernel");
+        }
         hssmf_status st = c.cuda_check(cudaMemcpyAsync(H.h_ranks, H.d_ranks, sizeof(int) * ij.size(),
                                                        cudaMemcpyDeviceToHost, X.s), "ranks");
         if (st) return st;
         if ((st = c.cuda_check(cudaStreamSynchronize(X.s), "ID"))) return st;
         H.ring.off = 0;
+        c.prof.resolve();
+        for (int t = 0; t < 3; ++t) c.id_launches += tier[t].empty() ? 0 : 1;
         for (size_t i = 0; i < idn.size(); ++i) {
           FrontRt& F = *idn[i].F;
           NodeRt& N = F.nd[idn[i].t];
           const int kr = H.h_ranks[2 * i], kc = H.h_ranks[2 * i + 1], d = F.d;
+          for (int side = 0; side < 2; ++side) {  // algorithmic work of the two IDs
+            const double mm = side ? N.mc : N.m, kk = side ? kc : kr;
+            c.id_bytes += sizeof(T) * (mm * d + kk * (mm - kk));
+            c.id_flops += 4.0 * mm * d * kk - 2.0 * kk * kk * (mm + d) + 4.0 * kk * kk * kk / 3.0;
+          }
           const bool cap = d >= F.nf;
           const bool ok_r = kr <= d - p || kr == N.m || cap;
           const bool ok_c = kc <= d - p || kc == N.mc || cap;
@@ -556,6 +599,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           }
         }
       }
+      c.prof.mark(PH_POSTID, X.s);
       // (d) after the ID: S <- S(J, :), R^r = V^* R, R^c = U^* R, skeleton sets
       std::vector<IntGatherJob> ig;
       for (auto& it : batch) {
@@ -608,6 +652,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       X.flush_gemm();
       X.launch(ig, [&](const IntGatherJob* d, int n) { HssKern<T>::int_gather(d, n, X.s); });
     }
+    c.prof.mark(PH_EXTRACT, X.s);
     // end of the round: fronts with every non-root node compressed are done
     std::vector<ExtractJob> ej;
     std::vector<FrontRt*> next;
@@ -662,10 +707,11 @@ void ulv_solve(Ctx<T>& X, const std::vector<FrontRt*>& fs, const std::vector<con
                const std::vector<long long>& ldin, const std::vector<T*>& xout,
                const std::vector<long long>& ldout, const std::vector<int>& nrhs, Pool& pool) {
   const Symbolic& S = X.c.sym;
-  int maxh = 0;
+  int maxh = 0, maxnr = 1;
   for (size_t i = 0; i < fs.size(); ++i) {
     FrontRt& F = *fs[i];
     maxh = std::max(maxh, F.height[F.k]);
+    maxnr = std::max(maxnr, nrhs[i]);
     for (int t : F.f11) {
       NodeRt& N = F.nd[t];
       N.bt = X.A(pool, (long long)N.m * nrhs[i]);
@@ -721,7 +767,7 @@ void ulv_solve(Ctx<T>& X, const std::vector<FrontRt*>& fs, const std::vector<con
         jobs.push_back(j);
       }
     }
-    X.launch(jobs, [&](const UlvFwdJob* d, int n) { HssKern<T>::ulv_fwd(d, n, X.s); });
+    X.launch(jobs, [&](const UlvFwdJob* d, int n) { HssKern<T>::ulv_fwd(d, n, maxnr, X.s); });
   }
   for (int lv = maxh; lv >= 0; --lv) {
     std::vector<UlvBwdJob> jobs;
@@ -760,7 +806,7 @@ void ulv_solve(Ctx<T>& X, const std::vector<FrontRt*>& fs, const std::vector<con
       }
     }
     X.flush_copy();
-    X.launch(jobs, [&](const UlvBwdJob* d, int n) { HssKern<T>::ulv_bwd(d, n, X.s); });
+    X.launch(jobs, [&](const UlvBwdJob* d, int n) { HssKern<T>::ulv_bwd(d, n, maxnr, X.s); });
   }
 }
 
@@ -771,6 +817,7 @@ hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
   hssmf_ctx& c = X.c;
   HssState& H = X.H;
   const Symbolic& S = c.sym;
+  c.prof.mark(PH_ULV, X.s);
   // explicit interpolative bases U = Pi_r [I; E_r], V = Pi_c [I; E_c]
   std::vector<BasisJob> bj;
   for (FrontRt* F : fs) {
@@ -890,6 +937,7 @@ hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     X.launch(lu, [&](const LuJob* d, int n) { HssKern<T>::lu(d, n, c.d_status, X.s); });
   }
   if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during the ULV factorization");
+  c.prof.mark(PH_SCHUR, X.s);
   // nested bases U^big, V^big of every non-root node, bottom-up
   int th = 0;
   for (FrontRt* F : fs) th = std::max(th, F->tree_h);
@@ -1025,6 +1073,8 @@ std::vector<FrontRt*> level_fronts(HssState& H, const LevelPlan& L) {
 
 void hss_begin_factor(hssmf_ctx& c) {
   c.hss_max_rank = c.hss_max_d = c.hss_rounds = 0;
+  c.id_launches = 0;
+  c.id_bytes = c.id_flops = 0.0;
   c.hss_flops = c.hss_bytes = 0.0;
   if (!c.hss) return;
   c.hss->fac.reset();

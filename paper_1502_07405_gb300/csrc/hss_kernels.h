@@ -128,12 +128,16 @@ struct HssKern {
   static void extract(const DevSym& ds, const double* values, const T* arena, const ExtractJob* jobs,
                       int njobs, cudaStream_t s);
   // returns -1 if max_m exceeds the shared-memory bound of the kernel
-  static int batched_id(const IdJob* jobs, int njobs, int max_m, double eps, cudaStream_t s);
+  static int batched_id(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, cudaStream_t s);
+  // one thread-block cluster of cl (8 or 16) CTAs per job; rdiag (njobs x min(max_m, max_d)
+  // doubles) and order (njobs x max_m ints) are scratch.  Returns -1 if no launch is possible.
+  static int batched_id_cluster(const IdJob* jobs, int njobs, int max_m, int max_d, double eps,
+                                double* rdiag, int* order, cudaStream_t s, int cl = 8);
   static void basis(const BasisJob* jobs, int njobs, cudaStream_t s);
   static void lq(const LqJob* jobs, int njobs, cudaStream_t s);
   static void lu(const LuJob* jobs, int njobs, unsigned* status, cudaStream_t s);
-  static void ulv_fwd(const UlvFwdJob* jobs, int njobs, cudaStream_t s);
-  static void ulv_bwd(const UlvBwdJob* jobs, int njobs, cudaStream_t s);
+  static void ulv_fwd(const UlvFwdJob* jobs, int njobs, int max_nrhs, cudaStream_t s);
+  static void ulv_bwd(const UlvBwdJob* jobs, int njobs, int max_nrhs, cudaStream_t s);
 };
 
 }  // namespace hssmf

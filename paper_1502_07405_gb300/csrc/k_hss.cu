@@ -1,4 +1,6 @@
 // Kernels of the HSS frontal matrices (Sections 2.2, 2.3, 4.3-4.5).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -36,6 +38,57 @@ __device__ double block_sum_d(double v, double* sh) {
   for (int w = 0; w < nw; ++w) s += sh[w];
   __syncthreads();
   return s;
+}
+
+// One warp applies H = I - tau v v^T (v[i] = 1, rows i..d-1 of v in shared
+// memory) to the column wj and returns the squared norm of rows i+1..d-1 of
+// the result in every lane.  Up to 32 rows per lane stay in registers, so
+// the column is read once.
+template <typename T, int RPL>
+__device__ __forceinline__ double warp_reflect_reg(T* wj, const double* v, int i, int d, T tau, int lane) {
+  {
+    T xr[RPL];
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int r = i + lane + 32 * q;
+      xr[q] = r < d ? wj[r] : T(0);
+      if (r < d) s += T(v[r]) * xr[q];
+    }
+    s = wsum<T>(s);
+    const T f = tau * s;
+    double nn = 0.0;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int r = i + lane + 32 * q;
+      if (r < d) {
+        const T x = xr[q] - f * T(v[r]);
+        wj[r] = x;
+        if (r > i) nn += (double)x * (double)x;
+      }
+    }
+    return warp_sum(nn);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ double warp_reflect(T* wj, const double* v, int i, int d, T tau, int lane) {
+  const int rows = d - i;
+  if (rows <= 32 * 4) return warp_reflect_reg<T, 4>(wj, v, i, d, tau, lane);
+  if (rows <= 32 * 8) return warp_reflect_reg<T, 8>(wj, v, i, d, tau, lane);
+  if (rows <= 32 * 16) return warp_reflect_reg<T, 16>(wj, v, i, d, tau, lane);
+  if (rows <= 32 * 32) return warp_reflect_reg<T, 32>(wj, v, i, d, tau, lane);
+  T s = T(0);
+  for (int r = i + lane; r < d; r += 32) s += T(v[r]) * wj[r];
+  s = wsum<T>(s);
+  const T f = tau * s;
+  double nn = 0.0;
+  for (int r = i + lane; r < d; r += 32) {
+    const T x = wj[r] - f * T(v[r]);
+    wj[r] = x;
+    if (r > i) nn += (double)x * (double)x;
+  }
+  return warp_sum(nn);
 }
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, Weyl key schedule.
@@ -245,7 +298,8 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr_id(const IdJob* __restrict_
   T* W = (T*)jb.W;
   extern __shared__ double smem[];
   double* cn = smem;              // m column norms^2
-  int* perm = (int*)(smem + m);   // m
+  double* vsh = smem + m;         // d: Householder vector of the step
+  int* perm = (int*)(vsh + d);    // m
   __shared__ double s_bv[ID_THREADS / 32];
   __shared__ int s_bi[ID_THREADS / 32];
   __shared__ double s_best;
@@ -316,26 +370,12 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr_id(const IdJob* __restrict_
     const T beta = alpha >= T(0) ? T(-nrm) : T(nrm);
     const T tau = (beta - alpha) / beta;
     const T scl = T(1) / (alpha - beta);
-    for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) W[r + i * ld] *= scl;
+    for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) vsh[r] = (double)(W[r + i * ld] * scl);
+    if (threadIdx.x == 0) vsh[i] = 1.0;
     __syncthreads();
     for (int j = i + 1 + wid; j < m; j += nw) {
-      T* wj = W + j * ld;
-      T s = T(0);
-      for (int r = i + 1 + lane; r < d; r += 32) s += W[r + i * ld] * wj[r];
-      s = wsum<T>(s) + wj[i];
-      const T fct = tau * s;
-      double nn = 0.0;
-      for (int r = i + 1 + lane; r < d; r += 32) {
-        T v = wj[r] - fct * W[r + i * ld];
-        wj[r] = v;
-        nn += (double)v * (double)v;
-      }
-      nn = warp_sum(nn);
-      __syncwarp();
-      if (lane == 0) {
-        wj[i] -= fct;
-        cn[j] = nn;
-      }
+      const double nn = warp_reflect<T>(W + j * ld, vsh, i, d, tau, lane);
+      if (lane == 0) cn[j] = nn;
     }
     __syncthreads();
     if (threadIdx.x == 0) W[i + i * ld] = beta;
@@ -358,10 +398,12 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr_id(const IdJob* __restrict_
 }
 
 template <typename T>
-int HssKern<T>::batched_id(const IdJob* jobs, int njobs, int max_m, double eps, cudaStream_t s) {
+int HssKern<T>::batched_id(const IdJob* jobs, int njobs, int max_m, int max_d, double eps,
+                           cudaStream_t s) {
   if (njobs <= 0) return 0;
-  const size_t smem = 12 * (size_t)std::max(max_m, 1);  // m norms (double) + m pivots (int)
-  if (smem > 200 * 1024) return -1;                       // m above 17066 is not supported
+  // m norms (double), d vector entries (double), m pivots (int)
+  const size_t smem = 12 * (size_t)std::max(max_m, 1) + 8 * (size_t)std::max(max_d, 1);
+  if (smem > 200 * 1024) return -1;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_cpqr_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -370,6 +412,209 @@ int HssKern<T>::batched_id(const IdJob* jobs, int njobs, int max_m, double eps, 
   k_cpqr_id<T><<<njobs, ID_THREADS, smem, s>>>(jobs, eps);
   count_launch();
   return 0;
+}
+
+// ---------------------------------------------------------------------------
+// The same ID for large nodes on a thread-block cluster of ID_CL CTAs (one
+// cluster per job).  CTA r of the cluster owns the columns j = r (mod ID_CL)
+// of W (global memory, L2-resident).  Per step: every CTA proposes its
+// largest remaining column norm; the cluster reduces the proposals through
+// distributed shared memory (largest norm, then smallest column index);
+// every CTA rebuilds the Householder vector from the pivot column and applies
+// it to its own columns, recomputing their norms from the trailing rows.
+// Columns are not moved: the pivot order is recorded, the skeleton columns
+// come first in piv and the others follow in increasing index, and X = R1^-1
+// R2 is laid out in that order (the basis Pi [I; X^T] does not depend on the
+// order of the non-skeleton columns).
+// ---------------------------------------------------------------------------
+template <typename T, int ID_CL>
+__global__ void __launch_bounds__(ID_THREADS) k_cpqr_id_cluster(const IdJob* __restrict__ jobs,
+                                                                double eps, double* rdiag_all,
+                                                                int* order_all, int max_m, int max_k) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int jid = blockIdx.x / ID_CL;
+  const IdJob jb = jobs[jid];
+  const int d = jb.d, m = jb.m;
+  const long long ld = d;
+  const T* Y = (const T*)jb.Y;
+  T* W = (T*)jb.W;
+  double* rdiag = rdiag_all + (long long)jid * max_k;  // |R| diagonal, by step
+  int* order = order_all + (long long)jid * max_m;     // pivot column of each step
+  extern __shared__ double smem[];
+  const int mo = (m - rank + ID_CL - 1) / ID_CL;  // columns owned by this CTA: rank + ID_CL * l
+  double* cn = smem;                               // mo norms^2 (negative: pivoted)
+  double* v = cn + mo;                             // d: Householder vector of the step
+  unsigned char* skel = (unsigned char*)(v + d);   // m flags, replicated in every CTA
+  __shared__ double s_bv[ID_THREADS / 32];
+  __shared__ int s_bi[ID_THREADS / 32];
+  __shared__ double s_cand_v;
+  __shared__ int s_cand_i;
+  __shared__ double s_best;
+  __shared__ int s_p;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = wid; l < mo; l += nw) {
+    const int j = rank + ID_CL * l;
+    double s = 0.0;
+    for (int r = lane; r < d; r += 32) {
+      T x = Y[r + j * ld];
+      W[r + j * ld] = x;
+      s += (double)x * (double)x;
+    }
+    s = warp_sum(s);
+    if (lane == 0) cn[l] = s;
+  }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) skel[j] = 0;
+  __syncthreads();
+  const int kmax = min(d, m);
+  int k = kmax;
+  double r11 = 0.0;
+  for (int i = 0; i < kmax; ++i) {
+    // local proposal: largest norm among the owned, unpivoted columns
+    double bv = -1.0;
+    int bi = m;
+    for (int l = threadIdx.x; l < mo; l += blockDim.x) {
+      double x = cn[l];
+      if (x > bv) { bv = x; bi = rank + ID_CL * l; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = s_bv[0];
+      int ix = s_bi[0];
+      for (int w = 1; w < nw; ++w)
+        if (s_bv[w] > b || (s_bv[w] == b && s_bi[w] < ix)) { b = s_bv[w]; ix = s_bi[w]; }
+      s_cand_v = b;
+      s_cand_i = ix;
+    }
+    cluster.sync();
+    if (wid == 0) {  // every CTA reduces the same proposals (lane r reads CTA r)
+      double b = -1.0;
+      int ix = m;
+      if (lane < ID_CL) {
+        b = *cluster.map_shared_rank(&s_cand_v, lane);
+        ix = *cluster.map_shared_rank(&s_cand_i, lane);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, b, o);
+        int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+        if (ov > b || (ov == b && oi < ix)) { b = ov; ix = oi; }
+      }
+      if (lane == 0) {
+        s_best = b;
+        s_p = ix;
+      }
+    }
+    __syncthreads();
+    const double nrm = sqrt(fmax(s_best, 0.0));
+    const int p = s_p;
+    if (i == 0) {
+      r11 = nrm;
+      if (!(r11 > 0.0)) { k = 0; break; }
+    } else if (!(nrm > eps * r11) || p >= m) {
+      k = i;
+      break;
+    }
+    // Householder vector of the pivot column, rows i..d-1
+    const T alpha = W[i + p * ld];
+    const T beta = alpha >= T(0) ? T(-nrm) : T(nrm);
+    const T tau = (beta - alpha) / beta;
+    const T scl = T(1) / (alpha - beta);
+    for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) v[r] = (double)(W[r + p * ld] * scl);
+    if (threadIdx.x == 0) {
+      v[i] = 1.0;
+      skel[p] = 1;
+      if (rank == 0) {
+        rdiag[i] = (double)beta;
+        order[i] = p;
+      }
+    }
+    if (p % ID_CL == rank && threadIdx.x == 0) cn[p / ID_CL] = -1.0;
+    __syncthreads();
+    // apply to the owned unpivoted columns; recompute their norms
+    for (int l = wid; l < mo; l += nw) {
+      const int j = rank + ID_CL * l;
+      if (j == p || skel[j]) continue;
+      const double nn = warp_reflect<T>(W + j * ld, v, i, d, tau, lane);
+      if (lane == 0) cn[l] = nn;
+    }
+    cluster.sync();  // every column updated before the next proposals
+  }
+  // No CTA leaves while a peer may still read its proposal; also publishes
+  // every column update and rdiag/order to the whole cluster.
+  cluster.sync();
+  // X = R1^-1 R2, one warp per owned non-skeleton column; R1(r, c) = W[r, order[c]],
+  // R1(r, r) = rdiag[r] (written by CTA 0 before the last cluster barrier)
+  const double* rd = rdiag;
+  T* X = (T*)jb.X;
+  for (int l = wid; l < mo; l += nw) {
+    const int j = rank + ID_CL * l;
+    if (skel[j]) continue;
+    int pos = 0;  // number of non-skeleton columns before j
+    for (int c = lane; c < j; c += 32) pos += skel[c] ? 0 : 1;
+    for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+    T* x = X + (long long)pos * k;
+    for (int r = k - 1; r >= 0; --r) {
+      T s = T(0);
+      for (int c = r + 1 + lane; c < k; c += 32) s += W[r + (long long)order[c] * ld] * x[c];
+      s = wsum<T>(s);
+      if (lane == 0) x[r] = (W[r + j * ld] - s) / T(rd[r]);
+      __syncwarp();
+    }
+    if (lane == 0) jb.piv[k + pos] = j;
+  }
+  if (rank == 0) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) jb.piv[i] = order[i];
+    if (threadIdx.x == 0) *jb.rank = k;
+  }
+}
+
+template <typename T, int CL>
+static int launch_id_cluster(const IdJob* jobs, int njobs, int max_m, int max_d, double eps,
+                             double* rdiag, int* order, cudaStream_t s) {
+  const size_t smem = sizeof(double) * ((size_t)max_m / CL + 1 + (size_t)max_d) + (size_t)max_m + 16;
+  if (smem > 200 * 1024) return -1;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cpqr_id_cluster<T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (CL > 8) cudaFuncSetAttribute(k_cpqr_id_cluster<T, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaGetLastError();
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * CL, 1, 1);
+  cfg.blockDim = dim3(ID_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const int max_k = std::max(std::min(max_m, max_d), 1);
+  if (cudaLaunchKernelEx(&cfg, k_cpqr_id_cluster<T, CL>, jobs, eps, rdiag, order, std::max(max_m, 1),
+                         max_k) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;  // cluster not schedulable: the caller falls back
+  }
+  count_launch();
+  return 0;
+}
+
+template <typename T>
+int HssKern<T>::batched_id_cluster(const IdJob* jobs, int njobs, int max_m, int max_d, double eps,
+                                   double* rdiag, int* order, cudaStream_t s, int cl) {
+  if (njobs <= 0) return 0;
+  if (cl >= 16 && launch_id_cluster<T, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s) == 0) return 0;
+  return launch_id_cluster<T, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -545,7 +790,7 @@ __global__ void __launch_bounds__(256) k_ulv_fwd(const UlvFwdJob* __restrict__ j
   const T* bh2 = (const T*)jb.bh2;
   const T* wc1 = (const T*)jb.wc1;
   const T* wc2 = (const T*)jb.wc2;
-  for (int j = 0; j < nrhs; ++j) {
+  for (int j = blockIdx.y; j < nrhs; j += gridDim.y) {  // columns are independent
     T* bt = (T*)jb.bt + (long long)j * m;
     T* bo = (T*)jb.bo + (long long)j * m;
     if (jb.leaf) {
@@ -619,9 +864,9 @@ __global__ void __launch_bounds__(256) k_ulv_fwd(const UlvFwdJob* __restrict__ j
 }
 
 template <typename T>
-void HssKern<T>::ulv_fwd(const UlvFwdJob* jobs, int njobs, cudaStream_t s) {
+void HssKern<T>::ulv_fwd(const UlvFwdJob* jobs, int njobs, int max_nrhs, cudaStream_t s) {
   if (njobs <= 0) return;
-  k_ulv_fwd<T><<<njobs, 256, 0, s>>>(jobs);
+  k_ulv_fwd<T><<<dim3(njobs, std::min(std::max(max_nrhs, 1), 256)), 256, 0, s>>>(jobs);
   count_launch();
 }
 
@@ -638,7 +883,7 @@ __global__ void __launch_bounds__(256) k_ulv_bwd(const UlvBwdJob* __restrict__ j
   const T* x1 = (const T*)jb.x1;
   const T* xh2 = (const T*)jb.xh2;
   __shared__ double sh[33];
-  for (int j = 0; j < nrhs; ++j) {
+  for (int j = blockIdx.y; j < nrhs; j += gridDim.y) {  // columns are independent
     T* x = (T*)jb.out + (long long)j * jb.ldout;
     for (int i = threadIdx.x; i < nk; i += blockDim.x) x[i] = x1[i + (long long)j * m];
     for (int i = threadIdx.x; i < jb.k; i += blockDim.x) x[nk + i] = xh2[i + (long long)j * jb.ldxh2];
@@ -660,9 +905,9 @@ __global__ void __launch_bounds__(256) k_ulv_bwd(const UlvBwdJob* __restrict__ j
 }
 
 template <typename T>
-void HssKern<T>::ulv_bwd(const UlvBwdJob* jobs, int njobs, cudaStream_t s) {
+void HssKern<T>::ulv_bwd(const UlvBwdJob* jobs, int njobs, int max_nrhs, cudaStream_t s) {
   if (njobs <= 0) return;
-  k_ulv_bwd<T><<<njobs, 256, 0, s>>>(jobs);
+  k_ulv_bwd<T><<<dim3(njobs, std::min(std::max(max_nrhs, 1), 256)), 256, 0, s>>>(jobs);
   count_launch();
 }
 

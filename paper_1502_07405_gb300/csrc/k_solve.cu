@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_solve_fwd_dense(const DFront* __restric
   const long long ld = f.nf;
   T* w = W + f.w_off;
   __shared__ T sh[33];
-  for (int j = 0; j < nrhs; ++j) {
+  for (int j = blockIdx.y; j < nrhs; j += gridDim.y) {  // columns are independent
     T* x = w + (long long)j * f.nf;
     if (!transpose) {
       if (threadIdx.x == 0) {
@@ -159,7 +159,7 @@ template <typename T>
 void Kern<T>::solve_fwd_dense(const DevSym& ds, const T* arena, const int* piv, T* W,
                               const int* flist, int nfr, int nrhs, int transpose, cudaStream_t s) {
   if (nfr <= 0) return;
-  k_solve_fwd_dense<T><<<nfr, 256, 0, s>>>(ds.fronts, arena, piv, W, flist, nrhs, transpose);
+  k_solve_fwd_dense<T><<<dim3(nfr, std::min(nrhs, 64)), 256, 0, s>>>(ds.fronts, arena, piv, W, flist, nrhs, transpose);
   count_launch();
 }
 
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_solve_bwd_dense(const DFront* __restric
   const T* F = ar + f.off;
   const long long ld = f.nf;
   __shared__ T sh[33];
-  for (int j = 0; j < nrhs; ++j) {
+  for (int j = blockIdx.y; j < nrhs; j += gridDim.y) {  // columns are independent
     T* x = W + f.w_off + (long long)j * f.nf;
     if (!transpose) {
       for (int r = threadIdx.x; r < f.ns; r += blockDim.x) {
@@ -252,7 +252,7 @@ template <typename T>
 void Kern<T>::solve_bwd_dense(const DevSym& ds, const T* arena, const int* piv, T* W, T* xp,
                               const int* flist, int nfr, int nrhs, int transpose, cudaStream_t s) {
   if (nfr <= 0) return;
-  k_solve_bwd_dense<T><<<nfr, 256, 0, s>>>(ds.fronts, arena, piv, W, xp, flist, ds.n, nrhs, transpose);
+  k_solve_bwd_dense<T><<<dim3(nfr, std::min(nrhs, 64)), 256, 0, s>>>(ds.fronts, arena, piv, W, xp, flist, ds.n, nrhs, transpose);
   count_launch();
 }
 

@@ -17,6 +17,7 @@
 #include "../../include/hssmf.h"
 #include "analyze.h"
 #include "hss.h"
+#include "hss_kernels.h"
 #include "kernels.h"
 #include "solver_ctx.h"
 
@@ -302,6 +303,7 @@ hssmf_status hssmf_ctx::factor_impl() {
   for (size_t h = 0; h < plan.size(); ++h) {
     const LevelPlan& L = plan[h];
     // dense fronts: assembly, then the blocked partial LU
+    prof.mark(PH_DENSE, stream);
     Kern<T>::assemble(ds, ar, d_values, d_tiles + L.asm_off, L.asm_n, stream);
     for (const StepPlan& sp : L.steps) {
       Kern<T>::panel_lu(ds, ar, d_piv, d_flist + L.dense_off, L.ndense, sp.k0, NB, d_status, stream);
@@ -350,6 +352,7 @@ hssmf_status hssmf_ctx::apply_impl(const double* b, double* x, int nrhs, int tra
   T* bp = W + wtot;
   T* xp = bp + (long long)n * nrhs;
   const T* ar = static_cast<const T*>(d_arena);
+  prof.mark(PH_SOLVE, stream);
   Kern<T>::permute_in(b, n, bp, d_perm, n, nrhs, stream);
   for (size_t h = 0; h < plan.size(); ++h) {  // forward, bottom-up
     const LevelPlan& L = plan[h];
@@ -370,6 +373,7 @@ hssmf_status hssmf_ctx::apply_impl(const double* b, double* x, int nrhs, int tra
     }
   }
   Kern<T>::permute_out(xp, x, n, d_perm, n, nrhs, stream);
+  prof.mark(PH_OUTER, stream);
   return HSSMF_OK;
 }
 
@@ -656,7 +660,9 @@ hssmf_status hssmf_factor(hssmf_ctx* c, const double* values) {
   if ((st = c->ensure_device())) return st;
   const size_t vb = sizeof(double) * c->sym.nnz;
   long long l0 = g_launches.load();
+  c->prof.reset();
   cudaEventRecord(c->ev0, c->stream);
+  c->prof.mark(PH_DENSE, c->stream);
   if (is_device_ptr(values)) {
     if ((st = c->cuda_check(cudaMemcpyAsync(c->d_values, values, vb, cudaMemcpyDeviceToDevice, c->stream), "values"))) return st;
   } else {
@@ -669,6 +675,7 @@ hssmf_status hssmf_factor(hssmf_ctx* c, const double* values) {
   cudaEventRecord(c->ev1, c->stream);
   if ((st = c->cuda_check(cudaGetLastError(), "factor launch"))) return st;
   if ((st = c->read_status())) return st;
+  c->prof.finish(c->stream);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   c->stats.t_factor_ms = ms;
@@ -706,6 +713,7 @@ static hssmf_status solve_common(hssmf_ctx* c, const double* B, double* X, int n
   double* Xd = xdev ? X : c->d_io + (size_t)n * nrhs;
   long long ldxd = xdev ? ldb : n;
   cudaMemsetAsync(c->d_status, 0, sizeof(unsigned) * 4, c->stream);
+  c->prof.mark(PH_OUTER, c->stream);
   st = c->outer_solve(Bd, ldbd, Xd, ldxd, nrhs, transpose);
   hssmf_status st2 = HSSMF_OK;
   if (!xdev && (st == HSSMF_OK || st == HSSMF_ERR_NOCONV))
@@ -713,6 +721,7 @@ static hssmf_status solve_common(hssmf_ctx* c, const double* B, double* X, int n
                                           nrhs, cudaMemcpyDeviceToHost, c->stream), "X download");
   cudaEventRecord(c->ev1, c->stream);
   hssmf_status st3 = c->read_status();
+  c->prof.finish(c->stream);
   if (st) return st;
   if (st2) return st2;
   if (st3) return st3;
@@ -739,6 +748,9 @@ hssmf_status hssmf_get_stats(const hssmf_ctx* c, hssmf_stats* out) {
   out->max_rank = c->hss_max_rank;
   out->max_d = c->hss_max_d;
   out->adaptive_rounds = c->hss_rounds;
+  out->id_launches = c->id_launches;
+  out->id_bytes = c->id_bytes;
+  out->id_flops = c->id_flops;
   return HSSMF_OK;
 }
 
@@ -763,6 +775,83 @@ hssmf_status hssmf_get_upd(const hssmf_ctx* c, int f, int* upd) {
   return HSSMF_OK;
 }
 
+}  // extern "C"
+
+template <typename T>
+static hssmf_status batched_id_impl(int njobs, const void* Y, const long long* y_off, const int* m,
+                                    const int* d, double eps, int* rank_host, int* piv,
+                                    const long long* p_off, void* X, const long long* x_off,
+                                    int use_cluster, cudaStream_t s) {
+  std::vector<IdJob> jobs(njobs);
+  long long wtot = 0;
+  int max_m = 1, max_d = 1;
+  for (int j = 0; j < njobs; ++j) {
+    if (m[j] < 1 || d[j] < 1) return HSSMF_ERR_ARG;
+    wtot += (long long)m[j] * d[j];
+    max_m = std::max(max_m, m[j]);
+    max_d = std::max(max_d, d[j]);
+  }
+  char* buf = nullptr;
+  const size_t bytes = sizeof(T) * wtot + sizeof(int) * njobs + sizeof(double) * (size_t)njobs * max_m +
+                       sizeof(int) * (size_t)njobs * max_m + 1024;
+  if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return HSSMF_ERR_OOM;
+  }
+  T* W = (T*)buf;
+  int* rk = (int*)(W + wtot);
+  double* rdiag = (double*)(((uintptr_t)(rk + njobs) + 255) & ~(uintptr_t)255);
+  int* order = (int*)(rdiag + (size_t)njobs * max_m);
+  long long w = 0;
+  for (int j = 0; j < njobs; ++j) {
+    jobs[j] = IdJob{(const T*)Y + y_off[j], W + w, piv + p_off[j], (T*)X + x_off[j], rk + j, d[j], m[j]};
+    w += (long long)m[j] * d[j];
+  }
+  IdJob* dj = nullptr;
+  hssmf_status st = HSSMF_OK;
+  if (cudaMalloc(&dj, sizeof(IdJob) * njobs) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(buf);
+    return HSSMF_ERR_OOM;
+  }
+  cudaMemcpyAsync(dj, jobs.data(), sizeof(IdJob) * njobs, cudaMemcpyHostToDevice, s);
+  int r = use_cluster ? HssKern<T>::batched_id_cluster(dj, njobs, max_m, max_d, eps, rdiag, order, s,
+                                                       use_cluster >= 16 ? 16 : 8)
+                      : HssKern<T>::batched_id(dj, njobs, max_m, max_d, eps, s);
+  if (r < 0) st = HSSMF_ERR_ARG;
+  if (!st) cudaMemcpyAsync(rank_host, rk, sizeof(int) * njobs, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) st = HSSMF_ERR_CUDA;
+  cudaFree(dj);
+  cudaFree(buf);
+  return st;
+}
+
+extern "C" {
+
+hssmf_status hssmf_batched_id(int prec, int njobs, const void* Y, const long long* y_off, const int* m,
+                              const int* d, double eps, int* rank_host, int* piv, const long long* p_off,
+                              void* X, const long long* x_off, int use_cluster, void* cuda_stream) {
+  if (njobs < 1 || !Y || !y_off || !m || !d || !rank_host || !piv || !p_off || !X || !x_off) return HSSMF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (prec == HSSMF_PREC_FP64)
+    return batched_id_impl<double>(njobs, Y, y_off, m, d, eps, rank_host, piv, p_off, X, x_off, use_cluster, s);
+  if (prec == HSSMF_PREC_FP32)
+    return batched_id_impl<float>(njobs, Y, y_off, m, d, eps, rank_host, piv, p_off, X, x_off, use_cluster, s);
+  return HSSMF_ERR_ARG;
+}
+
+hssmf_status hssmf_get_phase_times(const hssmf_ctx* c, double* ms, int n) {
+  if (!c || !ms || n < 0) return HSSMF_ERR_ARG;
+  for (int i = 0; i < n && i < PH_COUNT; ++i) ms[i] = c->prof.ms[i];
+  return HSSMF_OK;
+}
+
+hssmf_status hssmf_set_profiling(hssmf_ctx* c, int on) {
+  if (!c) return HSSMF_ERR_ARG;
+  c->prof.on = on != 0;
+  return HSSMF_OK;
+}
+
 const char* hssmf_last_error(const hssmf_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 void hssmf_destroy(hssmf_ctx* c) {
@@ -770,6 +859,7 @@ void hssmf_destroy(hssmf_ctx* c) {
   if (c->on_device) cudaStreamSynchronize(c->stream);
   c->free_all();
   hss_release(*c);
+  c->prof.release();
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;

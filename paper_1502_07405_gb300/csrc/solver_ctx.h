@@ -26,6 +26,64 @@ struct LevelPlan {
 
 struct HssState;  // HSS-front factor data (hss.cu)
 
+enum Phase {
+  PH_DENSE = 0, PH_SAMPLE, PH_EXTRACT, PH_PREID, PH_ID, PH_POSTID, PH_ULV, PH_SCHUR, PH_SOLVE,
+  PH_OUTER, PH_COUNT
+};
+
+// Phase timeline: an event is recorded at every phase change; the time
+// between two consecutive events is charged to the earlier phase.  Events
+// are resolved after stream synchronizations, so profiling adds no syncs.
+struct PhaseProf {
+  bool on = false;
+  double ms[PH_COUNT] = {0};
+  std::vector<std::pair<int, cudaEvent_t>> pending;
+  std::vector<cudaEvent_t> spare;
+  int cur = -2;
+  void mark(int p, cudaStream_t s) {
+    if (!on || p == cur) return;
+    cudaEvent_t e;
+    if (spare.empty()) {
+      if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+    } else {
+      e = spare.back();
+      spare.pop_back();
+    }
+    cudaEventRecord(e, s);
+    pending.push_back({p, e});
+    cur = p;
+  }
+  void resolve() {  // call only after the stream has been synchronized
+    if (pending.size() < 2) return;
+    for (size_t i = 0; i + 1 < pending.size(); ++i) {
+      float t = 0.f;
+      if (pending[i].first >= 0 && cudaEventElapsedTime(&t, pending[i].second, pending[i + 1].second) == cudaSuccess)
+        ms[pending[i].first] += t;
+      else
+        cudaGetLastError();
+      spare.push_back(pending[i].second);
+    }
+    pending.erase(pending.begin(), pending.end() - 1);
+  }
+  void finish(cudaStream_t s) {  // after a synchronization: close and drop the open interval
+    mark(-1, s);
+    cudaStreamSynchronize(s);
+    resolve();
+    for (auto& p : pending) spare.push_back(p.second);
+    pending.clear();
+    cur = -2;
+  }
+  void reset() {
+    for (double& v : ms) v = 0.0;
+  }
+  void release() {
+    for (auto& p : pending) cudaEventDestroy(p.second);
+    for (auto e : spare) cudaEventDestroy(e);
+    pending.clear();
+    spare.clear();
+  }
+};
+
 }  // namespace hssmf
 
 struct hssmf_ctx {
@@ -77,11 +135,14 @@ struct hssmf_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double dense_flops = 0.0, hss_flops = 0.0, factor_bytes_dense = 0.0, hss_bytes = 0.0;
   int hss_max_rank = 0, hss_max_d = 0, hss_rounds = 0, hss_first_level = -1;
+  int id_launches = 0;
+  double id_bytes = 0.0, id_flops = 0.0;
   int factor_launches = 0;
   int last_iters = 0;
   double last_relres = 0.0;
   // HSS-front state
   hssmf::HssState* hss = nullptr;
+  hssmf::PhaseProf prof;
 
   hssmf_status fail(hssmf_status st, const std::string& msg);
   hssmf_status cuda_check(cudaError_t e, const char* what);

@@ -1,0 +1,85 @@
+"""GPU interpolative decompositions (single-CTA and thread-block-cluster
+kernels) against the oracle's column-pivoted QR ID."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import hss
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _run_ids(Ys, eps, prec, cluster):
+    import paper_1502_07405_gb300 as P
+    dt = torch.float64 if prec == 0 else torch.float32
+    m = np.array([Y.shape[1] for Y in Ys], dtype=np.int32)
+    d = np.array([Y.shape[0] for Y in Ys], dtype=np.int32)
+    y_off = np.cumsum([0] + [Y.size for Y in Ys])[:-1].astype(np.int64)
+    p_off = np.cumsum([0] + list(m))[:-1].astype(np.int64)
+    x_off = np.cumsum([0] + [mm * mm // 4 + 1 for mm in m])[:-1].astype(np.int64)
+    Yd = torch.tensor(np.concatenate([Y.T.reshape(-1) for Y in Ys]), dtype=dt, device="cuda")
+    piv = torch.zeros(int(m.sum()), dtype=torch.int32, device="cuda")
+    X = torch.zeros(int(sum(mm * mm // 4 + 1 for mm in m)), dtype=dt, device="cuda")
+    ranks = np.zeros(len(Ys), dtype=np.int32)
+    lp = lambda a: a.ctypes.data_as(C.c_void_p)
+    P.lib.hssmf_batched_id.restype = C.c_int
+    st = P.lib.hssmf_batched_id(prec, len(Ys), C.c_void_p(Yd.data_ptr()), lp(y_off), lp(m), lp(d),
+                                C.c_double(eps), lp(ranks), C.c_void_p(piv.data_ptr()), lp(p_off),
+                                C.c_void_p(X.data_ptr()), lp(x_off), int(cluster), None)
+    assert st == 0
+    piv = piv.cpu().numpy()
+    X = X.cpu().double().numpy()
+    out = []
+    for j in range(len(Ys)):
+        k, mm = int(ranks[j]), int(m[j])
+        pj = piv[p_off[j]:p_off[j] + mm]
+        Xj = X[x_off[j]:x_off[j] + k * (mm - k)].reshape(mm - k, k).T if k else np.zeros((0, mm))
+        out.append((k, pj, Xj))
+    return out
+
+
+def _decaying(d, m, rank_scale, seed):
+    rng = np.random.default_rng(seed)
+    r = min(d, m)
+    Q1, _ = np.linalg.qr(rng.standard_normal((d, r)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((m, r)))
+    s = 10.0 ** (-np.arange(r) / rank_scale)
+    return (Q1 * s) @ Q2.T
+
+
+@pytest.mark.parametrize("cluster", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_id_matches_oracle(cluster, prec):
+    shapes = [(128, 128), (192, 128), (256, 300), (96, 700), (300, 64)]
+    Ys = [_decaying(d_, m_, 12.0, i) for i, (d_, m_) in enumerate(shapes)]
+    eps = 1e-6 if prec == 0 else 1e-4
+    res = _run_ids(Ys, eps, prec, cluster)
+    for Y, (k, piv, Xg) in zip(Ys, res):
+        ko, pivo, Ro = hss.cpqr_rank(Y, eps)
+        assert abs(k - ko) <= 1
+        kk = min(k, ko)
+        assert np.array_equal(piv[:kk], pivo[:kk])  # skeleton columns in pivot order
+        assert sorted(piv.tolist()) == list(range(Y.shape[1]))
+        # interpolation error of the GPU ID at its own rank is at the eps level
+        U = np.zeros((Y.shape[1], k))
+        U[piv[:k], :] = np.eye(k)
+        U[piv[k:], :] = Xg.T
+        err = np.linalg.norm(Y[:, piv[:k]] @ U.T - Y) / np.linalg.norm(Y)
+        assert err <= 50 * eps
+
+
+@pytest.mark.parametrize("cluster", [0, 1])
+def test_batched_id_exact_low_rank_and_zero(cluster):
+    rng = np.random.default_rng(5)
+    Y1 = rng.standard_normal((200, 9)) @ rng.standard_normal((9, 500))
+    Y2 = np.zeros((64, 80))
+    res = _run_ids([Y1, Y2], 1e-12, 0, cluster)
+    k, piv, Xg = res[0]
+    assert k == 9
+    U = np.zeros((500, 9))
+    U[piv[:9], :] = np.eye(9)
+    U[piv[9:], :] = Xg.T
+    assert np.linalg.norm(Y1[:, piv[:9]] @ U.T - Y1) <= 1e-12 * np.linalg.norm(Y1)
+    assert res[1][0] == 0
