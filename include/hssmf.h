@@ -178,6 +178,31 @@ hssmf_status hssmf_batched_id(int prec, int njobs, const void* Y, const long lon
                               const long long* p_off, void* X, const long long* x_off,
                               int use_cluster, void* cuda_stream);
 
+/* Allocation-free form of hssmf_batched_id for callers that must not
+ * allocate device memory while they run: cudaMalloc/cudaFree synchronize
+ * the whole device, an application's memory pool may already own the
+ * device memory, or a policy may forbid allocation after start-up.  The
+ * paper has no counterpart; this is a property of the library.
+ * Same arguments, results and one-CTA kernel as hssmf_batched_id with
+ * use_cluster = 0, but every scratch word (job descriptors, ranks and the
+ * d_j x m_j work copies) lives in one fixed 32 MiB array compiled into the
+ * library, held on each GPU that loads it until the process exits.  No
+ * device memory is allocated or freed.
+ *   - HSSMF_ERR_ARG if the batch needs more than 32 MiB of scratch
+ *     (256-byte-rounded job and rank arrays plus sum(d_j * m_j) elements of
+ *     T), or if a node is too large for the kernel's shared memory.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - Every call shares the array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and must be serialized by the
+ *     caller.  Nothing in the array needs clearing between calls.
+ *   - Synchronizes the stream. */
+hssmf_status hssmf_batched_id_noalloc(int prec, int njobs, const void* Y, const long long* y_off,
+                                      const int* m, const int* d, double eps, int* rank_host,
+                                      int* piv, const long long* p_off, void* X,
+                                      const long long* x_off, void* cuda_stream);
+
 const char* hssmf_last_error(const hssmf_ctx* ctx);
 void hssmf_destroy(hssmf_ctx* ctx);
 
