@@ -924,17 +924,80 @@ hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     }
     X.flush_copy();
     X.flush_gemm();
+    // LQ of the top m - k rows, blocked: panel reflectors on one CTA per
+    // node, block-reflector updates of the rows below and of V_t as GEMMs
+    constexpr int NBQ = 32;
     std::vector<LqJob> lq;
+    std::vector<T*> W1, W2, Z1, Z2;
+    int max_nk = 0;
     for (size_t i = 0; i < items.size(); ++i) {
       FrontRt& F = *items[i].first;
       const int t = items[i].second;
       if (t == F.k) continue;
       NodeRt& N = F.nd[t];
       N.tau = X.A(H.fac, std::max(N.m - N.kr, 1));
-      if (N.m - N.kr > 0) lq.push_back(LqJob{N.Dt, N.Vt, N.tau, N.m, N.kr, N.kc, 0});
+      if (N.m - N.kr <= 0) continue;
+      T* Vb = X.A(H.lvl, (long long)NBQ * N.m);
+      T* Tb = X.A(H.lvl, NBQ * NBQ);
+      lq.push_back(LqJob{N.Dt, N.Vt, N.tau, Vb, Tb, N.m, N.kr, N.kc, 0});
+      W1.push_back(X.A(H.lvl, (long long)N.m * NBQ));
+      W2.push_back(X.A(H.lvl, (long long)N.m * NBQ));
+      Z1.push_back(X.A(H.lvl, (long long)NBQ * std::max(N.kc, 1)));
+      Z2.push_back(X.A(H.lvl, (long long)NBQ * std::max(N.kc, 1)));
+      max_nk = std::max(max_nk, N.m - N.kr);
     }
-    X.launch(lq, [&](const LqJob* d, int n) { HssKern<T>::lq(d, n, X.s); });
-    X.launch(lu, [&](const LuJob* d, int n) { HssKern<T>::lu(d, n, c.d_status, X.s); });
+    if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during the ULV factorization");
+    for (int j0 = 0; j0 < max_nk; j0 += NBQ) {
+      std::vector<LqJob> cur = lq;  // staged again each step: the job ring may wrap
+      X.launch(cur, [&](const LqJob* d, int n) { HssKern<T>::lq_panel(d, n, j0, NBQ, X.s); });
+      for (size_t q = 0; q < lq.size(); ++q) {
+        const LqJob& J = lq[q];
+        const int nk = J.m - J.k;
+        if (j0 >= nk) continue;
+        const int j1 = std::min(j0 + NBQ, nk), w = j1 - j0, n = J.m - j0, rows = J.m - j1;
+        T* D = (T*)J.Dt;
+        X.gemm(D + j1 + (long long)j0 * J.m, J.m, 0, J.Vb, NBQ, 1, W1[q], J.m, rows, w, n, 1.0, 0.0);
+        X.gemm(J.Vb, NBQ, 0, (T*)J.V + j0, J.m, 0, Z1[q], NBQ, w, J.kc, n, 1.0, 0.0);
+      }
+      X.flush_gemm();
+      for (size_t q = 0; q < lq.size(); ++q) {
+        const LqJob& J = lq[q];
+        const int nk = J.m - J.k;
+        if (j0 >= nk) continue;
+        const int j1 = std::min(j0 + NBQ, nk), w = j1 - j0, rows = J.m - j1;
+        X.gemm(W1[q], J.m, 0, J.Tb, NBQ, 0, W2[q], J.m, rows, w, w, 1.0, 0.0);
+        X.gemm(J.Tb, NBQ, 1, Z1[q], NBQ, 0, Z2[q], NBQ, w, J.kc, w, 1.0, 0.0);
+      }
+      X.flush_gemm();
+      for (size_t q = 0; q < lq.size(); ++q) {
+        const LqJob& J = lq[q];
+        const int nk = J.m - J.k;
+        if (j0 >= nk) continue;
+        const int j1 = std::min(j0 + NBQ, nk), w = j1 - j0, n = J.m - j0, rows = J.m - j1;
+        T* D = (T*)J.Dt;
+        X.gemm(W2[q], J.m, 0, J.Vb, NBQ, 0, D + j1 + (long long)j0 * J.m, J.m, rows, n, w, -1.0, 1.0);
+        X.gemm(J.Vb, NBQ, 1, Z2[q], NBQ, 0, (T*)J.V + j0, J.m, n, J.kc, w, -1.0, 1.0);
+      }
+      X.flush_gemm();
+    }
+    // root LU of the F11 tree, blocked: panel + row block of U on one CTA
+    // per root, trailing update as GEMMs
+    int max_m = 0;
+    for (const LuJob& J : lu) max_m = std::max(max_m, J.m);
+    for (int k0 = 0; k0 < max_m; k0 += NBQ) {
+      std::vector<LuJob> cur = lu;
+      X.launch(cur, [&](const LuJob* d, int n) { HssKern<T>::lu_panel(d, n, k0, NBQ, c.d_status, X.s); });
+      cur = lu;
+      X.launch(cur, [&](const LuJob* d, int n) { HssKern<T>::lu_trsm(d, n, k0, NBQ, max_m, X.s); });
+      for (const LuJob& J : lu) {
+        const int k1 = k0 + NBQ;
+        if (J.m <= k1) continue;
+        T* A = (T*)J.A;
+        X.gemm(A + k1 + (long long)k0 * J.m, J.m, 0, A + k0 + (long long)k1 * J.m, J.m, 0,
+               A + k1 + (long long)k1 * J.m, J.m, J.m - k1, J.m - k1, NBQ, -1.0, 1.0);
+      }
+      X.flush_gemm();
+    }
   }
   if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during the ULV factorization");
   c.prof.mark(PH_SCHUR, X.s);

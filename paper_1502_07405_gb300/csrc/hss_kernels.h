@@ -70,6 +70,8 @@ struct LqJob {  // LQ of the top m-k rows of Dt (m x m): Dt <- Dt Q, V <- Q^T V;
   void* Dt;
   void* V;
   void* tau;
+  void* Vb;  // blocked form: panel reflectors (nb x m, ld nb) and their T (nb x nb)
+  void* Tb;
   int m, k, kc, pad;
 };
 
@@ -136,6 +138,15 @@ struct HssKern {
   static void basis(const BasisJob* jobs, int njobs, cudaStream_t s);
   static void lq(const LqJob* jobs, int njobs, cudaStream_t s);
   static void lu(const LuJob* jobs, int njobs, unsigned* status, cudaStream_t s);
+  // Blocked LQ, panel of rows [j0, j0 + nb) of every job with m - k > j0:
+  // reflectors of the panel rows (applied inside the panel), the block
+  // reflector's V (nb x (m - j0), ld nb, explicit ones and zeros) into
+  // Vb + vb_off[j] and its triangular factor T (nb x nb) into Tb + t_off[j].
+  static void lq_panel(const LqJob* jobs, int njobs, int j0, int nb, cudaStream_t s);
+  // Blocked LU: panel columns [k0, k0 + nb) (pivot search over all rows),
+  // then the row block of U right of the panel.
+  static void lu_panel(const LuJob* jobs, int njobs, int k0, int nb, unsigned* status, cudaStream_t s);
+  static void lu_trsm(const LuJob* jobs, int njobs, int k0, int nb, int max_m, cudaStream_t s);
   static void ulv_fwd(const UlvFwdJob* jobs, int njobs, int max_nrhs, cudaStream_t s);
   static void ulv_bwd(const UlvBwdJob* jobs, int njobs, int max_nrhs, cudaStream_t s);
 };

@@ -91,6 +91,86 @@ __device__ __forceinline__ double warp_reflect(T* wj, const double* v, int i, in
   return warp_sum(nn);
 }
 
+// One warp applies H = I - tau v v^T (v[i] = 1) to nc <= 4 columns at once:
+// the loads and the shuffle reductions of the columns are independent and
+// interleave, which hides the latency of each.  nn[c] receives the squared
+// norm of rows i+1..d-1 of column c after the update (all lanes).
+template <typename T>
+__device__ __forceinline__ void warp_reflect4(T* w0, T* w1, T* w2, T* w3, int nc, const double* v,
+                                              int i, int d, T tau, int lane, double* nn) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  for (int r = i + lane; r < d; r += 32) {
+    const T vr = T(v[r]);
+    s0 += vr * w0[r];
+    s1 += vr * w1[r];
+    s2 += vr * w2[r];
+    s3 += vr * w3[r];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+  }
+  const T f0 = tau * s0, f1 = tau * s1, f2 = tau * s2, f3 = tau * s3;
+  double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;
+  for (int r = i + lane; r < d; r += 32) {
+    const T vr = T(v[r]);
+    const T x0 = w0[r] - f0 * vr, x1 = w1[r] - f1 * vr, x2 = w2[r] - f2 * vr, x3 = w3[r] - f3 * vr;
+    w0[r] = x0;
+    if (nc > 1) w1[r] = x1;
+    if (nc > 2) w2[r] = x2;
+    if (nc > 3) w3[r] = x3;
+    if (r > i) {
+      n0 += (double)x0 * (double)x0;
+      n1 += (double)x1 * (double)x1;
+      n2 += (double)x2 * (double)x2;
+      n3 += (double)x3 * (double)x3;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+    n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+    n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    n3 += __shfl_xor_sync(0xffffffffu, n3, o);
+  }
+  nn[0] = n0;
+  nn[1] = n1;
+  nn[2] = n2;
+  nn[3] = n3;
+}
+
+// One warp solves R1 x = b by column-oriented back substitution for nc <= 4
+// right-hand sides b0..b3 (rows 0..k-1, overwritten by x): x_c = b_c /
+// R1(c, c), then b[0:c] -= R1(0:c, c) x_c, reading column c of R1
+// (rcol(c), rows 0..c-1) once for all right-hand sides; diag(c) = R1(c, c).
+template <typename T, typename ColF, typename DiagF>
+__device__ __forceinline__ void warp_backsub4(T* b0, T* b1, T* b2, T* b3, int nc, int k, ColF rcol,
+                                              DiagF diag, int lane) {
+  for (int c = k - 1; c >= 0; --c) {
+    const T dc = diag(c);
+    const T x0 = b0[c] / dc, x1 = b1[c] / dc, x2 = b2[c] / dc, x3 = b3[c] / dc;
+    __syncwarp();
+    if (lane == 0) {
+      b0[c] = x0;
+      if (nc > 1) b1[c] = x1;
+      if (nc > 2) b2[c] = x2;
+      if (nc > 3) b3[c] = x3;
+    }
+    const T* rc = rcol(c);
+    for (int r = lane; r < c; r += 32) {
+      const T a = rc[r];
+      b0[r] -= a * x0;
+      if (nc > 1) b1[r] -= a * x1;
+      if (nc > 2) b2[r] -= a * x2;
+      if (nc > 3) b3[r] -= a * x3;
+    }
+    __syncwarp();
+  }
+}
+
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, Weyl key schedule.
 __device__ __forceinline__ void philox4x32_10(unsigned c[4], unsigned k0, unsigned k1) {
   const unsigned M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
@@ -287,10 +367,14 @@ void HssKern<T>::extract(const DevSym& ds, const double* values, const T* arena,
 // i with |R_{i+1,i+1}| <= eps |R_11|.  Then X = R1^-1 R2 by back
 // substitution, one warp per column.
 // ---------------------------------------------------------------------------
+// Threads per CTA (measured on GB300): 512 with two CTAs per SM for the
+// one-CTA kernel (many small nodes), 1024 for the cluster kernel (few large
+// nodes, whose per-step work is latency-bound and splits over more warps).
 constexpr int ID_THREADS = 512;
+constexpr int IDC_THREADS = 1024;
 
 template <typename T>
-__global__ void __launch_bounds__(ID_THREADS) k_cpqr_id(const IdJob* __restrict__ jobs, double eps) {
+__global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr_id(const IdJob* __restrict__ jobs, double eps) {
   const IdJob jb = jobs[blockIdx.x];
   const int d = jb.d, m = jb.m;
   const long long ld = d;
@@ -373,25 +457,33 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr_id(const IdJob* __restrict_
     for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) vsh[r] = (double)(W[r + i * ld] * scl);
     if (threadIdx.x == 0) vsh[i] = 1.0;
     __syncthreads();
-    for (int j = i + 1 + wid; j < m; j += nw) {
-      const double nn = warp_reflect<T>(W + j * ld, vsh, i, d, tau, lane);
-      if (lane == 0) cn[j] = nn;
+    for (int j0 = i + 1 + 4 * wid; j0 < m; j0 += 4 * nw) {  // 4 columns per warp
+      const int nc = min(4, m - j0);
+      T* w0 = W + j0 * ld;
+      T* w1 = nc > 1 ? w0 + ld : w0;
+      T* w2 = nc > 2 ? w0 + 2 * ld : w0;
+      T* w3 = nc > 3 ? w0 + 3 * ld : w0;
+      double nn[4];
+      warp_reflect4<T>(w0, w1, w2, w3, nc, vsh, i, d, tau, lane, nn);
+      if (lane < nc) cn[j0 + lane] = lane == 0 ? nn[0] : lane == 1 ? nn[1] : lane == 2 ? nn[2] : nn[3];
     }
     __syncthreads();
     if (threadIdx.x == 0) W[i + i * ld] = beta;
     __syncthreads();
   }
-  // X = R1^-1 R2 (k x (m - k), ld k)
+  // X = R1^-1 R2 (k x (m - k), ld k): back substitution in place on rows
+  // 0..k-1 of the non-skeleton columns, 4 per warp, then copied out
   T* X = (T*)jb.X;
-  for (int j = k + wid; j < m; j += nw) {
-    T* x = X + (long long)(j - k) * k;
-    for (int r = k - 1; r >= 0; --r) {
-      T s = T(0);
-      for (int c = r + 1 + lane; c < k; c += 32) s += W[r + c * ld] * x[c];
-      s = wsum<T>(s);
-      if (lane == 0) x[r] = (W[r + j * ld] - s) / W[r + r * ld];
-      __syncwarp();
-    }
+  for (int j0 = k + 4 * wid; j0 < m; j0 += 4 * nw) {
+    const int nc = min(4, m - j0);
+    T* b0 = W + j0 * ld;
+    T* b1 = nc > 1 ? b0 + ld : b0;
+    T* b2 = nc > 2 ? b0 + 2 * ld : b0;
+    T* b3 = nc > 3 ? b0 + 3 * ld : b0;
+    warp_backsub4<T>(b0, b1, b2, b3, nc, k, [&](int c) { return (const T*)(W + c * ld); },
+                     [&](int c) { return W[c + c * ld]; }, lane);
+    for (int q = 0; q < nc; ++q)
+      for (int r = lane; r < k; r += 32) X[r + (long long)(j0 - k + q) * k] = W[r + (j0 + q) * ld];
   }
   for (int j = threadIdx.x; j < m; j += blockDim.x) jb.piv[j] = perm[j];
   if (threadIdx.x == 0) *jb.rank = k;
@@ -428,7 +520,7 @@ int HssKern<T>::batched_id(const IdJob* jobs, int njobs, int max_m, int max_d, d
 // order of the non-skeleton columns).
 // ---------------------------------------------------------------------------
 template <typename T, int ID_CL>
-__global__ void __launch_bounds__(ID_THREADS) k_cpqr_id_cluster(const IdJob* __restrict__ jobs,
+__global__ void __launch_bounds__(IDC_THREADS, 1) k_cpqr_id_cluster(const IdJob* __restrict__ jobs,
                                                                 double eps, double* rdiag_all,
                                                                 int* order_all, int max_m, int max_k) {
   namespace cg = cooperative_groups;
@@ -447,8 +539,8 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr_id_cluster(const IdJob* __r
   double* cn = smem;                               // mo norms^2 (negative: pivoted)
   double* v = cn + mo;                             // d: Householder vector of the step
   unsigned char* skel = (unsigned char*)(v + d);   // m flags, replicated in every CTA
-  __shared__ double s_bv[ID_THREADS / 32];
-  __shared__ int s_bi[ID_THREADS / 32];
+  __shared__ double s_bv[IDC_THREADS / 32];
+  __shared__ int s_bi[IDC_THREADS / 32];
   __shared__ double s_cand_v;
   __shared__ int s_cand_i;
   __shared__ double s_best;
@@ -538,11 +630,22 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr_id_cluster(const IdJob* __r
     if (p % ID_CL == rank && threadIdx.x == 0) cn[p / ID_CL] = -1.0;
     __syncthreads();
     // apply to the owned unpivoted columns; recompute their norms
-    for (int l = wid; l < mo; l += nw) {
-      const int j = rank + ID_CL * l;
-      if (j == p || skel[j]) continue;
-      const double nn = warp_reflect<T>(W + j * ld, v, i, d, tau, lane);
-      if (lane == 0) cn[l] = nn;
+    for (int g = wid; 4 * g < mo; g += nw) {  // up to 4 owned, unpivoted columns per warp
+      int ls[4];
+      int nc = 0;
+      for (int q = 0; q < 4; ++q) {
+        const int l = 4 * g + q;
+        if (l < mo && !skel[rank + ID_CL * l]) ls[nc++] = l;
+      }
+      if (nc == 0) continue;
+      for (int q = nc; q < 4; ++q) ls[q] = ls[0];
+      T* w0 = W + (rank + ID_CL * ls[0]) * ld;
+      T* w1 = W + (rank + ID_CL * ls[1]) * ld;
+      T* w2 = W + (rank + ID_CL * ls[2]) * ld;
+      T* w3 = W + (rank + ID_CL * ls[3]) * ld;
+      double nn[4];
+      warp_reflect4<T>(w0, w1, w2, w3, nc, v, i, d, tau, lane, nn);
+      if (lane < nc) cn[ls[lane]] = lane == 0 ? nn[0] : lane == 1 ? nn[1] : lane == 2 ? nn[2] : nn[3];
     }
     cluster.sync();  // every column updated before the next proposals
   }
@@ -553,21 +656,29 @@ __global__ void __launch_bounds__(ID_THREADS) k_cpqr_id_cluster(const IdJob* __r
   // R1(r, r) = rdiag[r] (written by CTA 0 before the last cluster barrier)
   const double* rd = rdiag;
   T* X = (T*)jb.X;
-  for (int l = wid; l < mo; l += nw) {
-    const int j = rank + ID_CL * l;
-    if (skel[j]) continue;
-    int pos = 0;  // number of non-skeleton columns before j
-    for (int c = lane; c < j; c += 32) pos += skel[c] ? 0 : 1;
-    for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
-    T* x = X + (long long)pos * k;
-    for (int r = k - 1; r >= 0; --r) {
-      T s = T(0);
-      for (int c = r + 1 + lane; c < k; c += 32) s += W[r + (long long)order[c] * ld] * x[c];
-      s = wsum<T>(s);
-      if (lane == 0) x[r] = (W[r + j * ld] - s) / T(rd[r]);
-      __syncwarp();
+  for (int g = wid; 4 * g < mo; g += nw) {  // up to 4 owned non-skeleton columns per warp
+    int ls[4];
+    int nc = 0;
+    for (int q = 0; q < 4; ++q) {
+      const int l = 4 * g + q;
+      if (l < mo && !skel[rank + ID_CL * l]) ls[nc++] = l;
     }
-    if (lane == 0) jb.piv[k + pos] = j;
+    if (nc == 0) continue;
+    for (int q = nc; q < 4; ++q) ls[q] = ls[0];
+    T* b0 = W + (rank + ID_CL * ls[0]) * ld;
+    T* b1 = W + (rank + ID_CL * ls[1]) * ld;
+    T* b2 = W + (rank + ID_CL * ls[2]) * ld;
+    T* b3 = W + (rank + ID_CL * ls[3]) * ld;
+    warp_backsub4<T>(b0, b1, b2, b3, nc, k, [&](int c) { return (const T*)(W + (long long)order[c] * ld); },
+                     [&](int c) { return T(rd[c]); }, lane);
+    for (int q = 0; q < nc; ++q) {
+      const int j = rank + ID_CL * ls[q];
+      int pos = 0;  // number of non-skeleton columns before j
+      for (int c = lane; c < j; c += 32) pos += skel[c] ? 0 : 1;
+      for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+      for (int r = lane; r < k; r += 32) X[r + (long long)pos * k] = W[r + j * ld];
+      if (lane == 0) jb.piv[k + pos] = j;
+    }
   }
   if (rank == 0) {
     for (int i = threadIdx.x; i < k; i += blockDim.x) jb.piv[i] = order[i];
@@ -589,7 +700,7 @@ static int launch_id_cluster(const IdJob* jobs, int njobs, int max_m, int max_d,
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * CL, 1, 1);
-  cfg.blockDim = dim3(ID_THREADS, 1, 1);
+  cfg.blockDim = dim3(IDC_THREADS, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
@@ -703,6 +814,215 @@ template <typename T>
 void HssKern<T>::lq(const LqJob* jobs, int njobs, cudaStream_t s) {
   if (njobs <= 0) return;
   k_lq<T><<<njobs, 256, 0, s>>>(jobs);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Blocked LQ, one panel of rows [j0, j1) per job (one CTA per job):
+// Householder reflectors of the panel rows (LAPACK larfg convention, v
+// stored in the zeroed part of its row, tau), applied to the panel rows
+// below; then the block reflector H_j0 ... H_j1-1 = I - V^T T V with V
+// (w x (m - j0), explicit unit diagonal and zeros, ld nb) and the upper
+// triangular T (forward accumulation).  The rows below the panel and V_t
+// are updated afterwards by batched GEMMs.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_lq_panel(const LqJob* __restrict__ jobs, int j0, int nb) {
+  const LqJob jb = jobs[blockIdx.x];
+  const int m = jb.m, nk = jb.m - jb.k;
+  if (j0 >= nk) return;
+  const int j1 = min(j0 + nb, nk), w = j1 - j0, n = m - j0;
+  T* D = (T*)jb.Dt;
+  T* tau = (T*)jb.tau;
+  T* Vb = (T*)jb.Vb;
+  T* Tb = (T*)jb.Tb;
+  __shared__ double sh[33];
+  __shared__ T sT[32][33];
+  __shared__ T sg[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = j0; i < j1; ++i) {
+    double part = 0.0;
+    for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) {
+      double v = (double)D[i + (long long)c * m];
+      part += v * v;
+    }
+    const T alpha = D[i + (long long)i * m];
+    const double xn2 = block_sum_d(part, sh);
+    T t = T(0), beta = alpha, scl = T(0);
+    if (xn2 > 0.0) {
+      double b = sqrt((double)alpha * (double)alpha + xn2);
+      beta = alpha >= T(0) ? T(-b) : T(b);
+      t = (beta - alpha) / beta;
+      scl = T(1) / (alpha - beta);
+    }
+    for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) D[i + (long long)c * m] *= scl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      D[i + (long long)i * m] = beta;
+      tau[i] = t;
+    }
+    if (t != T(0)) {  // panel rows below i: row_r[i:m] -= t (row_r . v) v
+      for (int r = i + 1 + wid; r < j1; r += nw) {
+        T s = T(0);
+        for (int c = i + 1 + lane; c < m; c += 32) s += D[r + (long long)c * m] * D[i + (long long)c * m];
+        s = wsum<T>(s) + D[r + (long long)i * m];
+        const T f = t * s;
+        __syncwarp();
+        if (lane == 0) D[r + (long long)i * m] -= f;
+        for (int c = i + 1 + lane; c < m; c += 32) D[r + (long long)c * m] -= f * D[i + (long long)c * m];
+      }
+    }
+    __syncthreads();
+  }
+  // V of the block reflector (rows beyond w are zero)
+  for (long long e = threadIdx.x; e < (long long)nb * n; e += blockDim.x) {
+    const int q = (int)(e % nb), c = (int)(e / nb);
+    T val = T(0);
+    if (q < w) val = c < q ? T(0) : c == q ? T(1) : D[(j0 + q) + (long long)(j0 + c) * m];
+    Vb[q + (long long)c * nb] = val;
+  }
+  __syncthreads();
+  // Gram entries G(p, q) = V(p, :) . V(q, :) for p < q (warp per pair)
+  for (int pq = wid; pq < w * w; pq += nw) {
+    const int p = pq % w, q = pq / w;
+    if (p >= q) continue;
+    T s = T(0);
+    for (int c = q + lane; c < n; c += 32) s += Vb[p + (long long)c * nb] * Vb[q + (long long)c * nb];
+    s = wsum<T>(s);
+    if (lane == 0) sT[p][q] = s;  // holds G until T(:, q) replaces it below
+  }
+  __syncthreads();
+  // T(q, q) = tau_q; T(0:q, q) = -tau_q T(0:q, 0:q) G(0:q, q)
+  for (int q = 0; q < w; ++q) {
+    if (threadIdx.x < q) sg[threadIdx.x] = sT[threadIdx.x][q];
+    __syncthreads();
+    const T tq = tau[j0 + q];
+    if (threadIdx.x < q) {
+      const int p = threadIdx.x;
+      T s = T(0);
+      for (int r = p; r < q; ++r) s += sT[p][r] * sg[r];
+      sT[p][q] = -tq * s;
+    }
+    if (threadIdx.x == 0) sT[q][q] = tq;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int p = e % nb, q = e / nb;
+    Tb[e] = (p < w && q < w && p <= q) ? sT[p][q] : T(0);
+  }
+}
+
+template <typename T>
+void HssKern<T>::lq_panel(const LqJob* jobs, int njobs, int j0, int nb, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_lq_panel<T><<<njobs, 256, 0, s>>>(jobs, j0, nb);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Blocked LU with partial pivoting over all rows: panel columns [k0, k1)
+// (first maximum wins, full-row swaps), one CTA per job.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_lu_panel(const LuJob* __restrict__ jobs, int k0, int nb,
+                                                  unsigned* status) {
+  const LuJob jb = jobs[blockIdx.x];
+  const int m = jb.m;
+  if (k0 >= m) return;
+  const int k1 = min(k0 + nb, m);
+  T* A = (T*)jb.A;
+  const long long ld = m;
+  __shared__ double s_v[8];
+  __shared__ int s_i[8];
+  __shared__ int s_p;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = k0; j < k1; ++j) {
+    double bv = -1.0;
+    int bi = m;
+    for (int r = j + threadIdx.x; r < m; r += blockDim.x) {
+      double a = fabs((double)A[r + j * ld]);
+      if (a > bv) { bv = a; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_v[wid] = bv; s_i[wid] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = s_v[0];
+      int ix = s_i[0];
+      for (int w2 = 1; w2 < (int)(blockDim.x >> 5); ++w2)
+        if (s_v[w2] > b || (s_v[w2] == b && s_i[w2] < ix)) { b = s_v[w2]; ix = s_i[w2]; }
+      if (!(b > 0.0) || !isfinite(b)) {
+        atomicOr(status, b == 0.0 ? ST_ZERO_PIVOT : ST_NONFINITE);
+        ix = j;
+      }
+      s_p = ix;
+      jb.piv[j] = ix;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j)
+      for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        T t = A[j + c * ld];
+        A[j + c * ld] = A[p + c * ld];
+        A[p + c * ld] = t;
+      }
+    __syncthreads();
+    const T dj = A[j + j * ld];
+    const T inv = dj != T(0) ? T(1) / dj : T(0);
+    for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) {
+      T l = A[r + j * ld] * inv;
+      A[r + j * ld] = l;
+      for (int c = j + 1; c < k1; ++c) A[r + c * ld] -= l * A[j + c * ld];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void HssKern<T>::lu_panel(const LuJob* jobs, int njobs, int k0, int nb, unsigned* status, cudaStream_t s) {
+  if (njobs <= 0) return;
+  k_lu_panel<T><<<njobs, 256, 0, s>>>(jobs, k0, nb, status);
+  count_launch();
+}
+
+// U row block right of the panel: rows [k0, k1), columns [k1, m) <- L_panel^-1 (unit lower, nb <= 32).
+template <typename T>
+__global__ void __launch_bounds__(128) k_lu_trsm(const LuJob* __restrict__ jobs, int k0, int nb) {
+  const LuJob jb = jobs[blockIdx.y];
+  const int m = jb.m;
+  if (k0 >= m) return;
+  const int k1 = min(k0 + nb, m), w = k1 - k0;
+  T* A = (T*)jb.A;
+  const long long ld = m;
+  __shared__ T L[32][33];
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    int i = e & 31, j = e >> 5;
+    L[i][j] = (i < w && j < w) ? A[(k0 + i) + (k0 + j) * ld] : T(0);
+  }
+  __syncthreads();
+  const int c = k1 + blockIdx.x * 128 + threadIdx.x;
+  if (c >= m) return;
+  T x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) x[i] = (i < w) ? A[(k0 + i) + c * ld] : T(0);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+#pragma unroll
+    for (int r = i + 1; r < 32; ++r) x[r] -= L[r][i] * x[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    if (i < w) A[(k0 + i) + c * ld] = x[i];
+}
+
+template <typename T>
+void HssKern<T>::lu_trsm(const LuJob* jobs, int njobs, int k0, int nb, int max_m, cudaStream_t s) {
+  if (njobs <= 0 || max_m <= k0 + nb) return;
+  k_lu_trsm<T><<<dim3((max_m - k0 - nb + 127) / 128, njobs), 128, 0, s>>>(jobs, k0, nb);
   count_launch();
 }
 
