@@ -171,8 +171,10 @@ hssmf_status hssmf_set_profiling(hssmf_ctx* ctx, int on);
  * and the interpolative basis is Pi [I; X^T].  y_off, m, d, p_off, x_off
  * are host arrays.  use_cluster = 0 runs every job on one CTA; 1..8 on a
  * thread-block cluster of 8 CTAs, 16 on a cluster of 16 CTAs (where the
- * device can schedule it, else 8).  Y is not modified.  Synchronizes the
- * stream. */
+ * device can schedule it, else 8), all working on the matrix in L2;
+ * use_cluster = -1 keeps every matrix in the shared memory of a cluster of
+ * 1..16 CTAs sized for the largest job (HSSMF_ERR_ARG if it does not fit).
+ * Y is not modified.  Synchronizes the stream. */
 hssmf_status hssmf_batched_id(int prec, int njobs, const void* Y, const long long* y_off,
                               const int* m, const int* d, double eps, int* rank_host, int* piv,
                               const long long* p_off, void* X, const long long* x_off,

@@ -36,6 +36,7 @@ constexpr size_t ALIGN = 256;
 // clusters for d * m up to ~1M, 16-CTA clusters beyond)
 constexpr long long kClusterIdWork = 64 * 1024;
 constexpr long long kClusterIdWork16 = 1024 * 1024;  // ... and on 16 CTAs from this size
+constexpr long long kTinyIdBytes = 32 * 1024;        // one CTA per job up to this matrix size
 
 struct Pool {  // device bump allocator over large chunks
   std::vector<std::pair<char*, size_t>> chunks;
@@ -540,16 +541,46 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during HSS compression");
       if (!ij.empty()) {
         if ((int)ij.size() > H.rank_cap) return c.fail(HSSMF_ERR_ARG, "too many IDs in one level");
-        // large IDs on thread-block clusters (16 CTAs for the largest), small
-        // ones on one CTA each
-        std::vector<IdJob> tier[3];
-        int tm[3] = {0, 0, 0}, td[3] = {0, 0, 0};
+        // Routing: nodes whose matrix fits in the shared memory of a cluster
+        // of 1..16 CTAs run there (no global traffic per step); tiny nodes
+        // run one per CTA (more CTAs per SM); the rest on clusters working
+        // from L2 (16 CTAs for the largest).
+        std::vector<IdJob> tier[3], smem_tier[5];
+        int tm[3] = {0, 0, 0}, td[3] = {0, 0, 0}, sm_m[5] = {0, 0, 0, 0, 0}, sm_d[5] = {0, 0, 0, 0, 0};
         for (const IdJob& j : ij) {
           const long long w = (long long)j.d * j.m;
+          const int cl = HssKern<T>::id_smem_cluster_size(j.d, j.m);
+          if (w * (long long)sizeof(T) > kTinyIdBytes && cl > 0) {
+            const int ti = cl == 1 ? 0 : cl == 2 ? 1 : cl == 4 ? 2 : cl == 8 ? 3 : 4;
+            smem_tier[ti].push_back(j);
+            sm_m[ti] = std::max(sm_m[ti], j.m);
+            sm_d[ti] = std::max(sm_d[ti], j.d);
+            continue;
+          }
           const int t = (w >= kClusterIdWork16 && j.m > 256) ? 2 : (w >= kClusterIdWork && j.m > 256) ? 1 : 0;
           tier[t].push_back(j);
           tm[t] = std::max(tm[t], j.m);
           td[t] = std::max(td[t], j.d);
+        }
+        for (int ti = 0; ti < 5; ++ti) {
+          if (smem_tier[ti].empty()) continue;
+          const int cl = 1 << ti;
+          const int bk = std::max(std::min(sm_m[ti], sm_d[ti]), 1);
+          double* rdiag = (double*)H.rnd.alloc(sizeof(double) * smem_tier[ti].size() * bk);
+          int* order = (int*)H.rnd.alloc(sizeof(int) * smem_tier[ti].size() * std::max(sm_m[ti], 1));
+          const IdJob* dj = H.ring.put(smem_tier[ti], X.s);
+          if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
+          if (HssKern<T>::batched_id_smem(dj, (int)smem_tier[ti].size(), sm_m[ti], sm_d[ti], eps, rdiag, order,
+                                          cl, X.s) < 0) {
+            for (const IdJob& j : smem_tier[ti]) {  // not schedulable: the L2-resident kernels
+              const int t = j.m > 256 ? 1 : 0;
+              tier[t].push_back(j);
+              tm[t] = std::max(tm[t], j.m);
+              td[t] = std::max(td[t], j.d);
+            }
+          } else {
+            ++c.id_launches;
+          }
         }
         for (int t = 2; t >= 1; --t) {
           if (tier[t].empty()) continue;

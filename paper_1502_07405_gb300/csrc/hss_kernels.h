@@ -135,6 +135,11 @@ struct HssKern {
   // doubles) and order (njobs x max_m ints) are scratch.  Returns -1 if no launch is possible.
   static int batched_id_cluster(const IdJob* jobs, int njobs, int max_m, int max_d, double eps,
                                 double* rdiag, int* order, cudaStream_t s, int cl = 8);
+  // Shared-memory-resident ID on clusters of cl CTAs (1, 2, 4, 8, 16); the
+  // smallest cl whose shared memory holds a d x m node, 0 if none does.
+  static int id_smem_cluster_size(int d, int m);
+  static int batched_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
+                             int* order, int cl, cudaStream_t s);
   static void basis(const BasisJob* jobs, int njobs, cudaStream_t s);
   static void lq(const LqJob* jobs, int njobs, cudaStream_t s);
   static void lu(const LuJob* jobs, int njobs, unsigned* status, cudaStream_t s);

@@ -40,67 +40,18 @@ __device__ double block_sum_d(double v, double* sh) {
   return s;
 }
 
-// One warp applies H = I - tau v v^T (v[i] = 1, rows i..d-1 of v in shared
-// memory) to the column wj and returns the squared norm of rows i+1..d-1 of
-// the result in every lane.  Up to 32 rows per lane stay in registers, so
-// the column is read once.
-template <typename T, int RPL>
-__device__ __forceinline__ double warp_reflect_reg(T* wj, const double* v, int i, int d, T tau, int lane) {
-  {
-    T xr[RPL];
-    T s = T(0);
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      const int r = i + lane + 32 * q;
-      xr[q] = r < d ? wj[r] : T(0);
-      if (r < d) s += T(v[r]) * xr[q];
-    }
-    s = wsum<T>(s);
-    const T f = tau * s;
-    double nn = 0.0;
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      const int r = i + lane + 32 * q;
-      if (r < d) {
-        const T x = xr[q] - f * T(v[r]);
-        wj[r] = x;
-        if (r > i) nn += (double)x * (double)x;
-      }
-    }
-    return warp_sum(nn);
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ double warp_reflect(T* wj, const double* v, int i, int d, T tau, int lane) {
-  const int rows = d - i;
-  if (rows <= 32 * 4) return warp_reflect_reg<T, 4>(wj, v, i, d, tau, lane);
-  if (rows <= 32 * 8) return warp_reflect_reg<T, 8>(wj, v, i, d, tau, lane);
-  if (rows <= 32 * 16) return warp_reflect_reg<T, 16>(wj, v, i, d, tau, lane);
-  if (rows <= 32 * 32) return warp_reflect_reg<T, 32>(wj, v, i, d, tau, lane);
-  T s = T(0);
-  for (int r = i + lane; r < d; r += 32) s += T(v[r]) * wj[r];
-  s = wsum<T>(s);
-  const T f = tau * s;
-  double nn = 0.0;
-  for (int r = i + lane; r < d; r += 32) {
-    const T x = wj[r] - f * T(v[r]);
-    wj[r] = x;
-    if (r > i) nn += (double)x * (double)x;
-  }
-  return warp_sum(nn);
-}
-
 // One warp applies H = I - tau v v^T (v[i] = 1) to nc <= 4 columns at once:
 // the loads and the shuffle reductions of the columns are independent and
 // interleave, which hides the latency of each.  nn[c] receives the squared
 // norm of rows i+1..d-1 of column c after the update (all lanes).
+// (All arithmetic is in T: FP64 runs at a small fraction of the FP32 rate on
+// this GPU, so the FP32 form keeps FP64 for the per-step rank decision only.)
 template <typename T>
-__device__ __forceinline__ void warp_reflect4(T* w0, T* w1, T* w2, T* w3, int nc, const double* v,
-                                              int i, int d, T tau, int lane, double* nn) {
+__device__ __forceinline__ void warp_reflect4(T* w0, T* w1, T* w2, T* w3, int nc, const T* v,
+                                              int i, int d, T tau, int lane, T* nn) {
   T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
   for (int r = i + lane; r < d; r += 32) {
-    const T vr = T(v[r]);
+    const T vr = v[r];
     s0 += vr * w0[r];
     s1 += vr * w1[r];
     s2 += vr * w2[r];
@@ -114,32 +65,45 @@ __device__ __forceinline__ void warp_reflect4(T* w0, T* w1, T* w2, T* w3, int nc
     s3 += __shfl_xor_sync(0xffffffffu, s3, o);
   }
   const T f0 = tau * s0, f1 = tau * s1, f2 = tau * s2, f3 = tau * s3;
-  double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;
+  T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
   for (int r = i + lane; r < d; r += 32) {
-    const T vr = T(v[r]);
+    const T vr = v[r];
     const T x0 = w0[r] - f0 * vr, x1 = w1[r] - f1 * vr, x2 = w2[r] - f2 * vr, x3 = w3[r] - f3 * vr;
     w0[r] = x0;
     if (nc > 1) w1[r] = x1;
     if (nc > 2) w2[r] = x2;
     if (nc > 3) w3[r] = x3;
     if (r > i) {
-      n0 += (double)x0 * (double)x0;
-      n1 += (double)x1 * (double)x1;
-      n2 += (double)x2 * (double)x2;
-      n3 += (double)x3 * (double)x3;
+      p0 += x0 * x0;
+      p1 += x1 * x1;
+      p2 += x2 * x2;
+      p3 += x3 * x3;
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    n0 += __shfl_xor_sync(0xffffffffu, n0, o);
-    n1 += __shfl_xor_sync(0xffffffffu, n1, o);
-    n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-    n3 += __shfl_xor_sync(0xffffffffu, n3, o);
+    p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+    p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+    p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+    p3 += __shfl_xor_sync(0xffffffffu, p3, o);
   }
-  nn[0] = n0;
-  nn[1] = n1;
-  nn[2] = n2;
-  nn[3] = n3;
+  nn[0] = p0;
+  nn[1] = p1;
+  nn[2] = p2;
+  nn[3] = p3;
+}
+
+// The per-step decision of the column-pivoted QR, taken by one thread in
+// FP64: pivot norm from the largest remaining squared norm, |R_11| at the
+// first step, and the rank rule |R_{i+1,i+1}| <= eps |R_11| (stop also when
+// R_11 = 0).  Returns 1 to stop.
+__device__ __forceinline__ int id_decide(double best, int i, double eps, double* r11, double* nrm) {
+  *nrm = sqrt(fmax(best, 0.0));
+  if (i == 0) {
+    *r11 = *nrm;
+    return !(*nrm > 0.0);
+  }
+  return !(*nrm > eps * *r11);
 }
 
 // One warp solves R1 x = b by column-oriented back substitution for nc <= 4
@@ -381,60 +345,59 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr_id(const IdJob* __restri
   const T* Y = (const T*)jb.Y;
   T* W = (T*)jb.W;
   extern __shared__ double smem[];
-  double* cn = smem;              // m column norms^2
-  double* vsh = smem + m;         // d: Householder vector of the step
-  int* perm = (int*)(vsh + d);    // m
-  __shared__ double s_bv[ID_THREADS / 32];
+  T* cn = (T*)smem;                  // m column norms^2
+  T* vsh = (T*)(smem + m);           // d: Householder vector of the step
+  int* perm = (int*)(smem + m + d);  // m
+  __shared__ T s_bv[ID_THREADS / 32];
   __shared__ int s_bi[ID_THREADS / 32];
-  __shared__ double s_best;
-  __shared__ int s_bidx;
+  __shared__ T s_nrm;
+  __shared__ int s_bidx, s_stop;
+  __shared__ double s_r11;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = wid; j < m; j += nw) {
-    double s = 0.0;
+    T sp = T(0);
     for (int r = lane; r < d; r += 32) {
       T v = Y[r + j * ld];
       W[r + j * ld] = v;
-      s += (double)v * (double)v;
+      sp += v * v;
     }
-    s = warp_sum(s);
+    sp = wsum<T>(sp);
     if (lane == 0) {
-      cn[j] = s;
+      cn[j] = sp;
       perm[j] = j;
     }
   }
   __syncthreads();
   const int kmax = min(d, m);
   int k = kmax;
-  double r11 = 0.0;
   for (int i = 0; i < kmax; ++i) {
-    double bv = -1.0;
+    T bv = T(-1);
     int bi = m;
     for (int j = i + threadIdx.x; j < m; j += blockDim.x) {
-      double v = cn[j];
+      const T v = cn[j];
       if (v > bv) { bv = v; bi = j; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, bv, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      const T ov = __shfl_down_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
     }
     if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double b = s_bv[0];
+    if (threadIdx.x == 0) {  // the only FP64 work of the step
+      T b = s_bv[0];
       int ix = s_bi[0];
       for (int w = 1; w < nw; ++w)
         if (s_bv[w] > b || (s_bv[w] == b && s_bi[w] < ix)) { b = s_bv[w]; ix = s_bi[w]; }
-      s_best = b;
+      double r11 = s_r11, nrm;
+      s_stop = id_decide((double)b, i, eps, &r11, &nrm);
+      s_r11 = r11;
+      s_nrm = T(nrm);
       s_bidx = ix;
     }
     __syncthreads();
-    const double nrm = sqrt(fmax(s_best, 0.0));
     const int p = s_bidx;
-    if (i == 0) {
-      r11 = nrm;
-      if (!(r11 > 0.0)) { k = 0; break; }
-    } else if (!(nrm > eps * r11)) {
+    if (s_stop) {
       k = i;
       break;
     }
@@ -445,17 +408,18 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr_id(const IdJob* __restri
         W[r + p * ld] = t;
       }
       if (threadIdx.x == 0) {
-        double t = cn[i]; cn[i] = cn[p]; cn[p] = t;
+        T t = cn[i]; cn[i] = cn[p]; cn[p] = t;
         int q = perm[i]; perm[i] = perm[p]; perm[p] = q;
       }
     }
     __syncthreads();
+    const T nrm = s_nrm;
     const T alpha = W[i + i * ld];
     const T beta = alpha >= T(0) ? T(-nrm) : T(nrm);
     const T tau = (beta - alpha) / beta;
     const T scl = T(1) / (alpha - beta);
-    for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) vsh[r] = (double)(W[r + i * ld] * scl);
-    if (threadIdx.x == 0) vsh[i] = 1.0;
+    for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) vsh[r] = W[r + i * ld] * scl;
+    if (threadIdx.x == 0) vsh[i] = T(1);
     __syncthreads();
     for (int j0 = i + 1 + 4 * wid; j0 < m; j0 += 4 * nw) {  // 4 columns per warp
       const int nc = min(4, m - j0);
@@ -463,7 +427,7 @@ __global__ void __launch_bounds__(ID_THREADS, 2) k_cpqr_id(const IdJob* __restri
       T* w1 = nc > 1 ? w0 + ld : w0;
       T* w2 = nc > 2 ? w0 + 2 * ld : w0;
       T* w3 = nc > 3 ? w0 + 3 * ld : w0;
-      double nn[4];
+      T nn[4];
       warp_reflect4<T>(w0, w1, w2, w3, nc, vsh, i, d, tau, lane, nn);
       if (lane < nc) cn[j0 + lane] = lane == 0 ? nn[0] : lane == 1 ? nn[1] : lane == 2 ? nn[2] : nn[3];
     }
@@ -536,49 +500,49 @@ __global__ void __launch_bounds__(IDC_THREADS, 1) k_cpqr_id_cluster(const IdJob*
   int* order = order_all + (long long)jid * max_m;     // pivot column of each step
   extern __shared__ double smem[];
   const int mo = (m - rank + ID_CL - 1) / ID_CL;  // columns owned by this CTA: rank + ID_CL * l
-  double* cn = smem;                               // mo norms^2 (negative: pivoted)
-  double* v = cn + mo;                             // d: Householder vector of the step
-  unsigned char* skel = (unsigned char*)(v + d);   // m flags, replicated in every CTA
-  __shared__ double s_bv[IDC_THREADS / 32];
+  T* cn = (T*)smem;                                        // mo norms^2 (negative: pivoted)
+  T* v = (T*)(smem + mo);                                  // d: Householder vector of the step
+  unsigned char* skel = (unsigned char*)(smem + mo + d);   // m flags, replicated in every CTA
+  __shared__ T s_bv[IDC_THREADS / 32];
   __shared__ int s_bi[IDC_THREADS / 32];
-  __shared__ double s_cand_v;
+  __shared__ T s_cand_v;
   __shared__ int s_cand_i;
-  __shared__ double s_best;
-  __shared__ int s_p;
+  __shared__ T s_nrm;
+  __shared__ int s_p, s_stop;
+  __shared__ double s_r11;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int l = wid; l < mo; l += nw) {
     const int j = rank + ID_CL * l;
-    double s = 0.0;
+    T sp = T(0);
     for (int r = lane; r < d; r += 32) {
       T x = Y[r + j * ld];
       W[r + j * ld] = x;
-      s += (double)x * (double)x;
+      sp += x * x;
     }
-    s = warp_sum(s);
-    if (lane == 0) cn[l] = s;
+    sp = wsum<T>(sp);
+    if (lane == 0) cn[l] = sp;
   }
   for (int j = threadIdx.x; j < m; j += blockDim.x) skel[j] = 0;
   __syncthreads();
   const int kmax = min(d, m);
   int k = kmax;
-  double r11 = 0.0;
   for (int i = 0; i < kmax; ++i) {
     // local proposal: largest norm among the owned, unpivoted columns
-    double bv = -1.0;
+    T bv = T(-1);
     int bi = m;
     for (int l = threadIdx.x; l < mo; l += blockDim.x) {
-      double x = cn[l];
+      const T x = cn[l];
       if (x > bv) { bv = x; bi = rank + ID_CL * l; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, bv, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      const T ov = __shfl_down_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
     }
     if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double b = s_bv[0];
+      T b = s_bv[0];
       int ix = s_bi[0];
       for (int w = 1; w < nw; ++w)
         if (s_bv[w] > b || (s_bv[w] == b && s_bi[w] < ix)) { b = s_bv[w]; ix = s_bi[w]; }
@@ -587,47 +551,47 @@ __global__ void __launch_bounds__(IDC_THREADS, 1) k_cpqr_id_cluster(const IdJob*
     }
     cluster.sync();
     if (wid == 0) {  // every CTA reduces the same proposals (lane r reads CTA r)
-      double b = -1.0;
+      T b = T(-1);
       int ix = m;
       if (lane < ID_CL) {
         b = *cluster.map_shared_rank(&s_cand_v, lane);
         ix = *cluster.map_shared_rank(&s_cand_i, lane);
       }
       for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, b, o);
-        int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+        const T ov = __shfl_xor_sync(0xffffffffu, b, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
         if (ov > b || (ov == b && oi < ix)) { b = ov; ix = oi; }
       }
-      if (lane == 0) {
-        s_best = b;
+      if (lane == 0) {  // identical in every CTA: same inputs, same FP64 decision
+        double r11 = s_r11, nrm;
+        s_stop = id_decide((double)b, i, eps, &r11, &nrm) || ix >= m;
+        s_r11 = r11;
+        s_nrm = T(nrm);
         s_p = ix;
       }
     }
     __syncthreads();
-    const double nrm = sqrt(fmax(s_best, 0.0));
     const int p = s_p;
-    if (i == 0) {
-      r11 = nrm;
-      if (!(r11 > 0.0)) { k = 0; break; }
-    } else if (!(nrm > eps * r11) || p >= m) {
+    if (s_stop) {
       k = i;
       break;
     }
+    const T nrm = s_nrm;
     // Householder vector of the pivot column, rows i..d-1
     const T alpha = W[i + p * ld];
     const T beta = alpha >= T(0) ? T(-nrm) : T(nrm);
     const T tau = (beta - alpha) / beta;
     const T scl = T(1) / (alpha - beta);
-    for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) v[r] = (double)(W[r + p * ld] * scl);
+    for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) v[r] = W[r + p * ld] * scl;
     if (threadIdx.x == 0) {
-      v[i] = 1.0;
+      v[i] = T(1);
       skel[p] = 1;
       if (rank == 0) {
         rdiag[i] = (double)beta;
         order[i] = p;
       }
     }
-    if (p % ID_CL == rank && threadIdx.x == 0) cn[p / ID_CL] = -1.0;
+    if (p % ID_CL == rank && threadIdx.x == 0) cn[p / ID_CL] = T(-1);
     __syncthreads();
     // apply to the owned unpivoted columns; recompute their norms
     for (int g = wid; 4 * g < mo; g += nw) {  // up to 4 owned, unpivoted columns per warp
@@ -643,7 +607,7 @@ __global__ void __launch_bounds__(IDC_THREADS, 1) k_cpqr_id_cluster(const IdJob*
       T* w1 = W + (rank + ID_CL * ls[1]) * ld;
       T* w2 = W + (rank + ID_CL * ls[2]) * ld;
       T* w3 = W + (rank + ID_CL * ls[3]) * ld;
-      double nn[4];
+      T nn[4];
       warp_reflect4<T>(w0, w1, w2, w3, nc, v, i, d, tau, lane, nn);
       if (lane < nc) cn[ls[lane]] = lane == 0 ? nn[0] : lane == 1 ? nn[1] : lane == 2 ? nn[2] : nn[3];
     }
@@ -726,6 +690,244 @@ int HssKern<T>::batched_id_cluster(const IdJob* jobs, int njobs, int max_m, int 
   if (njobs <= 0) return 0;
   if (cl >= 16 && launch_id_cluster<T, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s) == 0) return 0;
   return launch_id_cluster<T, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+}
+
+// ---------------------------------------------------------------------------
+// The ID with the node's matrix resident in shared memory, spread over a
+// cluster of CL CTAs (CL = 1 is a single CTA): CTA r keeps its columns
+// j = r (mod CL) in its own shared memory for the whole factorization, so a
+// step touches no global memory.  The pivot column is read from its owner
+// through distributed shared memory into a local copy of the Householder
+// vector.  Same pivot rule, rank rule, outputs and column order as
+// k_cpqr_id_cluster.
+// ---------------------------------------------------------------------------
+constexpr int IDS_THREADS = 1024;
+constexpr size_t kIdSmemBudget = 200 * 1024;
+
+__host__ __device__ inline size_t id_smem_bytes(int d, int m, int cl, int esz) {
+  const size_t mo = (size_t)(m + cl - 1) / cl;
+  return ((size_t)esz * mo * d + 15) / 16 * 16 + 8 * mo + 8 * (size_t)d + (size_t)m + 64;
+}
+
+template <typename T, int CL>
+__global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __restrict__ jobs, double eps,
+                                                                 double* rdiag_all, int* order_all, int max_m,
+                                                                 int max_k) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
+  const int jid = blockIdx.x / CL;
+  const IdJob jb = jobs[jid];
+  const int d = jb.d, m = jb.m;
+  const T* Y = (const T*)jb.Y;
+  double* rdiag = rdiag_all + (long long)jid * max_k;
+  int* order = order_all + (long long)jid * max_m;
+  extern __shared__ __align__(16) unsigned char sraw[];
+  const int mo = (m - rank + CL - 1) / CL;  // owned columns rank + CL * l
+  const int mo_max = (m + CL - 1) / CL;     // same layout in every CTA of the cluster
+  T* Wl = (T*)sraw;                          // d x mo_max, ld d
+  T* cn = (T*)(sraw + ((size_t)sizeof(T) * mo_max * d + 15) / 16 * 16);  // mo_max norms^2
+  T* v = (T*)((double*)cn + mo_max);                                     // d
+  unsigned char* skel = (unsigned char*)((double*)cn + mo_max + d);      // m
+  __shared__ T s_bv[IDS_THREADS / 32];
+  __shared__ int s_bi[IDS_THREADS / 32];
+  __shared__ T s_cand_v;
+  __shared__ int s_cand_i;
+  __shared__ T s_nrm;
+  __shared__ int s_p, s_stop;
+  __shared__ double s_r11;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = wid; l < mo; l += nw) {
+    const int j = rank + CL * l;
+    T sp = T(0);
+    for (int r = lane; r < d; r += 32) {
+      const T x = Y[r + (long long)j * d];
+      Wl[r + l * d] = x;
+      sp += x * x;
+    }
+    sp = wsum<T>(sp);
+    if (lane == 0) cn[l] = sp;
+  }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) skel[j] = 0;
+  __syncthreads();
+  const int kmax = min(d, m);
+  int k = kmax;
+  for (int i = 0; i < kmax; ++i) {
+    T bv = T(-1);
+    int bi = m;
+    for (int l = threadIdx.x; l < mo; l += blockDim.x) {
+      const T x = cn[l];
+      if (x > bv) { bv = x; bi = rank + CL * l; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_down_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
+    __syncthreads();
+    if (wid == 0) {
+      T b = lane < nw ? s_bv[lane] : T(-1);
+      int ix = lane < nw ? s_bi[lane] : m;
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, b, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+        if (ov > b || (ov == b && oi < ix)) { b = ov; ix = oi; }
+      }
+      if (lane == 0) { s_cand_v = b; s_cand_i = ix; }
+    }
+    if (CL > 1) cluster.sync(); else __syncthreads();
+    if (wid == 0) {
+      T b = T(-1);
+      int ix = m;
+      if (lane < CL) {
+        b = CL > 1 ? *cluster.map_shared_rank(&s_cand_v, lane) : s_cand_v;
+        ix = CL > 1 ? *cluster.map_shared_rank(&s_cand_i, lane) : s_cand_i;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, b, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
+        if (ov > b || (ov == b && oi < ix)) { b = ov; ix = oi; }
+      }
+      if (lane == 0) {  // identical in every CTA: same inputs, same FP64 decision
+        double r11 = s_r11, nrm;
+        s_stop = id_decide((double)b, i, eps, &r11, &nrm) || ix >= m;
+        s_r11 = r11;
+        s_nrm = T(nrm);
+        s_p = ix;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (s_stop) {
+      k = i;
+      break;
+    }
+    const T nrm = s_nrm;
+    // Householder vector from the pivot column, read from its owner's shared memory
+    const int owner = p % CL, lp = p / CL;
+    const T* pc = CL > 1 ? cluster.map_shared_rank(Wl + (long long)lp * d, owner) : Wl + (long long)lp * d;
+    const T alpha = pc[i];
+    const T beta = alpha >= T(0) ? T(-nrm) : T(nrm);
+    const T tau = (beta - alpha) / beta;
+    const T scl = T(1) / (alpha - beta);
+    for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) v[r] = pc[r] * scl;
+    if (threadIdx.x == 0) {
+      v[i] = T(1);
+      skel[p] = 1;
+      if (rank == 0) {
+        rdiag[i] = (double)beta;
+        order[i] = p;
+      }
+    }
+    if (owner == rank && threadIdx.x == 0) cn[lp] = T(-1);
+    __syncthreads();
+    for (int g = wid; 4 * g < mo; g += nw) {  // up to 4 owned, unpivoted columns per warp
+      int ls[4];
+      int nc = 0;
+      for (int q = 0; q < 4; ++q) {
+        const int l = 4 * g + q;
+        if (l < mo && !skel[rank + CL * l]) ls[nc++] = l;
+      }
+      if (nc == 0) continue;
+      for (int q = nc; q < 4; ++q) ls[q] = ls[0];
+      T nn[4];
+      warp_reflect4<T>(Wl + ls[0] * d, Wl + ls[1] * d, Wl + ls[2] * d, Wl + ls[3] * d, nc, v, i, d, tau, lane, nn);
+      if (lane < nc) cn[ls[lane]] = lane == 0 ? nn[0] : lane == 1 ? nn[1] : lane == 2 ? nn[2] : nn[3];
+    }
+    // the pivot column is no longer read by anyone after this barrier
+    if (CL > 1) cluster.sync(); else __syncthreads();
+  }
+  if (CL > 1) cluster.sync(); else __syncthreads();
+  // X = R1^-1 R2 on the owned non-skeleton columns, R1 columns read from their owners
+  const double* rd = rdiag;
+  T* X = (T*)jb.X;
+  for (int g = wid; 4 * g < mo; g += nw) {
+    int ls[4];
+    int nc = 0;
+    for (int q = 0; q < 4; ++q) {
+      const int l = 4 * g + q;
+      if (l < mo && !skel[rank + CL * l]) ls[nc++] = l;
+    }
+    if (nc == 0) continue;
+    for (int q = nc; q < 4; ++q) ls[q] = ls[0];
+    warp_backsub4<T>(Wl + ls[0] * d, Wl + ls[1] * d, Wl + ls[2] * d, Wl + ls[3] * d, nc, k,
+                     [&](int c) {
+                       const int pc2 = order[c];
+                       T* col = Wl + (long long)(pc2 / CL) * d;
+                       return (const T*)(CL > 1 ? cluster.map_shared_rank(col, pc2 % CL) : col);
+                     },
+                     [&](int c) { return T(rd[c]); }, lane);
+    for (int q = 0; q < nc; ++q) {
+      const int j = rank + CL * ls[q];
+      int pos = 0;
+      for (int c = lane; c < j; c += 32) pos += skel[c] ? 0 : 1;
+      for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+      for (int r = lane; r < k; r += 32) X[r + (long long)pos * k] = Wl[r + ls[q] * d];
+      if (lane == 0) jb.piv[k + pos] = j;
+    }
+  }
+  if (rank == 0) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) jb.piv[i] = order[i];
+    if (threadIdx.x == 0) *jb.rank = k;
+  }
+  // peers may still read this CTA's R1 columns
+  if (CL > 1) cluster.sync();
+}
+
+template <typename T, int CL>
+static int launch_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
+                          int* order, cudaStream_t s) {
+  const size_t smem = id_smem_bytes(max_d, max_m, CL, sizeof(T));
+  if (smem > kIdSmemBudget) return -1;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cpqr_id_smem<T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIdSmemBudget);
+    if (CL > 8) cudaFuncSetAttribute(k_cpqr_id_smem<T, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaGetLastError();
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * CL, 1, 1);
+  cfg.blockDim = dim3(IDS_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const int max_k = std::max(std::min(max_m, max_d), 1);
+  if (cudaLaunchKernelEx(&cfg, k_cpqr_id_smem<T, CL>, jobs, eps, rdiag, order, std::max(max_m, 1), max_k) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  count_launch();
+  return 0;
+}
+
+template <typename T>
+int HssKern<T>::id_smem_cluster_size(int d, int m) {
+  for (int cl = 1; cl <= 16; cl *= 2)
+    if (id_smem_bytes(d, m, cl, sizeof(T)) <= kIdSmemBudget) return cl;
+  return 0;
+}
+
+template <typename T>
+int HssKern<T>::batched_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
+                                int* order, int cl, cudaStream_t s) {
+  if (njobs <= 0) return 0;
+  switch (cl) {
+    case 1: return launch_id_smem<T, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 2: return launch_id_smem<T, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 4: return launch_id_smem<T, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 8: return launch_id_smem<T, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 16: return launch_id_smem<T, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    default: return -1;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -841,13 +1043,13 @@ __global__ void __launch_bounds__(256) k_lq_panel(const LqJob* __restrict__ jobs
   __shared__ T sg[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = j0; i < j1; ++i) {
-    double part = 0.0;
+    T part = T(0);
     for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) {
-      double v = (double)D[i + (long long)c * m];
+      const T v = D[i + (long long)c * m];
       part += v * v;
     }
     const T alpha = D[i + (long long)i * m];
-    const double xn2 = block_sum_d(part, sh);
+    const double xn2 = block_sum_d((double)part, sh);
     T t = T(0), beta = alpha, scl = T(0);
     if (xn2 > 0.0) {
       double b = sqrt((double)alpha * (double)alpha + xn2);
@@ -1212,10 +1414,9 @@ __global__ void __launch_bounds__(256) k_ulv_bwd(const UlvBwdJob* __restrict__ j
       const T t = tau[i];
       if (t == T(0)) continue;  // uniform across the block
       const double xi = (double)x[i];  // read before the reduction's barriers
-      double part = 0.0;
-      for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x)
-        part += (double)Dt[i + (long long)c * m] * (double)x[c];
-      const double s = block_sum_d(part, sh) + xi;
+      T part = T(0);
+      for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) part += Dt[i + (long long)c * m] * x[c];
+      const double s = block_sum_d((double)part, sh) + xi;
       const T f = t * T(s);
       if (threadIdx.x == 0) x[i] -= f;
       for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) x[c] -= f * Dt[i + (long long)c * m];

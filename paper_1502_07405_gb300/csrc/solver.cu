@@ -815,9 +815,15 @@ static hssmf_status batched_id_impl(int njobs, const void* Y, const long long* y
     return HSSMF_ERR_OOM;
   }
   cudaMemcpyAsync(dj, jobs.data(), sizeof(IdJob) * njobs, cudaMemcpyHostToDevice, s);
-  int r = use_cluster ? HssKern<T>::batched_id_cluster(dj, njobs, max_m, max_d, eps, rdiag, order, s,
-                                                       use_cluster >= 16 ? 16 : 8)
-                      : HssKern<T>::batched_id(dj, njobs, max_m, max_d, eps, s);
+  int r;
+  if (use_cluster < 0) {  // shared-memory-resident matrices on a cluster sized for the largest job
+    const int cl = HssKern<T>::id_smem_cluster_size(max_d, max_m);
+    r = cl > 0 ? HssKern<T>::batched_id_smem(dj, njobs, max_m, max_d, eps, rdiag, order, cl, s) : -1;
+  } else if (use_cluster > 0) {
+    r = HssKern<T>::batched_id_cluster(dj, njobs, max_m, max_d, eps, rdiag, order, s, use_cluster >= 16 ? 16 : 8);
+  } else {
+    r = HssKern<T>::batched_id(dj, njobs, max_m, max_d, eps, s);
+  }
   if (r < 0) st = HSSMF_ERR_ARG;
   if (!st) cudaMemcpyAsync(rank_host, rk, sizeof(int) * njobs, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) st = HSSMF_ERR_CUDA;

@@ -49,7 +49,7 @@ def _decaying(d, m, rank_scale, seed):
     return (Q1 * s) @ Q2.T
 
 
-@pytest.mark.parametrize("cluster", [0, 1])
+@pytest.mark.parametrize("cluster", [0, 1, -1])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_batched_id_matches_oracle(cluster, prec):
     shapes = [(128, 128), (192, 128), (256, 300), (96, 700), (300, 64)]
@@ -70,7 +70,7 @@ def test_batched_id_matches_oracle(cluster, prec):
         assert err <= 50 * eps
 
 
-@pytest.mark.parametrize("cluster", [0, 1])
+@pytest.mark.parametrize("cluster", [0, 1, -1])
 def test_batched_id_exact_low_rank_and_zero(cluster):
     rng = np.random.default_rng(5)
     Y1 = rng.standard_normal((200, 9)) @ rng.standard_normal((9, 500))
