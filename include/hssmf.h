@@ -180,6 +180,28 @@ hssmf_status hssmf_batched_id(int prec, int njobs, const void* Y, const long lon
                               const long long* p_off, void* X, const long long* x_off,
                               int use_cluster, void* cuda_stream);
 
+/* Kernel-level entry point: the FP32 GEMM of the FP32 factorization,
+ * C = alpha op(A) op(B) + beta C with op(A) m x k and op(B) k x n
+ * (transa/transb = 1: use the transpose), column-major device arrays with
+ * leading dimensions lda, ldb, ldc.  It runs on the tensor cores
+ * (tcgen05, 128 x 128 tiles, accumulator in tensor memory): every FP32
+ * operand value is split into three BF16 terms and the six term products of
+ * order >= 2^-16 are accumulated in FP32, which gives FP32-level accuracy.
+ * b_exact = 1 declares that every value of B is exactly a BF16 number
+ * (as the FP32 form's sampling matrix R is, Section 4.3), which drops the
+ * products to three; values of B that are not BF16 are then rounded.  The
+ * paper's products S = F R of eq. FtimesR, the sample updates of
+ * Algorithm 1 and the Schur complements of Sections 3.2 and 4.4 use this
+ * kernel in the FP32 form.
+ *   - HSSMF_ERR_ARG for negative sizes, null arrays or leading dimensions
+ *     below the stored rows; m, n or k = 0 is valid (C = beta C).
+ *   - HSSMF_ERR_TIMEOUT if a bounded wait inside the kernel ran out.
+ *   - Allocates and frees device scratch for the job and its tile list on
+ *     every call; synchronizes the stream. */
+hssmf_status hssmf_gemm_f32(int transa, int transb, int m, int n, int k, float alpha,
+                            const float* A, long long lda, const float* B, long long ldb,
+                            float beta, float* C, long long ldc, int b_exact, void* cuda_stream);
+
 /* Allocation-free form of hssmf_batched_id for callers that must not
  * allocate device memory while they run: cudaMalloc/cudaFree synchronize
  * the whole device, an application's memory pool may already own the

@@ -25,14 +25,18 @@ struct GemmJob {
   long long lda, ldb, ldc;
   int M, N, K;
   int ta, tb;  // 1 = use the transpose
+  // FP32 tensor-core path: operand values exactly representable in BF16
+  // (one split term instead of three)
+  int a_exact, b_exact;
   double alpha, beta;
 };
 
-struct Tile {  // one 64 x 64 output tile of one job
+struct Tile {  // one output tile of one job (64 x 64 SIMT, 128 x 128 tensor cores)
   int job, tm, tn;
 };
 
 constexpr int GEMM_TILE = 64;
+constexpr int GEMM_TILE_TC = 128;
 
 inline int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }
 

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "hss.h"
@@ -274,8 +275,11 @@ struct Ctx {  // per-call helpers
   }
   const int* ints(long long off) const { return c.d_ints + off; }
   // C = alpha op(A) op(B) + beta C
+  // b_exact: the values of B are exactly BF16 (the sampling matrix of the
+  // FP32 form), which halves the tensor-core products
   void gemm(const void* A_, long long lda, int ta, const void* B_, long long ldb, int tb, void* C_,
-            long long ldc, int M, int N, int K, double alpha, double beta, const int* crow = nullptr) {
+            long long ldc, int M, int N, int K, double alpha, double beta, const int* crow = nullptr,
+            int b_exact = 0) {
     if (M <= 0 || N <= 0) return;
     if (K <= 0 && beta == 1.0) return;
     GemmJob j;
@@ -284,21 +288,28 @@ struct Ctx {  // per-call helpers
     j.lda = lda; j.ldb = ldb; j.ldc = ldc;
     j.M = M; j.N = N; j.K = std::max(K, 0);
     j.ta = ta; j.tb = tb; j.alpha = alpha; j.beta = beta;
+    j.b_exact = b_exact;
     gj.push_back(j);
     H.flops += 2.0 * M * N * std::max(K, 0);
   }
+  // FP32: tensor cores (128 x 128 tiles); FP64: the DFMA kernel (64 x 64)
   void flush_gemm() {
     if (gj.empty()) return;
+    constexpr bool tc = std::is_same<T, float>::value;
+    const int tile = tc ? GEMM_TILE_TC : GEMM_TILE;
     std::vector<Tile> tiles;
     for (size_t i = 0; i < gj.size(); ++i) {
-      int tm = ceil_div(gj[i].M, 64), tn = ceil_div(gj[i].N, 64);
+      int tm = ceil_div(gj[i].M, tile), tn = ceil_div(gj[i].N, tile);
       for (int b = 0; b < tn; ++b)
         for (int a = 0; a < tm; ++a) tiles.push_back(Tile{(int)i, a, b});
     }
     const GemmJob* dj = H.ring.put(gj, s);
     const Tile* dt = H.ring.put(tiles, s);
     if (!dj || !dt) { oom = true; gj.clear(); return; }
-    Kern<T>::gemm(dj, dt, (int)tiles.size(), s);
+    if (tc)
+      gemm_tc(dj, dt, (int)tiles.size(), c.d_status, s);
+    else
+      Kern<T>::gemm(dj, dt, (int)tiles.size(), s);
     gj.clear();
   }
   void copy(const void* src, long long lds, int trans, void* dst, long long ldd, int rows, int cols,
@@ -367,9 +378,9 @@ void sample_fronts(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       const T* Rk = (const T*)F->Rch[k] + (long long)c0 * ch.nu;
       const int* pos = X.ints(F->pos_off[k]);
       X.gemm(U, ch.u_ld, 0, Rk, ch.nu, 0, (T*)F->Sr + (long long)c0 * F->nf, F->nf, ch.nu, w, ch.nu,
-             1.0, 1.0, pos);
+             1.0, 1.0, pos, 1);
       X.gemm(U, ch.u_ld, 1, Rk, ch.nu, 0, (T*)F->Sc + (long long)c0 * F->nf, F->nf, ch.nu, w, ch.nu,
-             1.0, 1.0, pos);
+             1.0, 1.0, pos, 1);
     }
     X.flush_gemm();
   }

@@ -1,0 +1,343 @@
+// FP32 GEMM on the 5th-generation tensor cores (tcgen05, accumulators in
+// tensor memory) for the dense contractions of the FP32 factorization: the
+// sampling products U_child R of eq. FtimesR (Section 4.3), the sample
+// updates of Algorithm 1 and the Schur-complement products (Sections 3.2,
+// 4.4).
+//
+// FP32 accuracy from BF16 multiplies: every FP32 operand value x is split
+// into three BF16 terms x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0),
+// x2 = bf16(x - x0 - x1)), which represent x to about 2^-24 |x|; the product
+// keeps the six term products of order >= 2^-16 (i + j <= 2), accumulated in
+// FP32 in tensor memory.  An operand whose values are exactly BF16 (the
+// sampling matrix R of the FP32 form) uses one term, and its products drop to
+// three.
+//
+// One CTA computes one 128 x 128 tile of C over the whole K range, 64 K per
+// stage, two stages: all 256 threads load a stage from global memory, split
+// it and store the BF16 terms into shared memory in the canonical K-major
+// layout (8 x 8 core matrices, no swizzle); one thread issues the tcgen05.mma
+// instructions of the stage and commits them to the stage's mbarrier, which
+// the threads wait on before refilling that stage.  The accumulator (128
+// lanes x 128 FP32 columns) is read back with tcgen05.ld and scattered to the
+// rows crow(i) of C.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/hssmf.h"
+#include "kernels.h"
+
+namespace hssmf {
+
+namespace {
+
+constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
+constexpr int TC_THREADS = 256;
+constexpr int TC_TERM_BYTES = TC_M * TC_K * 2;          // one BF16 term of one operand tile
+constexpr int TC_STAGE_BYTES = 6 * TC_TERM_BYTES;       // 3 terms of A, 3 terms of B
+constexpr int TC_STAGES = 2;
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;  // + alignment slack
+constexpr unsigned TC_TMEM_COLS = 128;
+constexpr long long TC_SPIN = 1LL << 26;  // bound on every mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Byte offset of element (r, k) of a 128 x 64 K-major BF16 tile: core
+// matrices of 8 rows x 16 bytes stored contiguously (128 B), the 8 core
+// matrices along K of a row group adjacent (leading byte offset 128 B), row
+// groups 1024 B apart (stride byte offset).
+__device__ __forceinline__ int tile_off(int r, int k) {
+  return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// tcgen05 shared-memory matrix descriptor, no swizzle: start address,
+// leading byte offset 128, stride byte offset 1024, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = n (multiple of 16).
+__device__ __forceinline__ uint32_t instr_desc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Waits for the completion of the phase with the given parity; false if the
+// bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < TC_SPIN; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Splits 8 FP32 values into nt BF16 terms (packed 8 per uint4).
+__device__ __forceinline__ void split8(const float* x, int nt, uint4* t0, uint4* t1, uint4* t2) {
+  uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const float a = x[2 * p], b = x[2 * p + 1];
+    __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b);
+    w0[p] = *reinterpret_cast<uint32_t*>(&h0);
+    if (nt > 1) {
+      const float ra = a - __low2float(h0), rb = b - __high2float(h0);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(ra, rb);
+      w1[p] = *reinterpret_cast<uint32_t*>(&h1);
+      const float sa = ra - __low2float(h1), sb = rb - __high2float(h1);
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(sa, sb);
+      w2[p] = *reinterpret_cast<uint32_t*>(&h2);
+    }
+  }
+  *t0 = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+  if (nt > 1) {
+    *t1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *t2 = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+  }
+}
+
+// Loads rows [r0, r0 + 128) x K range [k0, k0 + 64) of an operand whose
+// element (r, k) sits at P[r * sr + k * sk] (one of sr, sk is 1; rc = rows
+// contiguous), rows < R and k < K valid: k beyond K is stored as zero, rows
+// beyond R are not written (their products land in output rows or columns
+// that are never stored).  Each thread handles 4 chunks of 8 consecutive k of
+// one row; lanes walk the contiguous direction of the operand.
+__device__ __forceinline__ void load_tile(const float* __restrict__ P, long long sr, long long sk,
+                                          bool rc, int r0, int R, int k0, int K, int nt,
+                                          char* dst) {
+#pragma unroll
+  for (int q4 = 0; q4 < 4; ++q4) {
+    const int q = threadIdx.x + TC_THREADS * q4;
+    // rows contiguous: 32 consecutive rows per warp, same k chunk;
+    // k contiguous: 8 rows x 4 chunks per warp (one row group per store phase)
+    const int r = rc ? (q & 127) : ((q & 7) | ((q >> 5) << 3)) & 127;
+    const int kc = rc ? (q >> 7) : ((q >> 3) & 3) | ((q >> 9) << 2);
+    const int gr = r0 + r;
+    if (gr >= R) continue;
+    const int kb = k0 + 8 * kc;
+    float x[8];
+    const float* p = P + (long long)gr * sr;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = (kb + j < K) ? __ldg(p + (long long)(kb + j) * sk) : 0.f;
+    uint4 t0, t1, t2;
+    split8(x, nt, &t0, &t1, &t2);
+    const int o = tile_off(r, 8 * kc);
+    *reinterpret_cast<uint4*>(dst + o) = t0;
+    if (nt > 1) {
+      *reinterpret_cast<uint4*>(dst + TC_TERM_BYTES + o) = t1;
+      *reinterpret_cast<uint4*>(dst + 2 * TC_TERM_BYTES + o) = t2;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmJob* __restrict__ jobs,
+                                                           const Tile* __restrict__ tiles,
+                                                           unsigned* __restrict__ status) {
+  extern __shared__ char smem_raw[];
+  __shared__ __align__(8) unsigned long long s_bar[TC_STAGES];
+  __shared__ uint32_t s_tmem;
+  char* smem = (char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const Tile tl = tiles[blockIdx.x];
+  const GemmJob jb = jobs[tl.job];
+  const int m0 = tl.tm * TC_M, n0 = tl.tn * TC_N;
+  const int M = jb.M, N = jb.N, K = jb.K;
+  const int na = jb.a_exact ? 1 : 3, nb = jb.b_exact ? 1 : 3;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // op(A)(i, k) = A[i + k lda] or A[k + i lda]; op(B)(k, j) = B[k + j ldb] or B[j + k ldb]
+  const float* A = (const float*)jb.A;
+  const float* B = (const float*)jb.B;
+  const long long a_sr = jb.ta ? jb.lda : 1, a_sk = jb.ta ? 1 : jb.lda;
+  const long long b_sr = jb.tb ? 1 : jb.ldb, b_sk = jb.tb ? jb.ldb : 1;
+  const int nmma = min(TC_N, (N - n0 + 15) & ~15);
+  const uint32_t idesc = instr_desc(nmma);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < TC_STAGES; ++s) mbar_init(smem_u32(&s_bar[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  const int nk = (K + TC_K - 1) / TC_K;
+  bool ok = true;
+  for (int t = 0; t < nk; ++t) {
+    const int st = t & 1;
+    char* sa = smem + st * TC_STAGE_BYTES;
+    char* sb = sa + 3 * TC_TERM_BYTES;
+    if (t >= TC_STAGES) ok = ok && mbar_wait(smem_u32(&s_bar[st]), ((t - TC_STAGES) >> 1) & 1);
+    load_tile(A, a_sr, a_sk, jb.ta == 0, m0, M, t * TC_K, K, na, sa);
+    load_tile(B, b_sr, b_sk, jb.tb != 0, n0, N, t * TC_K, K, nb, sb);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
+#pragma unroll
+      for (int kk = 0; kk < TC_K / 16; ++kk) {
+        for (int i = 0; i < na; ++i)
+          for (int j = 0; j < nb && i + j <= 2; ++j) {
+            const uint64_t ad = smem_desc(a0 + i * TC_TERM_BYTES + kk * 256);
+            const uint64_t bd = smem_desc(b0 + j * TC_TERM_BYTES + kk * 256);
+            mma_bf16(tmem, ad, bd, idesc, (t > 0 || kk > 0 || i > 0 || j > 0) ? 1u : 0u);
+          }
+      }
+      mma_commit(smem_u32(&s_bar[st]));
+    }
+  }
+  // the last commit covers every MMA issued before it
+  if (nk > 0) ok = ok && mbar_wait(smem_u32(&s_bar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok && threadIdx.x == 0) set_status(status, ST_TIMEOUT);
+
+  // epilogue: warp w reads lanes 32 (w % 4) .. +31 (rows), columns 64 (w / 4) .. +63
+  const int q = warp & 3, h = warp >> 2;
+  const int i = 32 * q + lane, gi = m0 + i;
+  const float alpha = (float)jb.alpha, beta = (float)jb.beta;
+  const long long crow = gi < M ? (jb.crow ? jb.crow[gi] : gi) : 0;
+  float* C = (float*)jb.C;
+#pragma unroll 1
+  for (int cb = 0; cb < 2; ++cb) {
+    const int c0 = 64 * h + 32 * cb;
+    if (c0 >= nmma) break;  // warp-uniform
+    float v[32];
+    if (nk > 0 && ok) {
+      tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 32; ++e) v[e] = 0.f;
+    }
+    if (gi < M) {
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        const int gj = n0 + c0 + e;
+        if (gj < N) {
+          float* c = C + crow + (long long)gj * jb.ldc;
+          *c = (jb.beta == 0.0) ? alpha * v[e] : alpha * v[e] + beta * *c;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+void gemm_tc(const GemmJob* jobs, const Tile* tiles, int ntiles, unsigned* status, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    attr = true;
+  }
+  k_gemm_tc<<<ntiles, TC_THREADS, TC_SMEM, s>>>(jobs, tiles, status);
+  count_launch();
+}
+
+}  // namespace hssmf
+
+extern "C" hssmf_status hssmf_gemm_f32(int transa, int transb, int m, int n, int k, float alpha,
+                                       const float* A, long long lda, const float* B, long long ldb,
+                                       float beta, float* C, long long ldc, int b_exact, void* cuda_stream) {
+  using namespace hssmf;
+  if (m < 0 || n < 0 || k < 0) return HSSMF_ERR_ARG;
+  if (m == 0 || n == 0) return HSSMF_OK;
+  if (!C || ldc < m) return HSSMF_ERR_ARG;
+  if (k > 0 && (!A || !B || lda < (transa ? k : m) || ldb < (transb ? n : k))) return HSSMF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  GemmJob j;
+  std::memset(&j, 0, sizeof(j));
+  j.A = A; j.B = B; j.C = C;
+  j.lda = lda; j.ldb = ldb; j.ldc = ldc;
+  j.M = m; j.N = n; j.K = k;
+  j.ta = transa != 0; j.tb = transb != 0;
+  j.b_exact = b_exact != 0;
+  j.alpha = alpha; j.beta = beta;
+  std::vector<Tile> tiles;
+  for (int b = 0; b < ceil_div(n, GEMM_TILE_TC); ++b)
+    for (int a = 0; a < ceil_div(m, GEMM_TILE_TC); ++a) tiles.push_back(Tile{0, a, b});
+  const size_t bytes = 256 + sizeof(GemmJob) + sizeof(Tile) * tiles.size();
+  char* d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) return HSSMF_ERR_CUDA;
+  unsigned* st = (unsigned*)d;
+  GemmJob* dj = (GemmJob*)(d + 256);
+  Tile* dt = (Tile*)(d + 256 + sizeof(GemmJob));
+  hssmf_status r = HSSMF_OK;
+  unsigned hs = 0;
+  if (cudaMemsetAsync(st, 0, sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemcpyAsync(dj, &j, sizeof(j), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dt, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    r = HSSMF_ERR_CUDA;
+  if (r == HSSMF_OK) {
+    gemm_tc(dj, dt, (int)tiles.size(), st, s);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&hs, st, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      r = HSSMF_ERR_CUDA;
+    else if (hs & ST_TIMEOUT)
+      r = HSSMF_ERR_TIMEOUT;
+  }
+  cudaFree(d);
+  return r;
+}

@@ -1,5 +1,6 @@
 // Kernels of the HSS frontal matrices (Sections 2.2, 2.3, 4.3-4.5).
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -164,6 +165,32 @@ __device__ __forceinline__ double gauss(unsigned long long seed, unsigned g, uns
   return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
 }
 
+// The FP32 form's sampling matrix: the same Gaussian, evaluated in FP32 from
+// the top 24 bits of the two Philox words, rounded to the nearest BF16 value.
+// Exactly-BF16 values make the products U R on the tensor cores exact in R;
+// the whole FP32 factorization uses these values, so the random sketch stays
+// consistent across fronts (eq. Rmerge).
+__device__ __forceinline__ float gauss_bf16(unsigned long long seed, unsigned g, unsigned c) {
+  unsigned ctr[4] = {g, c, 0u, 0u};
+  philox4x32_10(ctr, (unsigned)(seed & 0xFFFFFFFFull), (unsigned)(seed >> 32));
+  const float s = 5.9604644775390625e-8f;  // 2^-24
+  const float u1 = ((float)(ctr[0] >> 8) + 0.5f) * s;
+  const float u2 = ((float)(ctr[1] >> 8) + 0.5f) * s;
+  const float v = sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+template <typename T>
+__device__ __forceinline__ T gauss_t(unsigned long long seed, unsigned g, unsigned c);
+template <>
+__device__ __forceinline__ double gauss_t<double>(unsigned long long seed, unsigned g, unsigned c) {
+  return gauss(seed, g, c);
+}
+template <>
+__device__ __forceinline__ float gauss_t<float>(unsigned long long seed, unsigned g, unsigned c) {
+  return gauss_bf16(seed, g, c);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -225,7 +252,7 @@ __global__ void k_philox(const PhiloxJob* __restrict__ jobs, unsigned long long 
   if (i >= jb.rows) return;
   const unsigned g = (unsigned)jb.gidx[i];
   T* out = (T*)jb.out;
-  for (int c = jb.c0; c < jb.c1; ++c) out[i + (long long)c * jb.ld] = T(gauss(seed, g, (unsigned)c));
+  for (int c = jb.c0; c < jb.c1; ++c) out[i + (long long)c * jb.ld] = gauss_t<T>(seed, g, (unsigned)c);
 }
 
 template <typename T>

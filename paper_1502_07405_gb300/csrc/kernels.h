@@ -62,6 +62,11 @@ struct Kern {
                               const int* flist, int nfr, int nrhs, int transpose, cudaStream_t s);
 };
 
+// FP32 GEMM over a tile list of 128 x 128 tiles on the tensor cores
+// (three-term BF16 split, FP32 accumulation in tensor memory); status gets
+// ST_TIMEOUT if a bounded wait ran out.
+void gemm_tc(const GemmJob* jobs, const Tile* tiles, int ntiles, unsigned* status, cudaStream_t s);
+
 // FP64 outer-iteration kernels ------------------------------------------------
 void spmv(const DevSym& ds, const double* values, const double* x, double* y, int nrhs,
           int transpose, cudaStream_t s);

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hssmf.h"
@@ -214,7 +215,7 @@ hssmf_status hssmf_ctx::build_plan() {
         j.beta = 1.0;
         int jid = (int)jobs.size();
         jobs.push_back(j);
-        int t = ceil_div(M, 64);
+        int t = ceil_div(M, fp32 ? GEMM_TILE_TC : GEMM_TILE);  // FP32: tensor-core tiles
         for (int tn = 0; tn < t; ++tn)
           for (int tm = 0; tm < t; ++tm) tiles.push_back(Tile{jid, tm, tn});
       }
@@ -308,7 +309,10 @@ hssmf_status hssmf_ctx::factor_impl() {
     for (const StepPlan& sp : L.steps) {
       Kern<T>::panel_lu(ds, ar, d_piv, d_flist + L.dense_off, L.ndense, sp.k0, NB, d_status, stream);
       Kern<T>::panel_trsm(ds, ar, d_flist + L.dense_off, L.ndense, sp.k0, NB, sp.trsm_chunks, stream);
-      Kern<T>::gemm(d_jobs, d_tiles + sp.tile_off, sp.ntiles, stream);
+      if (std::is_same<T, float>::value)
+        gemm_tc(d_jobs, d_tiles + sp.tile_off, sp.ntiles, d_status, stream);
+      else
+        Kern<T>::gemm(d_jobs, d_tiles + sp.tile_off, sp.ntiles, stream);
     }
     for (int f : L.dense) {
       double ns = fronts_host[f].ns, nu = fronts_host[f].nu;
