@@ -156,6 +156,15 @@ hssmf_status hssmf_get_upd(const hssmf_ctx* ctx, int f, int* upd);
 hssmf_status hssmf_get_phase_times(const hssmf_ctx* ctx, double* ms, int n);
 hssmf_status hssmf_set_profiling(hssmf_ctx* ctx, int on);
 
+/* Records of every interpolative decomposition of the last factorization
+ * run with profiling on (Algorithm 1 with the adaptive scheme of Section
+ * 2.2.1): 9 ints per node attempt -- front, HSS node, adaptive round of the
+ * front, sample columns d, rows m of the row ID, rows of the column ID,
+ * row rank, column rank, 1 if both IDs were accepted.  Copies at most
+ * max_records records into rec (host, may be NULL) and returns the number
+ * available, or -1 for a NULL context. */
+int hssmf_get_id_trace(const hssmf_ctx* ctx, int* rec, int max_records);
+
 /* Kernel-level entry point: a batch of interpolative decompositions
  * (Section 2.2, ID definitions; rank rule of Section 5.3).  Job j selects
  * columns of Y_j (d_j x m_j, column-major, leading dimension d_j, device
@@ -173,7 +182,10 @@ hssmf_status hssmf_set_profiling(hssmf_ctx* ctx, int on);
  * thread-block cluster of 8 CTAs, 16 on a cluster of 16 CTAs (where the
  * device can schedule it, else 8), all working on the matrix in L2;
  * use_cluster = -1 keeps every matrix in the shared memory of a cluster of
- * 1..16 CTAs sized for the largest job (HSSMF_ERR_ARG if it does not fit).
+ * 1..16 CTAs sized for the largest job (HSSMF_ERR_ARG if it does not fit);
+ * use_cluster = -2 (prec 1 only) keeps every matrix in the registers of a
+ * cluster of 1..16 CTAs, for d <= 512 and m <= 2048 (d <= 256) or m <= 1024
+ * (d <= 512), else HSSMF_ERR_ARG.
  * Y is not modified.  Synchronizes the stream. */
 hssmf_status hssmf_batched_id(int prec, int njobs, const void* Y, const long long* y_off,
                               const int* m, const int* d, double eps, int* rank_host, int* piv,

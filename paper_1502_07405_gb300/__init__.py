@@ -82,6 +82,8 @@ lib.hssmf_get_symbolic.argtypes = [_P, _IP, _IP, _IP, _IP, _IP]
 lib.hssmf_get_upd.argtypes = [_P, _I, _IP]
 lib.hssmf_get_phase_times.argtypes = [_P, C.POINTER(C.c_double), _I]
 lib.hssmf_set_profiling.argtypes = [_P, _I]
+lib.hssmf_get_id_trace.argtypes = [_P, _IP, _I]
+lib.hssmf_get_id_trace.restype = C.c_int
 lib.hssmf_last_error.argtypes = [_P]
 lib.hssmf_last_error.restype = C.c_char_p
 lib.hssmf_destroy.argtypes = [_P]
@@ -207,6 +209,17 @@ class Solver:
         buf = (C.c_double * len(self.PHASES))()
         self._check(lib.hssmf_get_phase_times(self._h, buf, len(self.PHASES)))
         return dict(zip(self.PHASES, list(buf)))
+
+    ID_TRACE_FIELDS = ("front", "node", "round", "d", "m", "mc", "kr", "kc", "accepted")
+
+    def get_id_trace(self):
+        """Per-node ID records of the last profiled factorization, an
+        (records x 9) int array with columns ID_TRACE_FIELDS."""
+        n = lib.hssmf_get_id_trace(self._h, None, 0)
+        buf = np.zeros((max(n, 0), 9), dtype=np.int32)
+        if n > 0:
+            lib.hssmf_get_id_trace(self._h, _int_ptr(buf), n)
+        return buf
 
     def get_symbolic(self, n_fronts):
         perm = np.zeros(self.n, dtype=np.int32)

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <type_traits>
 #include <vector>
 
@@ -292,24 +293,33 @@ struct Ctx {  // per-call helpers
     gj.push_back(j);
     H.flops += 2.0 * M * N * std::max(K, 0);
   }
-  // FP32: tensor cores (128 x 128 tiles); FP64: the DFMA kernel (64 x 64)
+  // FP32 products with a long K (the sampling products U R, the Schur
+  // expansions) run on the tensor cores in 128 x 128 tiles; short-K products
+  // and FP64 run on the CUDA-core kernel (64 x 64 tiles, several CTAs per SM)
+  static bool on_tensor_cores(const GemmJob& j) {
+    return std::is_same<T, float>::value && j.K >= 256 && j.M >= 128 && j.N >= 16;
+  }
   void flush_gemm() {
     if (gj.empty()) return;
-    constexpr bool tc = std::is_same<T, float>::value;
-    const int tile = tc ? GEMM_TILE_TC : GEMM_TILE;
-    std::vector<Tile> tiles;
-    for (size_t i = 0; i < gj.size(); ++i) {
-      int tm = ceil_div(gj[i].M, tile), tn = ceil_div(gj[i].N, tile);
-      for (int b = 0; b < tn; ++b)
-        for (int a = 0; a < tm; ++a) tiles.push_back(Tile{(int)i, a, b});
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool tc = pass == 1;
+      const int tile = tc ? GEMM_TILE_TC : GEMM_TILE;
+      std::vector<Tile> tiles;
+      for (size_t i = 0; i < gj.size(); ++i) {
+        if (on_tensor_cores(gj[i]) != tc) continue;
+        int tm = ceil_div(gj[i].M, tile), tn = ceil_div(gj[i].N, tile);
+        for (int b = 0; b < tn; ++b)
+          for (int a = 0; a < tm; ++a) tiles.push_back(Tile{(int)i, a, b});
+      }
+      if (tiles.empty()) continue;
+      const GemmJob* dj = H.ring.put(gj, s);
+      const Tile* dt = H.ring.put(tiles, s);
+      if (!dj || !dt) { oom = true; gj.clear(); return; }
+      if (tc)
+        gemm_tc(dj, dt, (int)tiles.size(), c.d_status, s);
+      else
+        Kern<T>::gemm(dj, dt, (int)tiles.size(), s);
     }
-    const GemmJob* dj = H.ring.put(gj, s);
-    const Tile* dt = H.ring.put(tiles, s);
-    if (!dj || !dt) { oom = true; gj.clear(); return; }
-    if (tc)
-      gemm_tc(dj, dt, (int)tiles.size(), c.d_status, s);
-    else
-      Kern<T>::gemm(dj, dt, (int)tiles.size(), s);
     gj.clear();
   }
   void copy(const void* src, long long lds, int trans, void* dst, long long ldd, int rows, int cols,
@@ -558,7 +568,20 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         // from L2 (16 CTAs for the largest).
         std::vector<IdJob> tier[3], smem_tier[5];
         int tm[3] = {0, 0, 0}, td[3] = {0, 0, 0}, sm_m[5] = {0, 0, 0, 0, 0}, sm_d[5] = {0, 0, 0, 0, 0};
+        std::map<int, std::vector<IdJob>> rr_tier;  // register-resident (FP32), by configuration
+        std::map<int, std::pair<int, int>> rr_md;
         for (const IdJob& j : ij) {
+          // registers hold less than shared memory: the register-resident
+          // kernel only where it needs no larger cluster
+          const int rr = HssKern<T>::id_rr_config(j.d, j.m);
+          const int cl_sm = HssKern<T>::id_smem_cluster_size(j.d, j.m);
+          if (rr > 0 && (cl_sm == 0 || (rr & 31) <= cl_sm)) {
+            rr_tier[rr].push_back(j);
+            auto& md = rr_md[rr];
+            md.first = std::max(md.first, j.m);
+            md.second = std::max(md.second, j.d);
+            continue;
+          }
           const long long w = (long long)j.d * j.m;
           const int cl = HssKern<T>::id_smem_cluster_size(j.d, j.m);
           if (w * (long long)sizeof(T) > kTinyIdBytes && cl > 0) {
@@ -572,6 +595,16 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           tier[t].push_back(j);
           tm[t] = std::max(tm[t], j.m);
           td[t] = std::max(td[t], j.d);
+        }
+        for (auto& kv : rr_tier) {
+          const int mm = rr_md[kv.first].first, dd = rr_md[kv.first].second;
+          double* rdiag = (double*)H.rnd.alloc(sizeof(double) * kv.second.size() * std::max(std::min(mm, dd), 1));
+          int* order = (int*)H.rnd.alloc(sizeof(int) * kv.second.size() * std::max(mm, 1));
+          const IdJob* dj = H.ring.put(kv.second, X.s);
+          if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
+          if (HssKern<T>::batched_id_rr(dj, (int)kv.second.size(), mm, dd, eps, rdiag, order, kv.first, X.s) < 0)
+            return c.fail(HSSMF_ERR_CUDA, "register-resident ID launch failed");
+          ++c.id_launches;
         }
         for (int ti = 0; ti < 5; ++ti) {
           if (smem_tier[ti].empty()) continue;
@@ -632,6 +665,10 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           const bool cap = d >= F.nf;
           const bool ok_r = kr <= d - p || kr == N.m || cap;
           const bool ok_c = kc <= d - p || kc == N.mc || cap;
+          if (c.prof.on) {
+            const int rec[9] = {F.f, idn[i].t, F.rounds, d, N.m, N.mc, kr, kc, (int)(ok_r && ok_c)};
+            c.id_trace.insert(c.id_trace.end(), rec, rec + 9);
+          }
           if (ok_r && ok_c) {
             N.done = true;
             N.kr = kr;
@@ -1180,6 +1217,7 @@ void hss_begin_factor(hssmf_ctx& c) {
   c.hss_max_rank = c.hss_max_d = c.hss_rounds = 0;
   c.id_launches = 0;
   c.id_bytes = c.id_flops = 0.0;
+  c.id_trace.clear();
   c.hss_flops = c.hss_bytes = 0.0;
   if (!c.hss) return;
   c.hss->fac.reset();

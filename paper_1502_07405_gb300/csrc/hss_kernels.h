@@ -138,6 +138,12 @@ struct HssKern {
   // Shared-memory-resident ID on clusters of cl CTAs (1, 2, 4, 8, 16); the
   // smallest cl whose shared memory holds a d x m node, 0 if none does.
   static int id_smem_cluster_size(int d, int m);
+  // register-resident ID (FP32 only): 0 if (d, m) does not fit, else a
+  // configuration code for batched_id_rr (cluster size, + 32 for the
+  // 16-rows-per-lane layout)
+  static int id_rr_config(int d, int m);
+  static int batched_id_rr(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
+                           int* order, int cfg, cudaStream_t s);
   static int batched_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
                              int* order, int cl, cudaStream_t s);
   static void basis(const BasisJob* jobs, int njobs, cudaStream_t s);

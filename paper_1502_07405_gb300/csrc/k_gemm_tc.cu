@@ -12,8 +12,9 @@
 // sampling matrix R of the FP32 form) uses one term, and its products drop to
 // three.
 //
-// One CTA computes one 128 x 128 tile of C over the whole K range, 64 K per
-// stage, two stages: all 256 threads load a stage from global memory, split
+// One CTA computes one 128 x 128 tile of C over the whole K range, 32 K per
+// stage, two stages (96 KB of shared memory: two CTAs per SM): all 256
+// threads load a stage from global memory, split
 // it and store the BF16 terms into shared memory in the canonical K-major
 // layout (8 x 8 core matrices, no swizzle); one thread issues the tcgen05.mma
 // instructions of the stage and commits them to the stage's mbarrier, which
@@ -33,7 +34,7 @@ namespace hssmf {
 
 namespace {
 
-constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
+constexpr int TC_M = 128, TC_N = 128, TC_K = 32;
 constexpr int TC_THREADS = 256;
 constexpr int TC_TERM_BYTES = TC_M * TC_K * 2;          // one BF16 term of one operand tile
 constexpr int TC_STAGE_BYTES = 6 * TC_TERM_BYTES;       // 3 terms of A, 3 terms of B
@@ -46,19 +47,20 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Byte offset of element (r, k) of a 128 x 64 K-major BF16 tile: core
-// matrices of 8 rows x 16 bytes stored contiguously (128 B), the 8 core
-// matrices along K of a row group adjacent (leading byte offset 128 B), row
-// groups 1024 B apart (stride byte offset).
+// Byte offset of element (r, k) of a 128 x TC_K K-major BF16 tile: core
+// matrices of 8 rows x 16 bytes stored contiguously (128 B), the TC_K / 8
+// core matrices along K of a row group adjacent (leading byte offset 128 B),
+// row groups TC_SBO bytes apart (stride byte offset).
+constexpr int TC_SBO = TC_K / 8 * 128;
 __device__ __forceinline__ int tile_off(int r, int k) {
-  return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+  return (r >> 3) * TC_SBO + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
 // tcgen05 shared-memory matrix descriptor, no swizzle: start address,
-// leading byte offset 128, stride byte offset 1024, descriptor version 1.
+// leading byte offset 128, stride byte offset TC_SBO, descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) |
-         ((uint64_t)(1024 >> 4) << 32) | (1ull << 46);
+         ((uint64_t)(TC_SBO >> 4) << 32) | (1ull << 46);
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
@@ -144,17 +146,19 @@ __device__ __forceinline__ void split8(const float* x, int nt, uint4* t0, uint4*
   }
 }
 
-// Loads rows [r0, r0 + 128) x K range [k0, k0 + 64) of an operand whose
+// Loads rows [r0, r0 + 128) x K range [k0, k0 + TC_K) of an operand whose
 // element (r, k) sits at P[r * sr + k * sk] (one of sr, sk is 1; rc = rows
 // contiguous), rows < R and k < K valid: k beyond K is stored as zero, rows
 // beyond R are not written (their products land in output rows or columns
-// that are never stored).  Each thread handles 4 chunks of 8 consecutive k of
-// one row; lanes walk the contiguous direction of the operand.
+// that are never stored).  Each thread handles TC_K / 16 chunks of 8
+// consecutive k of one row; lanes walk the contiguous direction of the
+// operand.
 __device__ __forceinline__ void load_tile(const float* __restrict__ P, long long sr, long long sk,
                                           bool rc, int r0, int R, int k0, int K, int nt,
                                           char* dst) {
+  static_assert(TC_K == 32 || TC_K == 64, "stage depth");
 #pragma unroll
-  for (int q4 = 0; q4 < 4; ++q4) {
+  for (int q4 = 0; q4 < TC_M * TC_K / 8 / TC_THREADS; ++q4) {
     const int q = threadIdx.x + TC_THREADS * q4;
     // rows contiguous: 32 consecutive rows per warp, same k chunk;
     // k contiguous: 8 rows x 4 chunks per warp (one row group per store phase)
@@ -178,7 +182,7 @@ __device__ __forceinline__ void load_tile(const float* __restrict__ P, long long
   }
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(const GemmJob* __restrict__ jobs,
+__global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __restrict__ jobs,
                                                            const Tile* __restrict__ tiles,
                                                            unsigned* __restrict__ status) {
   extern __shared__ char smem_raw[];

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "hss_kernels.h"
 
@@ -953,6 +954,360 @@ int HssKern<T>::batched_id_smem(const IdJob* jobs, int njobs, int max_m, int max
     case 4: return launch_id_smem<T, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
     case 8: return launch_id_smem<T, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
     case 16: return launch_id_smem<T, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    default: return -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same ID (FP32) with the matrix held in registers, for nodes with
+// d <= 32 RPL rows and m <= RR_NW CPW CL columns.  CTA r of a cluster of CL
+// owns the columns j = r (mod CL); warp w owns local columns w + RR_NW c
+// (c < CPW) and lane l holds rows l + 32 s (s < RPL) of each of them, so the
+// per-step Householder update touches no shared memory.  Per step:
+//   - every warp proposes its largest trailing norm (the norms sit in every
+//     lane after the shuffle reductions), one barrier, then every warp
+//     reduces the proposals itself (and, in a cluster, the CTA proposals
+//     exchanged through distributed shared memory) and takes the same
+//     decision: FP64 rank rule |R_ii|^2 <= eps^2 |R_11|^2 on the FP32 norms;
+//   - the owner warp of the pivot column writes the Householder vector to
+//     shared memory (peers in a cluster copy it with 16-byte DSMEM loads);
+//   - every warp applies the reflector to its unpivoted columns and
+//     recomputes their norms from the trailing rows.
+// R stays in place (columns are never moved); at the end the owned columns
+// go to the job's W array, and X = R1^-1 R2 is formed as in the cluster
+// kernels.
+// ---------------------------------------------------------------------------
+constexpr int RR_THREADS = 512;
+constexpr int RR_NW = RR_THREADS / 32;
+
+// Column of the CPW held by a warp whose total lane l holds after rr_reduce,
+// and the first lane holding the total of column c.
+template <int CPW>
+__device__ __forceinline__ int rr_col_of_lane(int lane) {
+  static_assert(CPW == 4 || CPW == 8, "4 or 8 columns per warp");
+  return CPW == 8 ? (((lane >> 4) & 1) << 2) | (((lane >> 3) & 1) << 1) | ((lane >> 2) & 1)
+                  : (((lane >> 4) & 1) << 1) | ((lane >> 3) & 1);
+}
+template <int CPW>
+__device__ __forceinline__ int rr_lane_of_col(int c) {
+  return CPW == 8 ? (((c >> 2) & 1) << 4) | (((c >> 1) & 1) << 3) | ((c & 1) << 2)
+                  : (((c >> 1) & 1) << 4) | ((c & 1) << 3);
+}
+
+// Warp sums of CPW per-lane values by a butterfly that hands half of the
+// values to the partner at each of the first log2(CPW) levels: CPW - 1 +
+// log2(32 / CPW) shuffles instead of 5 CPW.  Lane l returns the total of
+// column rr_col_of_lane(l).
+template <int CPW>
+__device__ __forceinline__ float rr_reduce(float (&y)[CPW], int lane) {
+#pragma unroll
+  for (int h = CPW / 2, off = 16; h >= 1; h >>= 1, off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int q = 0; q < h; ++q) {
+      const float send = up ? y[q] : y[q + h];
+      const float keep = up ? y[q + h] : y[q];
+      y[q] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  float t = y[0];
+#pragma unroll
+  for (int off = 16 / CPW; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  return t;
+}
+
+// Largest value, then smallest index, over the lanes (offsets from 16 down to lo).
+__device__ __forceinline__ void rr_argmax(float& b, int& p, int lo = 1) {
+#pragma unroll
+  for (int o = 16; o >= lo; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, b, o);
+    const int op = __shfl_xor_sync(0xffffffffu, p, o);
+    if (ov > b || (ov == b && op < p)) { b = ov; p = op; }
+  }
+}
+
+template <int RPL, int CPW, int CL>
+__global__ void __launch_bounds__(RR_THREADS, 1) k_cpqr_id_rr(const IdJob* __restrict__ jobs, double eps,
+                                                            double* rdiag_all, int* order_all, int max_m,
+                                                            int max_k) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  constexpr int DMAX = 32 * RPL;
+  const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
+  const int jid = blockIdx.x / CL;
+  const IdJob jb = jobs[jid];
+  const int d = jb.d, m = jb.m;
+  const long long ld = d;
+  const float* Y = (const float*)jb.Y;
+  float* W = (float*)jb.W;
+  double* rdiag = rdiag_all + (long long)jid * max_k;
+  int* order = order_all + (long long)jid * max_m;
+  __shared__ __align__(16) float s_v[DMAX];   // Householder vector of the step (owner CTA)
+  __shared__ __align__(16) float s_vl[DMAX];  // its copy in every CTA of a cluster
+  __shared__ float s_wv[RR_NW];
+  __shared__ int s_wj[RR_NW];
+  __shared__ float s_cv, s_tau, s_taul;
+  __shared__ int s_cj;
+  extern __shared__ unsigned char skel[];  // m flags for the epilogue
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int mycol = rr_col_of_lane<CPW>(lane);
+  const int myj = rank + CL * (wid + RR_NW * mycol);
+
+  float a[CPW][RPL];
+  unsigned act = 0;  // bit c: column c of this warp exists and is not pivoted
+  float y[CPW];
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) {
+    const int j = rank + CL * (wid + RR_NW * c);
+    if (j < m) act |= 1u << c;
+    float s2 = 0.f;
+#pragma unroll
+    for (int s = 0; s < RPL; ++s) {
+      const int r = lane + 32 * s;
+      a[c][s] = (j < m && r < d) ? Y[r + (long long)j * ld] : 0.f;
+      s2 += a[c][s] * a[c][s];
+    }
+    y[c] = s2;
+  }
+  float cnl = rr_reduce<CPW>(y, lane);  // trailing norm^2 of column mycol
+  if (!((act >> mycol) & 1)) cnl = -1.f;
+  // |R_11|^2 = the largest initial norm^2; thr = eps^2 |R_11|^2 computed in
+  // FP64 and rounded down to FP32, so that for every FP32 b, b > thr iff
+  // b > eps^2 |R_11|^2 exactly (no FP64 work inside the step loop)
+  float thr;
+  {
+    float bv = cnl;
+    int bj = cnl >= 0.f ? myj : m;
+    rr_argmax(bv, bj, 32 / CPW);
+    if (lane == 0) s_wv[wid] = bv;
+    __syncthreads();
+    float b = lane < RR_NW ? s_wv[lane] : -1.f;
+    rr_argmax(b, bj);
+    if (CL > 1) {
+      if (threadIdx.x == 0) s_cv = b;
+      cluster.sync();
+      b = lane < CL ? *cluster.map_shared_rank(&s_cv, lane) : -1.f;
+      rr_argmax(b, bj);
+      cluster.sync();  // s_cv is rewritten in the first step
+    } else {
+      __syncthreads();
+    }
+    thr = __double2float_rd(eps * eps * (double)fmaxf(b, 0.f));
+  }
+  const int kmax = min(d, m);
+  int k = kmax;
+  for (int i = 0; i < kmax; ++i) {
+    {  // proposal of this warp
+      float bv = cnl;
+      int bj = cnl >= 0.f ? myj : m;
+      rr_argmax(bv, bj, 32 / CPW);
+      if (lane == 0) { s_wv[wid] = bv; s_wj[wid] = bj; }
+    }
+    __syncthreads();
+    float b = lane < RR_NW ? s_wv[lane] : -1.f;
+    int p = lane < RR_NW ? s_wj[lane] : m;
+    rr_argmax(b, p);
+    if (CL > 1) {
+      if (threadIdx.x == 0) { s_cv = b; s_cj = p; }
+      cluster.sync();
+      b = -1.f;
+      p = m;
+      if (lane < CL) {
+        b = *cluster.map_shared_rank(&s_cv, lane);
+        p = *cluster.map_shared_rank(&s_cj, lane);
+      }
+      rr_argmax(b, p);
+    }
+    // the decision, identical in every warp of every CTA (same inputs)
+    const bool stop = (i == 0 ? !(b > 0.f) : !(b > thr)) || p >= m;
+    if (stop) {
+      k = i;
+      break;
+    }
+    const float nrm = sqrtf(b);
+    const int powner = p % CL, pl = p / CL, pw = pl % RR_NW, pc = pl / RR_NW;
+    if (rank == powner && wid == pw) {
+      float col[RPL];
+#pragma unroll
+      for (int s = 0; s < RPL; ++s) {
+        float x = 0.f;
+#pragma unroll
+        for (int c = 0; c < CPW; ++c)
+          if (c == pc) x = a[c][s];
+        col[s] = x;
+      }
+      const int si = i >> 5;
+      float xi = 0.f;
+#pragma unroll
+      for (int s = 0; s < RPL; ++s)
+        if (s == si) xi = col[s];
+      const float alpha = __shfl_sync(0xffffffffu, xi, i & 31);
+      const float beta = alpha >= 0.f ? -nrm : nrm;
+      const float scl = __frcp_rn(alpha - beta);
+#pragma unroll
+      for (int s = 0; s < RPL; ++s) {
+        const int r = lane + 32 * s;
+        s_v[r] = r > i ? col[s] * scl : (r == i ? 1.f : 0.f);
+      }
+      if (lane == 0) {
+        s_tau = (beta - alpha) * __frcp_rn(beta);
+        rdiag[i] = (double)beta;
+        order[i] = p;
+      }
+      act &= ~(1u << pc);  // the pivot column leaves the active set
+      if (mycol == pc) cnl = -1.f;
+    }
+    const float* vv = s_v;
+    float tau;
+    if (CL == 1) {
+      __syncthreads();
+      tau = s_tau;
+    } else {
+      cluster.sync();
+      const float4* src = reinterpret_cast<const float4*>(cluster.map_shared_rank(s_v, powner));
+      float4* dst = reinterpret_cast<float4*>(s_vl);
+      for (int q = threadIdx.x; q < DMAX / 4; q += RR_THREADS) dst[q] = src[q];
+      if (threadIdx.x == 0) s_taul = *cluster.map_shared_rank(&s_tau, powner);
+      __syncthreads();
+      vv = s_vl;
+      tau = s_taul;
+    }
+    float vr[RPL];
+#pragma unroll
+    for (int s = 0; s < RPL; ++s) vr[s] = vv[lane + 32 * s];
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      float t = 0.f;
+#pragma unroll
+      for (int s = 0; s < RPL; ++s) t += vr[s] * a[c][s];
+      y[c] = t;
+    }
+    const float dt = rr_reduce<CPW>(y, lane);
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      const float dc = __shfl_sync(0xffffffffu, dt, rr_lane_of_col<CPW>(c));
+      const float f = ((act >> c) & 1) ? tau * dc : 0.f;
+      float t = 0.f;
+#pragma unroll
+      for (int s = 0; s < RPL; ++s) {
+        a[c][s] -= f * vr[s];
+        if (lane + 32 * s > i) t += a[c][s] * a[c][s];
+      }
+      y[c] = t;
+    }
+    const float nt = rr_reduce<CPW>(y, lane);
+    if ((act >> mycol) & 1) cnl = nt;
+  }
+  // publish the owned columns (R rows in place) for the back substitution
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) {
+    const int j = rank + CL * (wid + RR_NW * c);
+    if (j < m) {
+#pragma unroll
+      for (int s = 0; s < RPL; ++s) {
+        const int r = lane + 32 * s;
+        if (r < d) W[r + (long long)j * ld] = a[c][s];
+      }
+    }
+  }
+  // every CTA has left the loop (no DSMEM reads remain) and every column,
+  // rdiag and order entry is visible to the whole cluster
+  if (CL > 1) cluster.sync(); else __syncthreads();
+  for (int j = threadIdx.x; j < m; j += RR_THREADS) skel[j] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < k; t += RR_THREADS) skel[order[t]] = 1;
+  __syncthreads();
+  const double* rd = rdiag;
+  float* X = (float*)jb.X;
+  const int mo = (m - rank + CL - 1) / CL;
+  for (int g = wid; 4 * g < mo; g += RR_NW) {  // up to 4 owned non-skeleton columns per warp
+    int ls[4];
+    int nc = 0;
+    for (int q = 0; q < 4; ++q) {
+      const int l = 4 * g + q;
+      if (l < mo && !skel[rank + CL * l]) ls[nc++] = l;
+    }
+    if (nc == 0) continue;
+    for (int q = nc; q < 4; ++q) ls[q] = ls[0];
+    float* b0 = W + (rank + CL * ls[0]) * ld;
+    float* b1 = W + (rank + CL * ls[1]) * ld;
+    float* b2 = W + (rank + CL * ls[2]) * ld;
+    float* b3 = W + (rank + CL * ls[3]) * ld;
+    warp_backsub4<float>(b0, b1, b2, b3, nc, k, [&](int c) { return (const float*)(W + (long long)order[c] * ld); },
+                         [&](int c) { return (float)rd[c]; }, lane);
+    for (int q = 0; q < nc; ++q) {
+      const int j = rank + CL * ls[q];
+      int pos = 0;  // number of non-skeleton columns before j
+      for (int c = lane; c < j; c += 32) pos += skel[c] ? 0 : 1;
+      for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+      for (int r = lane; r < k; r += 32) X[r + (long long)pos * k] = W[r + j * ld];
+      if (lane == 0) jb.piv[k + pos] = j;
+    }
+  }
+  if (rank == 0) {
+    for (int t = threadIdx.x; t < k; t += RR_THREADS) jb.piv[t] = order[t];
+    if (threadIdx.x == 0) *jb.rank = k;
+  }
+}
+
+template <int RPL, int CPW, int CL>
+static int launch_id_rr(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
+                        int* order, cudaStream_t s) {
+  if (max_d > 32 * RPL || max_m > RR_NW * CPW * CL) return -1;
+  static bool attr = false;
+  if (!attr) {
+    if (CL > 8) cudaFuncSetAttribute(k_cpqr_id_rr<RPL, CPW, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaGetLastError();
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * CL, 1, 1);
+  cfg.blockDim = dim3(RR_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)std::max(max_m, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const int max_k = std::max(std::min(max_m, max_d), 1);
+  if (cudaLaunchKernelEx(&cfg, k_cpqr_id_rr<RPL, CPW, CL>, jobs, eps, rdiag, order, std::max(max_m, 1), max_k) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  count_launch();
+  return 0;
+}
+
+template <typename T>
+int HssKern<T>::id_rr_config(int d, int m) {
+  if (!std::is_same<T, float>::value) return 0;
+  for (int cl = 1; cl <= 16; cl *= 2) {
+    if (d <= 256 && m <= RR_NW * 8 * cl) return cl;        // 8 rows x 8 columns per lane
+    if (d <= 512 && m <= RR_NW * 4 * cl) return 32 + cl;   // 16 rows x 4 columns per lane
+  }
+  return 0;
+}
+
+template <typename T>
+int HssKern<T>::batched_id_rr(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
+                              int* order, int cfg, cudaStream_t s) {
+  if (njobs <= 0) return 0;
+  if (!std::is_same<T, float>::value) return -1;
+  switch (cfg) {
+    case 1: return launch_id_rr<8, 8, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 2: return launch_id_rr<8, 8, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 4: return launch_id_rr<8, 8, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 8: return launch_id_rr<8, 8, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 16: return launch_id_rr<8, 8, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 33: return launch_id_rr<16, 4, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 34: return launch_id_rr<16, 4, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 36: return launch_id_rr<16, 4, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 40: return launch_id_rr<16, 4, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 48: return launch_id_rr<16, 4, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
     default: return -1;
   }
 }

@@ -215,7 +215,7 @@ hssmf_status hssmf_ctx::build_plan() {
         j.beta = 1.0;
         int jid = (int)jobs.size();
         jobs.push_back(j);
-        int t = ceil_div(M, fp32 ? GEMM_TILE_TC : GEMM_TILE);  // FP32: tensor-core tiles
+        int t = ceil_div(M, GEMM_TILE);
         for (int tn = 0; tn < t; ++tn)
           for (int tm = 0; tm < t; ++tm) tiles.push_back(Tile{jid, tm, tn});
       }
@@ -309,10 +309,7 @@ hssmf_status hssmf_ctx::factor_impl() {
     for (const StepPlan& sp : L.steps) {
       Kern<T>::panel_lu(ds, ar, d_piv, d_flist + L.dense_off, L.ndense, sp.k0, NB, d_status, stream);
       Kern<T>::panel_trsm(ds, ar, d_flist + L.dense_off, L.ndense, sp.k0, NB, sp.trsm_chunks, stream);
-      if (std::is_same<T, float>::value)
-        gemm_tc(d_jobs, d_tiles + sp.tile_off, sp.ntiles, d_status, stream);
-      else
-        Kern<T>::gemm(d_jobs, d_tiles + sp.tile_off, sp.ntiles, stream);
+      Kern<T>::gemm(d_jobs, d_tiles + sp.tile_off, sp.ntiles, stream);  // K = NB: CUDA cores
     }
     for (int f : L.dense) {
       double ns = fronts_host[f].ns, nu = fronts_host[f].nu;
@@ -820,7 +817,10 @@ static hssmf_status batched_id_impl(int njobs, const void* Y, const long long* y
   }
   cudaMemcpyAsync(dj, jobs.data(), sizeof(IdJob) * njobs, cudaMemcpyHostToDevice, s);
   int r;
-  if (use_cluster < 0) {  // shared-memory-resident matrices on a cluster sized for the largest job
+  if (use_cluster == -2) {  // register-resident matrices (FP32) on a cluster sized for the largest job
+    const int cfg = HssKern<T>::id_rr_config(max_d, max_m);
+    r = cfg > 0 ? HssKern<T>::batched_id_rr(dj, njobs, max_m, max_d, eps, rdiag, order, cfg, s) : -1;
+  } else if (use_cluster < 0) {  // shared-memory-resident matrices on a cluster sized for the largest job
     const int cl = HssKern<T>::id_smem_cluster_size(max_d, max_m);
     r = cl > 0 ? HssKern<T>::batched_id_smem(dj, njobs, max_m, max_d, eps, rdiag, order, cl, s) : -1;
   } else if (use_cluster > 0) {
@@ -854,6 +854,14 @@ hssmf_status hssmf_get_phase_times(const hssmf_ctx* c, double* ms, int n) {
   if (!c || !ms || n < 0) return HSSMF_ERR_ARG;
   for (int i = 0; i < n && i < PH_COUNT; ++i) ms[i] = c->prof.ms[i];
   return HSSMF_OK;
+}
+
+int hssmf_get_id_trace(const hssmf_ctx* c, int* rec, int max_records) {
+  if (!c) return -1;
+  const int n = (int)(c->id_trace.size() / 9);
+  if (rec)
+    for (int i = 0; i < std::min(n, max_records) * 9; ++i) rec[i] = c->id_trace[i];
+  return n;
 }
 
 hssmf_status hssmf_set_profiling(hssmf_ctx* c, int on) {

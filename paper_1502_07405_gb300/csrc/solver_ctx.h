@@ -143,6 +143,9 @@ struct hssmf_ctx {
   // HSS-front state
   hssmf::HssState* hss = nullptr;
   hssmf::PhaseProf prof;
+  // per-node ID records of the last factor (profiling on): front, node, round,
+  // d, m, mc, kr, kc, accepted
+  std::vector<int> id_trace;
 
   hssmf_status fail(hssmf_status st, const std::string& msg);
   hssmf_status cuda_check(cudaError_t e, const char* what);

@@ -49,9 +49,11 @@ def _decaying(d, m, rank_scale, seed):
     return (Q1 * s) @ Q2.T
 
 
-@pytest.mark.parametrize("cluster", [0, 1, -1])
+@pytest.mark.parametrize("cluster", [0, 1, -1, -2])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_batched_id_matches_oracle(cluster, prec):
+    if cluster == -2 and prec == 0:
+        pytest.skip("register-resident kernel is FP32 only")
     shapes = [(128, 128), (192, 128), (256, 300), (96, 700), (300, 64)]
     Ys = [_decaying(d_, m_, 12.0, i) for i, (d_, m_) in enumerate(shapes)]
     eps = 1e-6 if prec == 0 else 1e-4
@@ -82,4 +84,42 @@ def test_batched_id_exact_low_rank_and_zero(cluster):
     U[piv[:9], :] = np.eye(9)
     U[piv[9:], :] = Xg.T
     assert np.linalg.norm(Y1[:, piv[:9]] @ U.T - Y1) <= 1e-12 * np.linalg.norm(Y1)
+    assert res[1][0] == 0
+
+
+@pytest.mark.parametrize("shapes", [
+    [(128, 128), (192, 100), (64, 7)],          # 8 rows x 8 columns per lane, one CTA
+    [(256, 256), (200, 250), (250, 33)],        # cluster of 2
+    [(256, 2000), (130, 1500)],                 # cluster of 16
+    [(320, 64), (512, 60), (300, 17)],          # 16 rows x 4 columns per lane, one CTA
+    [(512, 1000), (400, 700), (257, 300)],      # 16 rows per lane, cluster of 16
+])
+def test_register_resident_id_shapes(shapes):
+    Ys = [_decaying(d_, m_, 9.0, 7 + i) for i, (d_, m_) in enumerate(shapes)]
+    eps = 1e-4
+    res = _run_ids(Ys, eps, 1, -2)
+    for Y, (k, piv, Xg) in zip(Ys, res):
+        ko, pivo, Ro = hss.cpqr_rank(Y, eps)
+        assert abs(k - ko) <= 1
+        kk = min(k, ko)
+        assert np.array_equal(piv[:kk], pivo[:kk])
+        assert sorted(piv.tolist()) == list(range(Y.shape[1]))
+        U = np.zeros((Y.shape[1], k))
+        U[piv[:k], :] = np.eye(k)
+        U[piv[k:], :] = Xg.T
+        err = np.linalg.norm(Y[:, piv[:k]] @ U.T - Y) / np.linalg.norm(Y)
+        assert err <= 50 * eps
+
+
+def test_register_resident_id_exact_low_rank_and_zero():
+    rng = np.random.default_rng(6)
+    Y1 = rng.standard_normal((200, 9)) @ rng.standard_normal((9, 500))
+    Y2 = np.zeros((64, 80))
+    res = _run_ids([Y1, Y2], 1e-5, 1, -2)
+    k, piv, Xg = res[0]
+    assert k == 9
+    U = np.zeros((500, 9))
+    U[piv[:9], :] = np.eye(9)
+    U[piv[9:], :] = Xg.T
+    assert np.linalg.norm(Y1[:, piv[:9]] @ U.T - Y1) <= 1e-5 * np.linalg.norm(Y1)
     assert res[1][0] == 0
