@@ -127,8 +127,9 @@ struct NodeRt {
   // per round
   void *Yr = nullptr, *Yc = nullptr, *Srp = nullptr, *Scp = nullptr, *Rrp = nullptr, *Rcp = nullptr;
   // factor
-  void *Uexp = nullptr, *Vexp = nullptr, *Dt = nullptr, *Vt = nullptr, *tau = nullptr;
+  void *Uexp = nullptr, *Vexp = nullptr, *Dt = nullptr, *Vt = nullptr, *tau = nullptr, *Tq = nullptr;
   int* lupiv = nullptr;
+  int* luperm = nullptr;
   void *Ubig = nullptr, *Vbig = nullptr;
   // solve scratch
   void *bt = nullptr, *bo = nullptr, *w = nullptr, *x = nullptr;
@@ -786,13 +787,14 @@ void ulv_solve(Ctx<T>& X, const std::vector<FrontRt*>& fs, const std::vector<con
                const std::vector<long long>& ldin, const std::vector<T*>& xout,
                const std::vector<long long>& ldout, const std::vector<int>& nrhs, Pool& pool) {
   const Symbolic& S = X.c.sym;
-  int maxh = 0, maxnr = 1;
+  int maxh = 0, maxnr = 1, maxm = 1;
   for (size_t i = 0; i < fs.size(); ++i) {
     FrontRt& F = *fs[i];
     maxh = std::max(maxh, F.height[F.k]);
     maxnr = std::max(maxnr, nrhs[i]);
     for (int t : F.f11) {
       NodeRt& N = F.nd[t];
+      maxm = std::max(maxm, N.m);
       N.bt = X.A(pool, (long long)N.m * nrhs[i]);
       N.bo = X.A(pool, (long long)N.m * nrhs[i]);
       N.w = X.A(pool, (long long)std::max(N.kc, 1) * nrhs[i]);
@@ -812,7 +814,7 @@ void ulv_solve(Ctx<T>& X, const std::vector<FrontRt*>& fs, const std::vector<con
         std::memset(&j, 0, sizeof(j));
         j.Dt = N.Dt;
         j.is_root = t == F.k;
-        j.piv = j.is_root ? N.lupiv : N.piv_r;
+        j.piv = j.is_root ? N.luperm : N.piv_r;
         j.X = N.Xr;
         j.Vt = N.Vt;
         j.leaf = tr.leaf(t);
@@ -846,7 +848,9 @@ void ulv_solve(Ctx<T>& X, const std::vector<FrontRt*>& fs, const std::vector<con
         jobs.push_back(j);
       }
     }
-    X.launch(jobs, [&](const UlvFwdJob* d, int n) { HssKern<T>::ulv_fwd(d, n, maxnr, X.s); });
+    X.launch(jobs, [&](const UlvFwdJob* d, int n) {
+      if (HssKern<T>::ulv_fwd(d, n, maxnr, maxm, X.s) < 0) X.oom = true;
+    });
   }
   for (int lv = maxh; lv >= 0; --lv) {
     std::vector<UlvBwdJob> jobs;
@@ -867,7 +871,7 @@ void ulv_solve(Ctx<T>& X, const std::vector<FrontRt*>& fs, const std::vector<con
         UlvBwdJob j;
         std::memset(&j, 0, sizeof(j));
         j.Dt = N.Dt;
-        j.tau = N.tau;
+        j.Tq = N.Tq;
         j.x1 = N.bo;
         j.xh2 = xpar + off;
         j.ldxh2 = PN.m;
@@ -885,7 +889,9 @@ void ulv_solve(Ctx<T>& X, const std::vector<FrontRt*>& fs, const std::vector<con
       }
     }
     X.flush_copy();
-    X.launch(jobs, [&](const UlvBwdJob* d, int n) { HssKern<T>::ulv_bwd(d, n, maxnr, X.s); });
+    X.launch(jobs, [&](const UlvBwdJob* d, int n) {
+      if (HssKern<T>::ulv_bwd(d, n, maxnr, maxm, X.s) < 0) X.oom = true;
+    });
   }
 }
 
@@ -965,7 +971,8 @@ hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       if (t == F.k) {
         N.Dt = Dm[i];
         N.lupiv = X.I(H.fac, m);
-        if (m > 0) lu.push_back(LuJob{N.Dt, N.lupiv, m, 0});
+        N.luperm = X.I(H.fac, m);
+        if (m > 0) lu.push_back(LuJob{N.Dt, N.lupiv, N.luperm, m, 0});
         continue;
       }
       N.Dt = X.A(H.fac, (long long)m * m);
@@ -1017,8 +1024,8 @@ hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       N.tau = X.A(H.fac, std::max(N.m - N.kr, 1));
       if (N.m - N.kr <= 0) continue;
       T* Vb = X.A(H.lvl, (long long)NBQ * N.m);
-      T* Tb = X.A(H.lvl, NBQ * NBQ);
-      lq.push_back(LqJob{N.Dt, N.Vt, N.tau, Vb, Tb, N.m, N.kr, N.kc, 0});
+      N.Tq = X.A(H.fac, (long long)NBQ * NBQ * ceil_div(N.m - N.kr, NBQ));
+      lq.push_back(LqJob{N.Dt, N.Vt, N.tau, Vb, N.Tq, N.m, N.kr, N.kc, 0});
       W1.push_back(X.A(H.lvl, (long long)N.m * NBQ));
       W2.push_back(X.A(H.lvl, (long long)N.m * NBQ));
       Z1.push_back(X.A(H.lvl, (long long)NBQ * std::max(N.kc, 1)));
@@ -1044,8 +1051,9 @@ hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         const int nk = J.m - J.k;
         if (j0 >= nk) continue;
         const int j1 = std::min(j0 + NBQ, nk), w = j1 - j0, rows = J.m - j1;
-        X.gemm(W1[q], J.m, 0, J.Tb, NBQ, 0, W2[q], J.m, rows, w, w, 1.0, 0.0);
-        X.gemm(J.Tb, NBQ, 1, Z1[q], NBQ, 0, Z2[q], NBQ, w, J.kc, w, 1.0, 0.0);
+        const T* Tb = (const T*)J.Tb + (long long)(j0 / NBQ) * NBQ * NBQ;
+        X.gemm(W1[q], J.m, 0, Tb, NBQ, 0, W2[q], J.m, rows, w, w, 1.0, 0.0);
+        X.gemm(Tb, NBQ, 1, Z1[q], NBQ, 0, Z2[q], NBQ, w, J.kc, w, 1.0, 0.0);
       }
       X.flush_gemm();
       for (size_t q = 0; q < lq.size(); ++q) {
@@ -1077,6 +1085,7 @@ hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       }
       X.flush_gemm();
     }
+    X.launch(lu, [&](const LuJob* d, int n) { HssKern<T>::lu_perm(d, n, X.s); });
   }
   if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during the ULV factorization");
   c.prof.mark(PH_SCHUR, X.s);

@@ -71,13 +71,14 @@ struct LqJob {  // LQ of the top m-k rows of Dt (m x m): Dt <- Dt Q, V <- Q^T V;
   void* V;
   void* tau;
   void* Vb;  // blocked form: panel reflectors (nb x m, ld nb) and their T (nb x nb)
-  void* Tb;
+  void* Tb;  // T of panel b at Tb + b nb^2 (kept for the solve)
   int m, k, kc, pad;
 };
 
 struct LuJob {  // in-place partial-pivoting LU of A (m x m, ld m)
   void* A;
   int* piv;
+  int* perm;  // after the factorization: row i of P A is row perm[i] of A
   int m, pad;
 };
 
@@ -106,12 +107,13 @@ struct UlvFwdJob {
   long long ldbsrc;
   int m, k, kc, mc, k1, k2, kc1, kc2, leaf, is_root, ldbh1, ldbh2, nrhs, pad;
 };
+// (root: piv holds the row permutation of the LU, row i of P b is b[piv[i]])
 
 // Backward ULV step: x_t = Q [x1; xhat2] with Q the product of the LQ
 // reflectors stored in the rows of Dt; x1 = bo[0:m-k] of the forward job.
 struct UlvBwdJob {
   const void* Dt;
-  const void* tau;
+  const void* Tq;   // T of each 32-reflector panel (32 x 32, upper), panel b at Tq + 1024 b
   const void* x1;   // (m - k) x nrhs, ld m
   const void* xh2;  // k x nrhs, ld ldxh2 (slice of the parent's x)
   void* out;        // m x nrhs, ld ldout
@@ -147,7 +149,6 @@ struct HssKern {
   static int batched_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
                              int* order, int cl, cudaStream_t s);
   static void basis(const BasisJob* jobs, int njobs, cudaStream_t s);
-  static void lq(const LqJob* jobs, int njobs, cudaStream_t s);
   static void lu(const LuJob* jobs, int njobs, unsigned* status, cudaStream_t s);
   // Blocked LQ, panel of rows [j0, j0 + nb) of every job with m - k > j0:
   // reflectors of the panel rows (applied inside the panel), the block
@@ -158,8 +159,11 @@ struct HssKern {
   // then the row block of U right of the panel.
   static void lu_panel(const LuJob* jobs, int njobs, int k0, int nb, unsigned* status, cudaStream_t s);
   static void lu_trsm(const LuJob* jobs, int njobs, int k0, int nb, int max_m, cudaStream_t s);
-  static void ulv_fwd(const UlvFwdJob* jobs, int njobs, int max_nrhs, cudaStream_t s);
-  static void ulv_bwd(const UlvBwdJob* jobs, int njobs, int max_nrhs, cudaStream_t s);
+  // row permutation of each finished LU from its interchanges
+  static void lu_perm(const LuJob* jobs, int njobs, cudaStream_t s);
+  // max_m bounds the node sizes (shared-memory vectors); -1 if too large
+  static int ulv_fwd(const UlvFwdJob* jobs, int njobs, int max_nrhs, int max_m, cudaStream_t s);
+  static int ulv_bwd(const UlvBwdJob* jobs, int njobs, int max_nrhs, int max_m, cudaStream_t s);
 };
 
 }  // namespace hssmf

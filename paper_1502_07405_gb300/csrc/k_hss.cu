@@ -29,14 +29,16 @@ __device__ __forceinline__ double wsum<double>(double v) { return warp_sum(v); }
 template <>
 __device__ __forceinline__ float wsum<float>(float v) { return warp_sumf(v); }
 
-// block-wide sum of a double, result in every thread (blockDim multiple of 32)
-__device__ double block_sum_d(double v, double* sh) {
-  v = warp_sum(v);
+
+// block-wide sum in T, result in every thread (sh: 32 T)
+template <typename T>
+__device__ T block_sum_t(T v, T* sh) {
+  v = wsum<T>(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
   if (lane == 0) sh[wid] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = T(0);
   for (int w = 0; w < nw; ++w) s += sh[w];
   __syncthreads();
   return s;
@@ -1337,71 +1339,6 @@ void HssKern<T>::basis(const BasisJob* jobs, int njobs, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// LQ of the top m - k rows of Dt (Section 2.3 ULV step): Householder
-// reflectors H_i from the rows (LAPACK larfg convention, v stored in the
-// zeroed part of row i), applied from the right to the rows below and from
-// the left to V.  One CTA per job.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_lq(const LqJob* __restrict__ jobs) {
-  const LqJob jb = jobs[blockIdx.x];
-  const int m = jb.m, nk = jb.m - jb.k, kc = jb.kc;
-  T* D = (T*)jb.Dt;
-  T* V = (T*)jb.V;
-  T* tau = (T*)jb.tau;
-  __shared__ double sh[33];
-  for (int i = 0; i < nk; ++i) {
-    double part = 0.0;
-    for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) {
-      double v = (double)D[i + (long long)c * m];
-      part += v * v;
-    }
-    const double xn2 = block_sum_d(part, sh);
-    const T alpha = D[i + (long long)i * m];
-    T t = T(0), beta = alpha, scl = T(0);
-    if (xn2 > 0.0) {
-      double b = sqrt((double)alpha * (double)alpha + xn2);
-      beta = alpha >= T(0) ? T(-b) : T(b);
-      t = (beta - alpha) / beta;
-      scl = T(1) / (alpha - beta);
-    }
-    __syncthreads();
-    for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) D[i + (long long)c * m] *= scl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      D[i + (long long)i * m] = beta;
-      tau[i] = t;
-    }
-    if (t != T(0)) {
-      // rows r > i:  row_r[i:m] -= t (row_r[i:m] . v) v^T, v = [1, D[i, i+1:m]]
-      for (int r = i + 1 + threadIdx.x; r < m; r += blockDim.x) {
-        T s = D[r + (long long)i * m];
-        for (int c = i + 1; c < m; ++c) s += D[r + (long long)c * m] * D[i + (long long)c * m];
-        const T f = t * s;
-        D[r + (long long)i * m] -= f;
-        for (int c = i + 1; c < m; ++c) D[r + (long long)c * m] -= f * D[i + (long long)c * m];
-      }
-      // V rows i..m-1:  V -= t v (v^T V)
-      for (int c = threadIdx.x; c < kc; c += blockDim.x) {
-        T s = V[i + (long long)c * m];
-        for (int r = i + 1; r < m; ++r) s += D[i + (long long)r * m] * V[r + (long long)c * m];
-        const T f = t * s;
-        V[i + (long long)c * m] -= f;
-        for (int r = i + 1; r < m; ++r) V[r + (long long)c * m] -= f * D[i + (long long)r * m];
-      }
-    }
-    __syncthreads();
-  }
-}
-
-template <typename T>
-void HssKern<T>::lq(const LqJob* jobs, int njobs, cudaStream_t s) {
-  if (njobs <= 0) return;
-  k_lq<T><<<njobs, 256, 0, s>>>(jobs);
-  count_launch();
-}
-
-// ---------------------------------------------------------------------------
 // Blocked LQ, one panel of rows [j0, j1) per job (one CTA per job):
 // Householder reflectors of the panel rows (LAPACK larfg convention, v
 // stored in the zeroed part of its row, tau), applied to the panel rows
@@ -1419,8 +1356,8 @@ __global__ void __launch_bounds__(256) k_lq_panel(const LqJob* __restrict__ jobs
   T* D = (T*)jb.Dt;
   T* tau = (T*)jb.tau;
   T* Vb = (T*)jb.Vb;
-  T* Tb = (T*)jb.Tb;
-  __shared__ double sh[33];
+  T* Tb = (T*)jb.Tb + (long long)(j0 / nb) * nb * nb;  // T of this panel, kept for the solve
+  __shared__ T sh[33];
   __shared__ T sT[32][33];
   __shared__ T sg[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1431,11 +1368,11 @@ __global__ void __launch_bounds__(256) k_lq_panel(const LqJob* __restrict__ jobs
       part += v * v;
     }
     const T alpha = D[i + (long long)i * m];
-    const double xn2 = block_sum_d((double)part, sh);
+    const T xn2 = block_sum_t<T>(part, sh);
     T t = T(0), beta = alpha, scl = T(0);
-    if (xn2 > 0.0) {
-      double b = sqrt((double)alpha * (double)alpha + xn2);
-      beta = alpha >= T(0) ? T(-b) : T(b);
+    if (xn2 > T(0)) {
+      const T b = sqrt(alpha * alpha + xn2);
+      beta = alpha >= T(0) ? -b : b;
       t = (beta - alpha) / beta;
       scl = T(1) / (alpha - beta);
     }
@@ -1516,31 +1453,31 @@ __global__ void __launch_bounds__(256) k_lu_panel(const LuJob* __restrict__ jobs
   const int k1 = min(k0 + nb, m);
   T* A = (T*)jb.A;
   const long long ld = m;
-  __shared__ double s_v[8];
+  __shared__ T s_v[8];  // (comparisons of |a| are exact in T: same pivots as in FP64)
   __shared__ int s_i[8];
   __shared__ int s_p;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int j = k0; j < k1; ++j) {
-    double bv = -1.0;
+    T bv = T(-1);
     int bi = m;
     for (int r = j + threadIdx.x; r < m; r += blockDim.x) {
-      double a = fabs((double)A[r + j * ld]);
+      const T a = tabs(A[r + j * ld]);
       if (a > bv) { bv = a; bi = r; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      T ov = __shfl_down_sync(0xffffffffu, bv, o);
       int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
     }
     if (lane == 0) { s_v[wid] = bv; s_i[wid] = bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double b = s_v[0];
+      T b = s_v[0];
       int ix = s_i[0];
       for (int w2 = 1; w2 < (int)(blockDim.x >> 5); ++w2)
         if (s_v[w2] > b || (s_v[w2] == b && s_i[w2] < ix)) { b = s_v[w2]; ix = s_i[w2]; }
-      if (!(b > 0.0) || !isfinite(b)) {
-        atomicOr(status, b == 0.0 ? ST_ZERO_PIVOT : ST_NONFINITE);
+      if (!(b > T(0)) || !isfinite(b)) {
+        atomicOr(status, b == T(0) ? ST_ZERO_PIVOT : ST_NONFINITE);
         ix = j;
       }
       s_p = ix;
@@ -1611,75 +1548,90 @@ void HssKern<T>::lu_trsm(const LuJob* jobs, int njobs, int k0, int nb, int max_m
 }
 
 // ---------------------------------------------------------------------------
-// Small dense LU with partial pivoting (root of the F11 tree).  One CTA.
+// Blocked triangular sweeps on a shared-memory vector (one CTA), used by the
+// ULV solve: warp 0 solves each 32 x 32 diagonal block with the block's rows
+// in registers, then every thread updates the rows past the block with
+// coalesced column reads; two barriers per 32 columns.
 // ---------------------------------------------------------------------------
+// x[0:n] <- L^-1 x[0:n] (L = A(0:n, 0:n) lower, unit diagonal if unit), then
+// x[n:mt] -= A(n:mt, 0:n) x[0:n].
 template <typename T>
-__global__ void __launch_bounds__(256) k_lu_small(const LuJob* __restrict__ jobs, unsigned* status) {
-  const LuJob jb = jobs[blockIdx.x];
-  const int m = jb.m;
-  T* A = (T*)jb.A;
-  __shared__ double s_v[8];
-  __shared__ int s_i[8];
-  __shared__ int s_p;
+__device__ void blk_lower_solve(const T* __restrict__ A, long long lda, T* x, int n, int mt, bool unit) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int j = 0; j < m; ++j) {
-    double bv = -1.0;
-    int bi = m;
-    for (int r = j + threadIdx.x; r < m; r += blockDim.x) {
-      double a = fabs((double)A[r + (long long)j * m]);
-      if (a > bv) { bv = a; bi = r; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, bv, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { s_v[wid] = bv; s_i[wid] = bi; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double b = s_v[0];
-      int ix = s_i[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-        if (s_v[w] > b || (s_v[w] == b && s_i[w] < ix)) { b = s_v[w]; ix = s_i[w]; }
-      if (!(b > 0.0) || !isfinite(b)) {
-        atomicOr(status, b == 0.0 ? ST_ZERO_PIVOT : ST_NONFINITE);
-        ix = j;
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    const int nb = min(32, n - c0);
+    if (wid == 0) {
+      T Lr[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        Lr[c] = (lane < nb && c < nb) ? A[(c0 + lane) + (long long)(c0 + c) * lda] : T(0);
+      T v = lane < nb ? x[c0 + lane] : T(0);
+      const T inv = (!unit && lane < nb) ? T(1) / A[(c0 + lane) + (long long)(c0 + lane) * lda] : T(1);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < nb) {
+          const T xc = __shfl_sync(0xffffffffu, v, c) * __shfl_sync(0xffffffffu, inv, c);
+          if (lane == c) v = xc;
+          else if (lane > c) v -= Lr[c] * xc;
+        }
       }
-      s_p = ix;
-      jb.piv[j] = ix;
+      if (lane < nb) x[c0 + lane] = v;
     }
     __syncthreads();
-    const int p = s_p;
-    if (p != j)
-      for (int c = threadIdx.x; c < m; c += blockDim.x) {
-        T t = A[j + (long long)c * m];
-        A[j + (long long)c * m] = A[p + (long long)c * m];
-        A[p + (long long)c * m] = t;
-      }
-    __syncthreads();
-    const T dj = A[j + (long long)j * m];
-    const T inv = dj != T(0) ? T(1) / dj : T(0);
-    for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) {
-      T l = A[r + (long long)j * m] * inv;
-      A[r + (long long)j * m] = l;
-      for (int c = j + 1; c < m; ++c) A[r + (long long)c * m] -= l * A[j + (long long)c * m];
+    for (int r = c0 + nb + threadIdx.x; r < mt; r += blockDim.x) {
+      T s = T(0);
+      for (int c = 0; c < nb; ++c) s += A[r + (long long)(c0 + c) * lda] * x[c0 + c];
+      x[r] -= s;
     }
     __syncthreads();
   }
 }
 
+// x[0:n] <- U^-1 x[0:n], U = A(0:n, 0:n) upper with its diagonal.
 template <typename T>
-void HssKern<T>::lu(const LuJob* jobs, int njobs, unsigned* status, cudaStream_t s) {
-  if (njobs <= 0) return;
-  k_lu_small<T><<<njobs, 256, 0, s>>>(jobs, status);
-  count_launch();
+__device__ void blk_upper_solve(const T* __restrict__ A, long long lda, T* x, int n) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int b = (n + 31) / 32 - 1; b >= 0; --b) {
+    const int c0 = 32 * b, nb = min(32, n - c0);
+    if (wid == 0) {
+      T Ur[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        Ur[c] = (lane < nb && c < nb) ? A[(c0 + lane) + (long long)(c0 + c) * lda] : T(0);
+      T v = lane < nb ? x[c0 + lane] : T(0);
+      const T inv = lane < nb ? T(1) / A[(c0 + lane) + (long long)(c0 + lane) * lda] : T(1);
+#pragma unroll
+      for (int c = 31; c >= 0; --c) {
+        if (c < nb) {
+          const T xc = __shfl_sync(0xffffffffu, v, c) * __shfl_sync(0xffffffffu, inv, c);
+          if (lane == c) v = xc;
+          else if (lane < c) v -= Ur[c] * xc;
+        }
+      }
+      if (lane < nb) x[c0 + lane] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < c0; r += blockDim.x) {
+      T s = T(0);
+      for (int c = 0; c < nb; ++c) s += A[r + (long long)(c0 + c) * lda] * x[c0 + c];
+      x[r] -= s;
+    }
+    __syncthreads();
+  }
 }
 
+constexpr int ULV_THREADS = 256;
+constexpr size_t kUlvSmemMax = 200 * 1024;
+
 // ---------------------------------------------------------------------------
-// ULV forward step of one node (see UlvFwdJob).
+// ULV forward step of one node (see UlvFwdJob), one CTA per (node, column):
+//   b_t = leaf rows of b, or [bhat_1 - B12 w_2; bhat_2 - B21 w_1];
+//   root: x = U^-1 L^-1 P b_t;
+//   else: bo = Omega b_t, x1 = L^-1 bo[0:m-k], bhat = bo[m-k:] - D21 x1,
+//         w = V_t^T [w_1; w_2] + Vt(0:m-k, :)^T x1.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_ulv_fwd(const UlvFwdJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(ULV_THREADS) k_ulv_fwd(const UlvFwdJob* __restrict__ jobs) {
   const UlvFwdJob jb = jobs[blockIdx.x];
   const int nrhs = jb.nrhs;
   const int m = jb.m, k = jb.k, nk = jb.m - jb.k;
@@ -1694,123 +1646,187 @@ __global__ void __launch_bounds__(256) k_ulv_fwd(const UlvFwdJob* __restrict__ j
   const T* bh2 = (const T*)jb.bh2;
   const T* wc1 = (const T*)jb.wc1;
   const T* wc2 = (const T*)jb.wc2;
+  extern __shared__ __align__(16) unsigned char ulv_sm[];
+  T* bt = (T*)ulv_sm;  // m
+  T* pb = bt + m;      // m
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = blockIdx.y; j < nrhs; j += gridDim.y) {  // columns are independent
-    T* bt = (T*)jb.bt + (long long)j * m;
-    T* bo = (T*)jb.bo + (long long)j * m;
     if (jb.leaf) {
       for (int i = threadIdx.x; i < m; i += blockDim.x) bt[i] = bsrc[i + j * jb.ldbsrc];
     } else {
+      const T* w2 = wc2 + (long long)j * jb.kc2;
+      const T* w1 = wc1 + (long long)j * jb.kc1;
       for (int i = threadIdx.x; i < jb.k1; i += blockDim.x) {
         T s = bh1[i + (long long)j * jb.ldbh1];
-        for (int c = 0; c < jb.kc2; ++c) s -= B12[i + (long long)c * jb.k1] * wc2[c + (long long)j * jb.kc2];
+        for (int c = 0; c < jb.kc2; ++c) s -= B12[i + (long long)c * jb.k1] * w2[c];
         bt[i] = s;
       }
       for (int i = threadIdx.x; i < jb.k2; i += blockDim.x) {
         T s = bh2[i + (long long)j * jb.ldbh2];
-        for (int c = 0; c < jb.kc1; ++c) s -= B21[i + (long long)c * jb.k2] * wc1[c + (long long)j * jb.kc1];
+        for (int c = 0; c < jb.kc1; ++c) s -= B21[i + (long long)c * jb.k2] * w1[c];
         bt[jb.k1 + i] = s;
       }
     }
     __syncthreads();
-    if (jb.is_root) {  // LU solve with interchanges
-      if (threadIdx.x == 0)
-        for (int i = 0; i < m; ++i) {
-          int p = jb.piv[i];
-          if (p != i) { T t = bt[i]; bt[i] = bt[p]; bt[p] = t; }
-        }
-      __syncthreads();
-      for (int c = 0; c < m; ++c) {
-        const T xc = bt[c];
-        for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) bt[r] -= Dt[r + (long long)c * m] * xc;
-        __syncthreads();
-      }
-      for (int c = m - 1; c >= 0; --c) {
-        const T xc = bt[c] / Dt[c + (long long)c * m];
-        __syncthreads();
-        if (threadIdx.x == 0) bt[c] = xc;
-        for (int r = threadIdx.x; r < c; r += blockDim.x) bt[r] -= Dt[r + (long long)c * m] * xc;
-        __syncthreads();
-      }
-      for (int i = threadIdx.x; i < m; i += blockDim.x) bo[i] = bt[i];
+    // pb = P b_t: the LU row permutation at the root, Pi^T otherwise
+    for (int i = threadIdx.x; i < m; i += blockDim.x) pb[i] = bt[jb.piv[i]];
+    __syncthreads();
+    T* bo = (T*)jb.bo + (long long)j * m;
+    if (jb.is_root) {
+      blk_lower_solve<T>(Dt, m, pb, m, m, true);
+      blk_upper_solve<T>(Dt, m, pb, m);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) bo[i] = pb[i];
       __syncthreads();
       continue;
     }
-    // bo = Omega bt
-    for (int i = threadIdx.x; i < nk; i += blockDim.x) {
-      T s = bt[jb.piv[k + i]];
-      for (int c = 0; c < k; ++c) s -= X[c + (long long)i * k] * bt[jb.piv[c]];
-      bo[i] = s;
+    // Omega: bt[0:nk] = pb[k + i] - E(i, :) pb[0:k]; bt[nk:] = pb[0:k]
+    for (int i = wid; i < nk; i += nw) {
+      T s = T(0);
+      for (int c = lane; c < k; c += 32) s += X[c + (long long)i * k] * pb[c];
+      s = wsum<T>(s);
+      if (lane == 0) bt[i] = pb[k + i] - s;
     }
-    for (int i = threadIdx.x; i < k; i += blockDim.x) bo[nk + i] = bt[jb.piv[i]];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) bt[nk + i] = pb[i];
     __syncthreads();
-    // x1 = L^-1 bo[0:nk]; bhat = bo[nk:] - D21 x1  (one column sweep)
-    for (int c = 0; c < nk; ++c) {
-      const T xc = bo[c] / Dt[c + (long long)c * m];
-      __syncthreads();
-      if (threadIdx.x == 0) bo[c] = xc;
-      for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) bo[r] -= Dt[r + (long long)c * m] * xc;
-      __syncthreads();
-    }
-    // w = V_t^T [wc1; wc2] + Vt_top^T x1
+    // x1 = L^-1 bt[0:nk]; bhat = bt[nk:] - D21 x1
+    blk_lower_solve<T>(Dt, m, bt, nk, m, false);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) bo[i] = bt[i];
+    // w = V_t^T [wc1; wc2] + Vt(0:nk, :)^T x1, one warp per entry
     T* w = (T*)jb.w + (long long)j * jb.kc;
-    for (int c = threadIdx.x; c < jb.kc; c += blockDim.x) {
+    for (int c = wid; c < jb.kc; c += nw) {
       T s = T(0);
       if (!jb.leaf) {
-        for (int r = 0; r < jb.kc1; ++r) s += Vloc[r + (long long)c * jb.mc] * wc1[r + (long long)j * jb.kc1];
-        for (int r = 0; r < jb.kc2; ++r)
+        for (int r = lane; r < jb.kc1; r += 32) s += Vloc[r + (long long)c * jb.mc] * wc1[r + (long long)j * jb.kc1];
+        for (int r = lane; r < jb.kc2; r += 32)
           s += Vloc[jb.kc1 + r + (long long)c * jb.mc] * wc2[r + (long long)j * jb.kc2];
       }
-      for (int r = 0; r < nk; ++r) s += Vt[r + (long long)c * m] * bo[r];
-      w[c] = s;
+      for (int r = lane; r < nk; r += 32) s += Vt[r + (long long)c * m] * bt[r];
+      s = wsum<T>(s);
+      if (lane == 0) w[c] = s;
     }
     __syncthreads();
   }
 }
 
 template <typename T>
-void HssKern<T>::ulv_fwd(const UlvFwdJob* jobs, int njobs, int max_nrhs, cudaStream_t s) {
-  if (njobs <= 0) return;
-  k_ulv_fwd<T><<<dim3(njobs, std::min(std::max(max_nrhs, 1), 256)), 256, 0, s>>>(jobs);
+int HssKern<T>::ulv_fwd(const UlvFwdJob* jobs, int njobs, int max_nrhs, int max_m, cudaStream_t s) {
+  if (njobs <= 0) return 0;
+  const size_t smem = 2 * sizeof(T) * (size_t)std::max(max_m, 1);
+  if (smem > kUlvSmemMax) return -1;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_ulv_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUlvSmemMax);
+    attr = true;
+  }
+  k_ulv_fwd<T><<<dim3(njobs, std::min(std::max(max_nrhs, 1), 256)), ULV_THREADS, smem, s>>>(jobs);
   count_launch();
+  return 0;
 }
 
 // ---------------------------------------------------------------------------
-// ULV backward step of one node: out = Q [x1; xhat2].
+// ULV backward step of one node: x = H_0 ... H_{m-k-1} [x1; xhat2], applied
+// one 32-reflector panel at a time from the last: with V_b the panel's
+// reflector rows (unit at their own column, Dt to the right) and T_b its
+// upper-triangular factor, x <- x - V_b^T (T_b (V_b x)).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_ulv_bwd(const UlvBwdJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(ULV_THREADS) k_ulv_bwd(const UlvBwdJob* __restrict__ jobs) {
   const UlvBwdJob jb = jobs[blockIdx.x];
   const int nrhs = jb.nrhs;
   const int m = jb.m, nk = jb.m - jb.k;
   const T* Dt = (const T*)jb.Dt;
-  const T* tau = (const T*)jb.tau;
+  const T* Tq = (const T*)jb.Tq;
   const T* x1 = (const T*)jb.x1;
   const T* xh2 = (const T*)jb.xh2;
-  __shared__ double sh[33];
+  extern __shared__ __align__(16) unsigned char ulv_sm[];
+  T* x = (T*)ulv_sm;  // m
+  __shared__ T part[ULV_THREADS / 32][32];
+  __shared__ T zq[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = blockIdx.y; j < nrhs; j += gridDim.y) {  // columns are independent
-    T* x = (T*)jb.out + (long long)j * jb.ldout;
     for (int i = threadIdx.x; i < nk; i += blockDim.x) x[i] = x1[i + (long long)j * m];
     for (int i = threadIdx.x; i < jb.k; i += blockDim.x) x[nk + i] = xh2[i + (long long)j * jb.ldxh2];
     __syncthreads();
-    for (int i = nk - 1; i >= 0; --i) {
-      const T t = tau[i];
-      if (t == T(0)) continue;  // uniform across the block
-      const double xi = (double)x[i];  // read before the reduction's barriers
-      T part = T(0);
-      for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) part += Dt[i + (long long)c * m] * x[c];
-      const double s = block_sum_d((double)part, sh) + xi;
-      const T f = t * T(s);
-      if (threadIdx.x == 0) x[i] -= f;
-      for (int c = i + 1 + threadIdx.x; c < m; c += blockDim.x) x[c] -= f * Dt[i + (long long)c * m];
+    for (int b = (nk + 31) / 32 - 1; b >= 0; --b) {
+      const int i0 = 32 * b, w = min(32, nk - i0);
+      // y_q = v_{i0+q} . x, lanes = reflectors, warps split the columns
+      T y = T(0);
+      if (lane < w) {
+        const int iq = i0 + lane;
+        for (int c = i0 + wid; c < m; c += nw) {
+          const T xc = x[c];
+          if (c > iq) y += Dt[iq + (long long)c * m] * xc;
+          else if (c == iq) y += xc;
+        }
+      }
+      part[wid][lane] = y;
       __syncthreads();
+      if (wid == 0) {
+        T yq = T(0);
+        for (int q = 0; q < nw; ++q) yq += part[q][lane];
+        // z = T_b y (upper triangular)
+        const T* Tb = Tq + (long long)b * 1024;
+        T z = T(0);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const T yc = __shfl_sync(0xffffffffu, yq, c);
+          if (c < w && lane <= c) z += Tb[lane + 32 * c] * yc;
+        }
+        zq[lane] = lane < w ? z : T(0);
+      }
+      __syncthreads();
+      // x[c] -= sum_q V_b(q, c) z_q for c >= i0
+      for (int c = i0 + threadIdx.x; c < m; c += blockDim.x) {
+        T s = T(0);
+        const int qmax = min(w, c - i0 + 1);
+        for (int q = 0; q < qmax; ++q) {
+          const int iq = i0 + q;
+          s += (c == iq ? T(1) : Dt[iq + (long long)c * m]) * zq[q];
+        }
+        x[c] -= s;
+      }
+      __syncthreads();
+    }
+    T* out = (T*)jb.out + (long long)j * jb.ldout;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) out[i] = x[i];
+    __syncthreads();
+  }
+}
+
+template <typename T>
+int HssKern<T>::ulv_bwd(const UlvBwdJob* jobs, int njobs, int max_nrhs, int max_m, cudaStream_t s) {
+  if (njobs <= 0) return 0;
+  const size_t smem = sizeof(T) * (size_t)std::max(max_m, 1);
+  if (smem > kUlvSmemMax) return -1;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_ulv_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUlvSmemMax);
+    attr = true;
+  }
+  k_ulv_bwd<T><<<dim3(njobs, std::min(std::max(max_nrhs, 1), 256)), ULV_THREADS, smem, s>>>(jobs);
+  count_launch();
+  return 0;
+}
+
+// Row permutation of a finished LU from its sequential interchanges.
+__global__ void k_lu_perm(const LuJob* __restrict__ jobs) {
+  const LuJob jb = jobs[blockIdx.x];
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < jb.m; ++i) jb.perm[i] = i;
+  for (int i = 0; i < jb.m; ++i) {
+    const int p = jb.piv[i];
+    if (p != i && p >= 0 && p < jb.m) {
+      const int t = jb.perm[i];
+      jb.perm[i] = jb.perm[p];
+      jb.perm[p] = t;
     }
   }
 }
 
 template <typename T>
-void HssKern<T>::ulv_bwd(const UlvBwdJob* jobs, int njobs, int max_nrhs, cudaStream_t s) {
+void HssKern<T>::lu_perm(const LuJob* jobs, int njobs, cudaStream_t s) {
   if (njobs <= 0) return;
-  k_ulv_bwd<T><<<dim3(njobs, std::min(std::max(max_nrhs, 1), 256)), 256, 0, s>>>(jobs);
+  k_lu_perm<<<njobs, 32, 0, s>>>(jobs);
   count_launch();
 }
 
