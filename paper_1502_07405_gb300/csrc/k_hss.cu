@@ -97,6 +97,69 @@ __device__ __forceinline__ void warp_reflect4(T* w0, T* w1, T* w2, T* w3, int nc
   nn[3] = p3;
 }
 
+// The same with the reflector unscaled: v holds the raw pivot column on rows
+// > i, vi replaces row i, and tau is tau / vi^2 (H = I - tau v v^T is
+// unchanged).  Row i of every column is updated as well.
+template <typename T>
+__device__ __forceinline__ void warp_reflect4v(T* w0, T* w1, T* w2, T* w3, int nc, const T* v, T vi,
+                                               int i, int d, T tau, int lane, T* nn) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  for (int r = i + lane; r < d; r += 32) {
+    const T vr = r == i ? vi : v[r];
+    s0 += vr * w0[r];
+    s1 += vr * w1[r];
+    s2 += vr * w2[r];
+    s3 += vr * w3[r];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+  }
+  const T f0 = tau * s0, f1 = tau * s1, f2 = tau * s2, f3 = tau * s3;
+  T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+  for (int r = i + lane; r < d; r += 32) {
+    const T vr = r == i ? vi : v[r];
+    const T x0 = w0[r] - f0 * vr, x1 = w1[r] - f1 * vr, x2 = w2[r] - f2 * vr, x3 = w3[r] - f3 * vr;
+    w0[r] = x0;
+    if (nc > 1) w1[r] = x1;
+    if (nc > 2) w2[r] = x2;
+    if (nc > 3) w3[r] = x3;
+    if (r > i) {
+      p0 += x0 * x0;
+      p1 += x1 * x1;
+      p2 += x2 * x2;
+      p3 += x3 * x3;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+    p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+    p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+    p3 += __shfl_xor_sync(0xffffffffu, p3, o);
+  }
+  nn[0] = p0;
+  nn[1] = p1;
+  nn[2] = p2;
+  nn[3] = p3;
+}
+
+// eps^2 |R_11|^2 in FP64, rounded down to T: for every T value b,
+// b > id_threshold(eps, r11sq) iff b > eps^2 r11sq exactly.
+template <typename T>
+__device__ __forceinline__ T id_threshold(double eps, T r11sq);
+template <>
+__device__ __forceinline__ float id_threshold<float>(double eps, float r11sq) {
+  return __double2float_rd(eps * eps * (double)fmaxf(r11sq, 0.f));
+}
+template <>
+__device__ __forceinline__ double id_threshold<double>(double eps, double r11sq) {
+  return eps * eps * fmax(r11sq, 0.0);
+}
+
 // The per-step decision of the column-pivoted QR, taken by one thread in
 // FP64: pivot norm from the largest remaining squared norm, |R_11| at the
 // first step, and the rank rule |R_{i+1,i+1}| <= eps |R_11| (stop also when
@@ -734,11 +797,23 @@ int HssKern<T>::batched_id_cluster(const IdJob* jobs, int njobs, int max_m, int 
 constexpr int IDS_THREADS = 1024;
 constexpr size_t kIdSmemBudget = 200 * 1024;
 
+// column stride of the resident matrix: 16-byte aligned columns
+__host__ __device__ inline int id_smem_ld(int d) { return (d + 3) & ~3; }
+
 __host__ __device__ inline size_t id_smem_bytes(int d, int m, int cl, int esz) {
   const size_t mo = (size_t)(m + cl - 1) / cl;
-  return ((size_t)esz * mo * d + 15) / 16 * 16 + 8 * mo + 8 * (size_t)d + (size_t)m + 64;
+  const size_t ld = (size_t)id_smem_ld(d);
+  return (size_t)esz * mo * ld + (size_t)esz * ld + (size_t)m + 64;
 }
 
+// Per step (every CTA of the cluster, 32 warps): the warps' proposals (the
+// largest trailing norm among the columns each warp updated in the previous
+// step) are reduced to a CTA proposal, exchanged through distributed shared
+// memory, and every warp takes the same decision (rank rule compared in T
+// against eps^2 |R_11|^2 computed once in FP64 and rounded down, which is
+// exact for every T value); every CTA copies the raw pivot column from its
+// owner with 16-byte loads, and the warps apply the reflector with the
+// Householder scaling folded into tau, recomputing norms and proposals.
 template <typename T, int CL>
 __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __restrict__ jobs, double eps,
                                                                  double* rdiag_all, int* order_all, int max_m,
@@ -749,109 +824,109 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
   const int jid = blockIdx.x / CL;
   const IdJob jb = jobs[jid];
   const int d = jb.d, m = jb.m;
+  const int ldw = id_smem_ld(d);
   const T* Y = (const T*)jb.Y;
   double* rdiag = rdiag_all + (long long)jid * max_k;
   int* order = order_all + (long long)jid * max_m;
   extern __shared__ __align__(16) unsigned char sraw[];
   const int mo = (m - rank + CL - 1) / CL;  // owned columns rank + CL * l
   const int mo_max = (m + CL - 1) / CL;     // same layout in every CTA of the cluster
-  T* Wl = (T*)sraw;                          // d x mo_max, ld d
-  T* cn = (T*)(sraw + ((size_t)sizeof(T) * mo_max * d + 15) / 16 * 16);  // mo_max norms^2
-  T* v = (T*)((double*)cn + mo_max);                                     // d
-  unsigned char* skel = (unsigned char*)((double*)cn + mo_max + d);      // m
+  T* Wl = (T*)sraw;                          // ldw x mo_max
+  T* v = Wl + (size_t)ldw * mo_max;          // ldw: raw pivot column of the step
+  unsigned char* skel = (unsigned char*)(v + ldw);  // m
   __shared__ T s_bv[IDS_THREADS / 32];
   __shared__ int s_bi[IDS_THREADS / 32];
-  __shared__ T s_cand_v;
-  __shared__ int s_cand_i;
-  __shared__ T s_nrm;
-  __shared__ int s_p, s_stop;
-  __shared__ double s_r11;
+  __shared__ T s_cand_v[2];
+  __shared__ int s_cand_i[2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int l = wid; l < mo; l += nw) {
-    const int j = rank + CL * l;
-    T sp = T(0);
-    for (int r = lane; r < d; r += 32) {
-      const T x = Y[r + (long long)j * d];
-      Wl[r + l * d] = x;
-      sp += x * x;
+  {  // copy in, initial norms and proposals
+    T bv = T(-1);
+    int bi = m;
+    for (int g = wid; 4 * g < mo; g += nw) {
+      for (int q = 0; q < 4; ++q) {
+        const int l = 4 * g + q;
+        if (l >= mo) break;
+        const int j = rank + CL * l;
+        T sp = T(0);
+        for (int r = lane; r < d; r += 32) {
+          const T x = Y[r + (long long)j * d];
+          Wl[r + (size_t)l * ldw] = x;
+          sp += x * x;
+        }
+        sp = wsum<T>(sp);
+        if (sp > bv) { bv = sp; bi = j; }
+      }
     }
-    sp = wsum<T>(sp);
-    if (lane == 0) cn[l] = sp;
+    if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
   }
   for (int j = threadIdx.x; j < m; j += blockDim.x) skel[j] = 0;
-  __syncthreads();
+  // reduction of the warp proposals to the cluster's pivot (b, p), taken
+  // identically by every warp
+  auto pivot = [&](int par, T& b, int& p) {
+    __syncthreads();
+    if (CL == 1) {
+      b = s_bv[lane];
+      p = s_bi[lane];
+    } else {
+      if (wid == 0) {
+        T c = s_bv[lane];
+        int ci = s_bi[lane];
+        for (int o = 16; o > 0; o >>= 1) {
+          const T ov = __shfl_xor_sync(0xffffffffu, c, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
+          if (ov > c || (ov == c && oi < ci)) { c = ov; ci = oi; }
+        }
+        if (lane == 0) { s_cand_v[par] = c; s_cand_i[par] = ci; }
+      }
+      cluster.sync();
+      b = T(-1);
+      p = m;
+      if (lane < CL) {
+        b = *cluster.map_shared_rank(&s_cand_v[par], lane);
+        p = *cluster.map_shared_rank(&s_cand_i[par], lane);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, b, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, p, o);
+      if (ov > b || (ov == b && oi < p)) { b = ov; p = oi; }
+    }
+  };
+  T b;
+  int p;
+  pivot(0, b, p);
+  const T thr = id_threshold<T>(eps, b);  // eps^2 |R_11|^2, rounded down to T
   const int kmax = min(d, m);
   int k = kmax;
   for (int i = 0; i < kmax; ++i) {
-    T bv = T(-1);
-    int bi = m;
-    for (int l = threadIdx.x; l < mo; l += blockDim.x) {
-      const T x = cn[l];
-      if (x > bv) { bv = x; bi = rank + CL * l; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ov = __shfl_down_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
-    __syncthreads();
-    if (wid == 0) {
-      T b = lane < nw ? s_bv[lane] : T(-1);
-      int ix = lane < nw ? s_bi[lane] : m;
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, b, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
-        if (ov > b || (ov == b && oi < ix)) { b = ov; ix = oi; }
-      }
-      if (lane == 0) { s_cand_v = b; s_cand_i = ix; }
-    }
-    if (CL > 1) cluster.sync(); else __syncthreads();
-    if (wid == 0) {
-      T b = T(-1);
-      int ix = m;
-      if (lane < CL) {
-        b = CL > 1 ? *cluster.map_shared_rank(&s_cand_v, lane) : s_cand_v;
-        ix = CL > 1 ? *cluster.map_shared_rank(&s_cand_i, lane) : s_cand_i;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, b, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, ix, o);
-        if (ov > b || (ov == b && oi < ix)) { b = ov; ix = oi; }
-      }
-      if (lane == 0) {  // identical in every CTA: same inputs, same FP64 decision
-        double r11 = s_r11, nrm;
-        s_stop = id_decide((double)b, i, eps, &r11, &nrm) || ix >= m;
-        s_r11 = r11;
-        s_nrm = T(nrm);
-        s_p = ix;
-      }
-    }
-    __syncthreads();
-    const int p = s_p;
-    if (s_stop) {
+    if (i > 0) pivot(i & 1, b, p);
+    const bool stop = (i == 0 ? !(b > T(0)) : !(b > thr)) || p >= m;
+    if (stop) {
       k = i;
       break;
     }
-    const T nrm = s_nrm;
-    // Householder vector from the pivot column, read from its owner's shared memory
+    const T nrm = sqrt(b);
+    // raw pivot column, rows from the 16-byte boundary at or below i
     const int owner = p % CL, lp = p / CL;
-    const T* pc = CL > 1 ? cluster.map_shared_rank(Wl + (long long)lp * d, owner) : Wl + (long long)lp * d;
-    const T alpha = pc[i];
-    const T beta = alpha >= T(0) ? T(-nrm) : T(nrm);
-    const T tau = (beta - alpha) / beta;
-    const T scl = T(1) / (alpha - beta);
-    for (int r = i + 1 + threadIdx.x; r < d; r += blockDim.x) v[r] = pc[r] * scl;
-    if (threadIdx.x == 0) {
-      v[i] = T(1);
-      skel[p] = 1;
-      if (rank == 0) {
-        rdiag[i] = (double)beta;
-        order[i] = p;
-      }
-    }
-    if (owner == rank && threadIdx.x == 0) cn[lp] = T(-1);
+    const T* pc = Wl + (size_t)lp * ldw;
+    if (CL > 1) pc = cluster.map_shared_rank(pc, owner);
+    constexpr int E = 16 / sizeof(T);
+    const int i0 = i - i % E;
+    const int4* src = reinterpret_cast<const int4*>(pc + i0);
+    int4* dst = reinterpret_cast<int4*>(v + i0);
+    for (int q = threadIdx.x; q < (ldw - i0) / E; q += blockDim.x) dst[q] = src[q];
+    if (threadIdx.x == 0) skel[p] = 1;
     __syncthreads();
+    const T alpha = v[i];
+    const T beta = alpha >= T(0) ? -nrm : nrm;
+    const T vi = alpha - beta;           // row i of the unscaled reflector
+    const T tau = T(-1) / (beta * vi);   // tau / vi^2
+    if (rank == 0 && threadIdx.x == 0) {
+      rdiag[i] = (double)beta;
+      order[i] = p;
+    }
+    T bv = T(-1);
+    int bi = m;
     for (int g = wid; 4 * g < mo; g += nw) {  // up to 4 owned, unpivoted columns per warp
       int ls[4];
       int nc = 0;
@@ -862,11 +937,15 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
       if (nc == 0) continue;
       for (int q = nc; q < 4; ++q) ls[q] = ls[0];
       T nn[4];
-      warp_reflect4<T>(Wl + ls[0] * d, Wl + ls[1] * d, Wl + ls[2] * d, Wl + ls[3] * d, nc, v, i, d, tau, lane, nn);
-      if (lane < nc) cn[ls[lane]] = lane == 0 ? nn[0] : lane == 1 ? nn[1] : lane == 2 ? nn[2] : nn[3];
+      warp_reflect4v<T>(Wl + ls[0] * (size_t)ldw, Wl + ls[1] * (size_t)ldw, Wl + ls[2] * (size_t)ldw,
+                        Wl + ls[3] * (size_t)ldw, nc, v, vi, i, d, tau, lane, nn);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = rank + CL * ls[q];
+        if (q < nc && (nn[q] > bv || (nn[q] == bv && j < bi))) { bv = nn[q]; bi = j; }
+      }
     }
-    // the pivot column is no longer read by anyone after this barrier
-    if (CL > 1) cluster.sync(); else __syncthreads();
+    if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
   }
   if (CL > 1) cluster.sync(); else __syncthreads();
   // X = R1^-1 R2 on the owned non-skeleton columns, R1 columns read from their owners
@@ -881,10 +960,11 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
     }
     if (nc == 0) continue;
     for (int q = nc; q < 4; ++q) ls[q] = ls[0];
-    warp_backsub4<T>(Wl + ls[0] * d, Wl + ls[1] * d, Wl + ls[2] * d, Wl + ls[3] * d, nc, k,
+    warp_backsub4<T>(Wl + ls[0] * (size_t)ldw, Wl + ls[1] * (size_t)ldw, Wl + ls[2] * (size_t)ldw,
+                     Wl + ls[3] * (size_t)ldw, nc, k,
                      [&](int c) {
                        const int pc2 = order[c];
-                       T* col = Wl + (long long)(pc2 / CL) * d;
+                       T* col = Wl + (size_t)(pc2 / CL) * ldw;
                        return (const T*)(CL > 1 ? cluster.map_shared_rank(col, pc2 % CL) : col);
                      },
                      [&](int c) { return T(rd[c]); }, lane);
@@ -893,7 +973,7 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
       int pos = 0;
       for (int c = lane; c < j; c += 32) pos += skel[c] ? 0 : 1;
       for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
-      for (int r = lane; r < k; r += 32) X[r + (long long)pos * k] = Wl[r + ls[q] * d];
+      for (int r = lane; r < k; r += 32) X[r + (long long)pos * k] = Wl[r + ls[q] * (size_t)ldw];
       if (lane == 0) jb.piv[k + pos] = j;
     }
   }
@@ -1286,12 +1366,15 @@ static int launch_id_rr(const IdJob* jobs, int njobs, int max_m, int max_d, doub
 
 template <typename T>
 int HssKern<T>::id_rr_config(int d, int m) {
-  if (!std::is_same<T, float>::value) return 0;
-  for (int cl = 1; cl <= 16; cl *= 2) {
-    if (d <= 256 && m <= RR_NW * 8 * cl) return cl;        // 8 rows x 8 columns per lane
-    if (d <= 512 && m <= RR_NW * 4 * cl) return 32 + cl;   // 16 rows x 4 columns per lane
+  if constexpr (!std::is_same<T, float>::value) {
+    return 0;
+  } else {
+    for (int cl = 1; cl <= 16; cl *= 2) {
+      if (d <= 256 && m <= RR_NW * 8 * cl) return cl;        // 8 rows x 8 columns per lane
+      if (d <= 512 && m <= RR_NW * 4 * cl) return 32 + cl;   // 16 rows x 4 columns per lane
+    }
+    return 0;
   }
-  return 0;
 }
 
 template <typename T>
