@@ -128,8 +128,13 @@ hssmf_status hssmf_factor(hssmf_ctx* ctx, const double* values);
  * residual is <= rtol; HSSMF_ERR_NOCONV if one does not within maxit. */
 hssmf_status hssmf_solve(hssmf_ctx* ctx, const double* B, double* X, int nrhs, int ldb);
 
-/* Same for A^T X = B: the transposed operators of the factorization in
- * reverse order, with the outer iteration on A^T. */
+/* Same for A^T X = B (Section 3.3 applied to A^T): dense fronts apply
+ * U^T, then L^T with the row interchanges; HSS fronts use the ULV
+ * factorization of the transposed HSS matrix (D^T, row and column
+ * generators exchanged, B12 <-> B21^T) and Z^T = F11^-T V^big_k, built on
+ * the device at the first solve_T after each factorization and kept until
+ * the next one (the first call takes about as long as the ULV part of the
+ * factorization); the outer iteration runs on A^T. */
 hssmf_status hssmf_solve_T(hssmf_ctx* ctx, const double* B, double* X, int nrhs, int ldb);
 
 hssmf_status hssmf_get_stats(const hssmf_ctx* ctx, hssmf_stats* out);

@@ -130,6 +130,14 @@ struct NodeRt {
   void *Uexp = nullptr, *Vexp = nullptr, *Dt = nullptr, *Vt = nullptr, *tau = nullptr, *Tq = nullptr;
   int* lupiv = nullptr;
   int* luperm = nullptr;
+  // transposed generators (D^T; B21^T and B12^T, the B12 and B21 of the
+  // transposed matrix) and the ULV factorization of the transposed F11,
+  // built at the first solve_T after a factorization; swap_view exchanges
+  // them with the fields above
+  void *DT = nullptr, *Bt12 = nullptr, *Bt21 = nullptr;
+  void *DtT = nullptr, *VtT = nullptr, *tauT = nullptr, *TqT = nullptr;
+  int* lupivT = nullptr;
+  int* lupermT = nullptr;
   void *Ubig = nullptr, *Vbig = nullptr;
   // solve scratch
   void *bt = nullptr, *bo = nullptr, *w = nullptr, *x = nullptr;
@@ -148,14 +156,56 @@ struct FrontRt {
   int tree_h = 0;
   // low-rank Schur and solve data
   void* Z = nullptr;
+  void* ZT = nullptr;  // the same for the transposed front (solve_T)
   int k = -1, q = -1, root = -1;
   std::vector<int> f11;  // F11 subtree nodes in postorder
+};
+
+// Exchanges the generators of the front's HSS matrix with those of its
+// transpose (row and column IDs, bases and ranks, D <-> D^T, B12 <-> B21^T,
+// B21 <-> B12^T) and the ULV data with the transposed ULV data: every
+// routine that works on the view then works on the transposed front.
+// Applying it twice restores the front.
+void swap_view(FrontRt& F) {
+  for (NodeRt& N : F.nd) {
+    std::swap(N.kr, N.kc);
+    std::swap(N.m, N.mc);
+    std::swap(N.piv_r, N.piv_c);
+    std::swap(N.Xr, N.Xc);
+    std::swap(N.Ir, N.Ic);
+    std::swap(N.Uexp, N.Vexp);
+    std::swap(N.Ubig, N.Vbig);
+    std::swap(N.D, N.DT);
+    std::swap(N.B12, N.Bt12);
+    std::swap(N.B21, N.Bt21);
+    std::swap(N.Dt, N.DtT);
+    std::swap(N.Vt, N.VtT);
+    std::swap(N.tau, N.tauT);
+    std::swap(N.Tq, N.TqT);
+    std::swap(N.lupiv, N.lupivT);
+    std::swap(N.luperm, N.lupermT);
+  }
+  std::swap(F.Z, F.ZT);
+}
+
+struct ViewGuard {  // transposed view of the listed fronts for a scope
+  std::vector<FrontRt*> fs;
+  bool on;
+  ViewGuard(const std::vector<FrontRt*>& f, bool t) : fs(f), on(t) {
+    if (on)
+      for (FrontRt* F : fs) swap_view(*F);
+  }
+  ~ViewGuard() {
+    if (on)
+      for (FrontRt* F : fs) swap_view(*F);
+  }
 };
 
 }  // namespace
 
 struct HssState {
   Pool fac, lvl, rnd, sol;
+  bool transposed_ready = false;  // ULV of the transposed F11 trees built
   Ring ring;
   int* d_ranks = nullptr;
   int* h_ranks = nullptr;
@@ -437,6 +487,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     F->compressed = false;
     F->R = F->Sr = F->Sc = nullptr;
     F->Rch[0] = F->Rch[1] = nullptr;
+    F->Z = F->ZT = nullptr;
     ensure_cols(X, *F, S.fronts[F->f]);
   }
   std::vector<FrontRt*> todo = fs;
@@ -897,26 +948,14 @@ void ulv_solve(Ctx<T>& X, const std::vector<FrontRt*>& fs, const std::vector<con
 
 // ULV-like factorization of F11 (Section 2.3), then Theta^* Phi and the dense
 // update matrix F22 - Theta^* Phi of every front of the level (Section 4.4).
+// ULV-like factorization of the F11 trees of the listed fronts (Section 2.3),
+// bottom-up; reads the node generators (D, B, the row IDs, the explicit
+// column bases) and writes Dt, Vt, tau, Tq and the root LU.
 template <typename T>
-hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
+hssmf_status ulv_factor_f11(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
   hssmf_ctx& c = X.c;
   HssState& H = X.H;
   const Symbolic& S = c.sym;
-  c.prof.mark(PH_ULV, X.s);
-  // explicit interpolative bases U = Pi_r [I; E_r], V = Pi_c [I; E_c]
-  std::vector<BasisJob> bj;
-  for (FrontRt* F : fs) {
-    const ClusterTree& tr = S.fronts[F->f].tree;
-    for (int t = 0; t < tr.size(); ++t) {
-      if (t == tr.root()) continue;
-      NodeRt& N = F->nd[t];
-      N.Uexp = X.A(H.fac, (long long)N.m * N.kr);
-      N.Vexp = X.A(H.fac, (long long)N.mc * N.kc);
-      if (N.kr) bj.push_back(BasisJob{N.piv_r, N.Xr, N.Uexp, std::max(N.m, 1), N.m, N.kr});
-      if (N.kc) bj.push_back(BasisJob{N.piv_c, N.Xc, N.Vexp, std::max(N.mc, 1), N.mc, N.kc});
-    }
-  }
-  X.launch(bj, [&](const BasisJob* d, int n) { HssKern<T>::basis(d, n, X.s); });
   // ULV, bottom-up over the F11 trees
   int maxh = 0;
   for (FrontRt* F : fs) maxh = std::max(maxh, F->height[F->k]);
@@ -1087,7 +1126,54 @@ hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     }
     X.launch(lu, [&](const LuJob* d, int n) { HssKern<T>::lu_perm(d, n, X.s); });
   }
-  if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during the ULV factorization");
+  return X.oom ? c.fail(HSSMF_ERR_OOM, "device memory exhausted during the ULV factorization") : HSSMF_OK;
+}
+
+// Z = F11^-1 U^big_k of every front with an update block (Section 4.4).
+template <typename T>
+void ulv_z(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
+  HssState& H = X.H;
+  // Z = F11^-1 U^big_k for fronts with an update block
+  std::vector<FrontRt*> sf;
+  std::vector<const T*> bin;
+  std::vector<long long> ldin, ldout;
+  std::vector<T*> xout;
+  std::vector<int> nr;
+  for (FrontRt* F : fs) {
+    if (F->nu == 0 || F->nd[F->k].kr == 0) continue;
+    F->Z = X.A(H.fac, (long long)F->ns * F->nd[F->k].kr);
+    sf.push_back(F);
+    bin.push_back((const T*)F->nd[F->k].Ubig);
+    ldin.push_back(F->ns);
+    xout.push_back((T*)F->Z);
+    ldout.push_back(F->ns);
+    nr.push_back(F->nd[F->k].kr);
+  }
+  if (!sf.empty()) ulv_solve(X, sf, bin, ldin, xout, ldout, nr, H.lvl);
+}
+
+template <typename T>
+hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
+  hssmf_ctx& c = X.c;
+  HssState& H = X.H;
+  const Symbolic& S = c.sym;
+  c.prof.mark(PH_ULV, X.s);
+  // explicit interpolative bases U = Pi_r [I; E_r], V = Pi_c [I; E_c]
+  std::vector<BasisJob> bj;
+  for (FrontRt* F : fs) {
+    const ClusterTree& tr = S.fronts[F->f].tree;
+    for (int t = 0; t < tr.size(); ++t) {
+      if (t == tr.root()) continue;
+      NodeRt& N = F->nd[t];
+      N.Uexp = X.A(H.fac, (long long)N.m * N.kr);
+      N.Vexp = X.A(H.fac, (long long)N.mc * N.kc);
+      if (N.kr) bj.push_back(BasisJob{N.piv_r, N.Xr, N.Uexp, std::max(N.m, 1), N.m, N.kr});
+      if (N.kc) bj.push_back(BasisJob{N.piv_c, N.Xc, N.Vexp, std::max(N.mc, 1), N.mc, N.kc});
+    }
+  }
+  X.launch(bj, [&](const BasisJob* d, int n) { HssKern<T>::basis(d, n, X.s); });
+  hssmf_status st = ulv_factor_f11(X, fs);
+  if (st) return st;
   c.prof.mark(PH_SCHUR, X.s);
   // nested bases U^big, V^big of every non-root node, bottom-up
   int th = 0;
@@ -1116,23 +1202,7 @@ hssmf_status factor_ulv_schur(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     }
     X.flush_gemm();
   }
-  // Z = F11^-1 U^big_k for fronts with an update block
-  std::vector<FrontRt*> sf;
-  std::vector<const T*> bin;
-  std::vector<long long> ldin, ldout;
-  std::vector<T*> xout;
-  std::vector<int> nr;
-  for (FrontRt* F : fs) {
-    if (F->nu == 0 || F->nd[F->k].kr == 0) continue;
-    F->Z = X.A(H.fac, (long long)F->ns * F->nd[F->k].kr);
-    sf.push_back(F);
-    bin.push_back((const T*)F->nd[F->k].Ubig);
-    ldin.push_back(F->ns);
-    xout.push_back((T*)F->Z);
-    ldout.push_back(F->ns);
-    nr.push_back(F->nd[F->k].kr);
-  }
-  if (!sf.empty()) ulv_solve(X, sf, bin, ldin, xout, ldout, nr, H.lvl);
+  ulv_z(X, fs);
   // W = V^big_k^* Z, Theta^* = U^big_q B_qk W, Phi^* = V^big_q B_kq^*
   std::vector<T*> Wk(fs.size()), G2(fs.size()), Th(fs.size()), Ph(fs.size());
   for (size_t i = 0; i < fs.size(); ++i) {
@@ -1229,6 +1299,7 @@ void hss_begin_factor(hssmf_ctx& c) {
   c.id_trace.clear();
   c.hss_flops = c.hss_bytes = 0.0;
   if (!c.hss) return;
+  c.hss->transposed_ready = false;
   c.hss->fac.reset();
   c.hss->sol.reset();
   c.hss->sol_nrhs = -1;
@@ -1252,12 +1323,65 @@ hssmf_status hss_factor_level(hssmf_ctx& c, int level) {
   return HSSMF_OK;
 }
 
+// ULV factorization of the transposed F11 of every HSS front and Z^T =
+// F11^-T V^big_k (solve_T, Section 3.3): the same routines run on the
+// transposed view of each front after transposed copies of D, B12, B21.
+template <typename T>
+hssmf_status ensure_transposed(hssmf_ctx& c) {
+  HssState& H = *c.hss;
+  if (H.transposed_ready) return HSSMF_OK;
+  const Symbolic& S = c.sym;
+  for (size_t h = 0; h < c.plan.size(); ++h) {
+    if (c.plan[h].hss.empty()) continue;
+    Ctx<T> X(c);
+    H.lvl.reset();
+    std::vector<FrontRt*> fs = level_fronts(H, c.plan[h]);
+    for (FrontRt* F : fs) {
+      const ClusterTree& tr = S.fronts[F->f].tree;
+      for (int t = 0; t < tr.size(); ++t) {
+        NodeRt& N = F->nd[t];
+        if (tr.leaf(t)) {
+          if (!N.D) continue;
+          N.DT = X.A(H.fac, (long long)N.n * N.n);
+          X.copy(N.D, N.n, 1, N.DT, N.n, N.n, N.n);
+        } else {
+          const NodeRt &a = F->nd[tr.c1[t]], &b = F->nd[tr.c2[t]];
+          N.Bt12 = X.A(H.fac, (long long)std::max(a.kc, 1) * std::max(b.kr, 1));  // B21^T
+          N.Bt21 = X.A(H.fac, (long long)std::max(b.kc, 1) * std::max(a.kr, 1));  // B12^T
+          X.copy(N.B21, std::max(b.kr, 1), 1, N.Bt12, std::max(a.kc, 1), a.kc, b.kr);
+          X.copy(N.B12, std::max(a.kr, 1), 1, N.Bt21, std::max(b.kc, 1), b.kc, a.kr);
+        }
+      }
+    }
+    X.flush_copy();
+    if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted building the transposed ULV");
+    hssmf_status st;
+    {
+      ViewGuard view(fs, true);
+      st = ulv_factor_f11(X, fs);
+      if (!st) ulv_z(X, fs);
+    }
+    if (st) return st;
+    if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted building the transposed ULV");
+    if ((st = c.cuda_check(cudaStreamSynchronize(c.stream), "transposed ULV"))) return st;
+    H.ring.off = 0;
+  }
+  H.transposed_ready = true;
+  return HSSMF_OK;
+}
+
+// Forward multifrontal step of the HSS fronts of a level (Section 4.4);
+// with transpose, the same on the transposed fronts (solve_T).
 template <typename T>
 hssmf_status hss_solve_fwd_level(hssmf_ctx& c, int level, T* W, int nrhs, int transpose) {
-  if (transpose) return c.fail(HSSMF_ERR_ARG, "solve_T with HSS fronts is not available yet");
+  if (transpose) {
+    hssmf_status st = ensure_transposed<T>(c);
+    if (st) return st;
+  }
   Ctx<T> X(c);
   HssState& H = X.H;
   std::vector<FrontRt*> fs = level_fronts(H, c.plan[level]);
+  ViewGuard view(fs, transpose != 0);
   // scratch for this level is taken from the solve pool; the pool is reset
   // at the first (bottom) HSS level of every solve
   if (level == c.hss_first_level) H.sol.reset();
@@ -1306,10 +1430,10 @@ hssmf_status hss_solve_fwd_level(hssmf_ctx& c, int level, T* W, int nrhs, int tr
 
 template <typename T>
 hssmf_status hss_solve_bwd_level(hssmf_ctx& c, int level, T* W, T* xp, int nrhs, int transpose) {
-  if (transpose) return c.fail(HSSMF_ERR_ARG, "solve_T with HSS fronts is not available yet");
   Ctx<T> X(c);
   HssState& H = X.H;
   std::vector<FrontRt*> fs = level_fronts(H, c.plan[level]);
+  ViewGuard view(fs, transpose != 0);
   // x_s = y - Z B_kq (V^big_q)^* x_u
   std::vector<T*> t3(fs.size()), t4(fs.size());
   for (size_t i = 0; i < fs.size(); ++i) {

@@ -96,3 +96,68 @@ def test_adaptive_rounds_grow_d():
     assert st["adaptive_rounds"] > 0 and st["max_d"] > 16
     x = s.solve(b)
     assert _relres(A, x, b)[0] <= 1e-9
+
+
+def _convdiff(side=64):
+    return problems.grid_convdiff2d(side, 30.0, -20.0), (side, side, 1)
+
+
+def test_solve_T_tiny_eps_is_exact_nonsymmetric_2d():
+    """solve_T through HSS fronts: at eps -> 0 one application equals the
+    oracle's transposed dense solution (A nonsymmetric) to 1e-10."""
+    A, dims = _convdiff()
+    b = problems.rhs_uniform(A.n, 2, 3)
+    s = _gpu(A, dims, hss_tol=1e-14, maxit=0, **HSS2D)
+    assert s.get_stats()["n_hss_fronts"] > 20
+    x = s.solve_T(b)
+    xo = mf.apply_inverse(_oracle(A, dims), b, transpose=True)
+    assert np.linalg.norm(x - xo) <= 1e-10 * np.linalg.norm(xo)
+    r = b - A.to_scipy().T @ x
+    assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_T_single_application_within_10x_of_oracle(prec):
+    A, dims = _convdiff()
+    b = problems.rhs_uniform(A.n, 1, 4)
+    eps = 1e-6 if prec == 0 else 1e-4
+    s = _gpu(A, dims, hss_tol=eps, maxit=0, precision=prec, **HSS2D)
+    x = s.solve_T(b)
+    fo = _oracle(A, dims, hss_tol=eps, **HSS2D)
+    xo = mf.apply_inverse(fo, b, transpose=True)
+    At = A.to_scipy().T
+    rg = np.linalg.norm(b[:, 0] - At @ x[:, 0]) / np.linalg.norm(b)
+    ro = np.linalg.norm(b[:, 0] - At @ xo[:, 0]) / np.linalg.norm(b)
+    assert rg <= 10 * ro + (1e-14 if prec == 0 else 1e-6), (rg, ro)
+
+
+def test_solve_and_solve_T_interleave():
+    """solve_T builds the transposed ULV once; solve afterwards is unchanged."""
+    A, dims = _convdiff()
+    b = problems.rhs_uniform(A.n, 1, 5)
+    s = _gpu(A, dims, hss_tol=1e-6, maxit=0, **HSS2D)
+    x1 = s.solve(b)
+    xt1 = s.solve_T(b)
+    x2 = s.solve(b)
+    xt2 = s.solve_T(b)
+    np.testing.assert_array_equal(x1, x2)
+    np.testing.assert_array_equal(xt1, xt2)
+    assert np.linalg.norm(x1 - xt1) > 1e-6 * np.linalg.norm(x1)  # A is nonsymmetric
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_T_gmres_to_1e10(prec):
+    A, dims = _convdiff()
+    b = problems.rhs_uniform(A.n, 3, 6)
+    s = _gpu(A, dims, hss_tol=1e-3, precision=prec, **HSS2D)
+    x = s.solve_T(b)
+    At = A.to_scipy().T
+    rel = np.linalg.norm(b - At @ x, axis=0) / np.linalg.norm(b, axis=0)
+    assert np.all(rel <= 1e-10), rel
+    # and the 3D HSS path
+    dims3 = (16, 16, 16)
+    A3 = problems.grid_poisson(dims3)
+    b3 = problems.rhs_uniform(A3.n, 2, 7)
+    s3 = _gpu(A3, dims3, hss_tol=1e-3, hss_min_front=256, d0=64, dd=32, precision=prec)
+    x3 = s3.solve_T(b3)
+    assert np.all(_relres(A3, x3, b3) <= 1e-10)
