@@ -187,7 +187,8 @@ int hssmf_get_id_trace(const hssmf_ctx* ctx, int* rec, int max_records);
  * thread-block cluster of 8 CTAs, 16 on a cluster of 16 CTAs (where the
  * device can schedule it, else 8), all working on the matrix in L2;
  * use_cluster = -1 keeps every matrix in the shared memory of a cluster of
- * 1..16 CTAs sized for the largest job (HSSMF_ERR_ARG if it does not fit);
+ * 1..16 CTAs sized for the largest job (past 16 CTAs the columns that do not
+ * fit stay in global memory);
  * use_cluster = -2 (prec 1 only) keeps every matrix in the registers of a
  * cluster of 1..16 CTAs, for d <= 512 and m <= 2048 (d <= 256) or m <= 1024
  * (d <= 512), else HSSMF_ERR_ARG.

@@ -614,10 +614,12 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during HSS compression");
       if (!ij.empty()) {
         if ((int)ij.size() > H.rank_cap) return c.fail(HSSMF_ERR_ARG, "too many IDs in one level");
-        // Routing: nodes whose matrix fits in the shared memory of a cluster
-        // of 1..16 CTAs run there (no global traffic per step); tiny nodes
-        // run one per CTA (more CTAs per SM); the rest on clusters working
-        // from L2 (16 CTAs for the largest).
+        // Routing: FP32 nodes that fit in the registers of a cluster no larger
+        // than their shared-memory cluster run register-resident; other nodes
+        // run with their matrix in the shared memory of a cluster of 1..16
+        // CTAs (overflow columns in global memory); tiny nodes one per CTA
+        // (more CTAs per SM).  The L2-resident cluster kernels remain the
+        // fallback where a cluster cannot be scheduled.
         std::vector<IdJob> tier[3], smem_tier[5];
         int tm[3] = {0, 0, 0}, td[3] = {0, 0, 0}, sm_m[5] = {0, 0, 0, 0, 0}, sm_d[5] = {0, 0, 0, 0, 0};
         std::map<int, std::vector<IdJob>> rr_tier;  // register-resident (FP32), by configuration
@@ -634,9 +636,11 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
             md.second = std::max(md.second, j.d);
             continue;
           }
+          // shared-memory kernel on the smallest cluster that holds the
+          // matrix; past 16 CTAs the overflow columns stay in global memory
           const long long w = (long long)j.d * j.m;
-          const int cl = HssKern<T>::id_smem_cluster_size(j.d, j.m);
-          if (w * (long long)sizeof(T) > kTinyIdBytes && cl > 0) {
+          const int cl = cl_sm > 0 ? cl_sm : 16;
+          if (w * (long long)sizeof(T) > kTinyIdBytes) {
             const int ti = cl == 1 ? 0 : cl == 2 ? 1 : cl == 4 ? 2 : cl == 8 ? 3 : 4;
             smem_tier[ti].push_back(j);
             sm_m[ti] = std::max(sm_m[ti], j.m);

@@ -814,10 +814,10 @@ __host__ __device__ inline size_t id_smem_bytes(int d, int m, int cl, int esz) {
 // exact for every T value); every CTA copies the raw pivot column from its
 // owner with 16-byte loads, and the warps apply the reflector with the
 // Householder scaling folded into tau, recomputing norms and proposals.
-template <typename T, int CL>
+template <typename T, int CL, bool OVF>
 __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __restrict__ jobs, double eps,
                                                                  double* rdiag_all, int* order_all, int max_m,
-                                                                 int max_k) {
+                                                                 int max_k, int ms) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
@@ -826,14 +826,22 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
   const int d = jb.d, m = jb.m;
   const int ldw = id_smem_ld(d);
   const T* Y = (const T*)jb.Y;
+  T* W = (T*)jb.W;  // owned columns beyond the shared-memory capacity stay here (ld d)
   double* rdiag = rdiag_all + (long long)jid * max_k;
   int* order = order_all + (long long)jid * max_m;
   extern __shared__ __align__(16) unsigned char sraw[];
   const int mo = (m - rank + CL - 1) / CL;  // owned columns rank + CL * l
   const int mo_max = (m + CL - 1) / CL;     // same layout in every CTA of the cluster
-  T* Wl = (T*)sraw;                          // ldw x mo_max
-  T* v = Wl + (size_t)ldw * mo_max;          // ldw: raw pivot column of the step
+  const int msh = min(mo_max, ms);          // local columns 0..msh-1 in shared memory
+  T* Wl = (T*)sraw;                          // ldw x msh
+  T* v = Wl + (size_t)ldw * msh;             // ldw: raw pivot column of the step
   unsigned char* skel = (unsigned char*)(v + ldw);  // m
+  // column l owned by this CTA: shared memory, or global memory past the capacity
+  // (OVF: some owned columns live in global memory; otherwise all are shared)
+  auto colp = [&](int l) -> T* {
+    if (!OVF || l < ms) return Wl + (size_t)l * ldw;
+    return W + (size_t)(rank + CL * l) * d;
+  };
   __shared__ T s_bv[IDS_THREADS / 32];
   __shared__ int s_bi[IDS_THREADS / 32];
   __shared__ T s_cand_v[2];
@@ -848,9 +856,10 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
         if (l >= mo) break;
         const int j = rank + CL * l;
         T sp = T(0);
+        T* col = colp(l);
         for (int r = lane; r < d; r += 32) {
           const T x = Y[r + (long long)j * d];
-          Wl[r + (size_t)l * ldw] = x;
+          col[r] = x;
           sp += x * x;
         }
         sp = wsum<T>(sp);
@@ -908,13 +917,18 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
     const T nrm = sqrt(b);
     // raw pivot column, rows from the 16-byte boundary at or below i
     const int owner = p % CL, lp = p / CL;
-    const T* pc = Wl + (size_t)lp * ldw;
-    if (CL > 1) pc = cluster.map_shared_rank(pc, owner);
-    constexpr int E = 16 / sizeof(T);
-    const int i0 = i - i % E;
-    const int4* src = reinterpret_cast<const int4*>(pc + i0);
-    int4* dst = reinterpret_cast<int4*>(v + i0);
-    for (int q = threadIdx.x; q < (ldw - i0) / E; q += blockDim.x) dst[q] = src[q];
+    if (!OVF || lp < ms) {
+      const T* pc = Wl + (size_t)lp * ldw;
+      if (CL > 1) pc = cluster.map_shared_rank(pc, owner);
+      constexpr int E = 16 / sizeof(T);
+      const int i0 = i - i % E;
+      const int4* src = reinterpret_cast<const int4*>(pc + i0);
+      int4* dst = reinterpret_cast<int4*>(v + i0);
+      for (int q = threadIdx.x; q < (ldw - i0) / E; q += blockDim.x) dst[q] = src[q];
+    } else {  // (global writes of the owner are ordered by the cluster barrier)
+      const T* pc = W + (size_t)p * d;
+      for (int r = i + threadIdx.x; r < d; r += blockDim.x) v[r] = pc[r];
+    }
     if (threadIdx.x == 0) skel[p] = 1;
     __syncthreads();
     const T alpha = v[i];
@@ -937,8 +951,11 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
       if (nc == 0) continue;
       for (int q = nc; q < 4; ++q) ls[q] = ls[0];
       T nn[4];
-      warp_reflect4v<T>(Wl + ls[0] * (size_t)ldw, Wl + ls[1] * (size_t)ldw, Wl + ls[2] * (size_t)ldw,
-                        Wl + ls[3] * (size_t)ldw, nc, v, vi, i, d, tau, lane, nn);
+      if (!OVF || ls[nc - 1] < ms)  // all in shared memory: keep the shared-memory addressing visible
+        warp_reflect4v<T>(Wl + ls[0] * (size_t)ldw, Wl + ls[1] * (size_t)ldw, Wl + ls[2] * (size_t)ldw,
+                          Wl + ls[3] * (size_t)ldw, nc, v, vi, i, d, tau, lane, nn);
+      else
+        warp_reflect4v<T>(colp(ls[0]), colp(ls[1]), colp(ls[2]), colp(ls[3]), nc, v, vi, i, d, tau, lane, nn);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int j = rank + CL * ls[q];
@@ -960,11 +977,11 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
     }
     if (nc == 0) continue;
     for (int q = nc; q < 4; ++q) ls[q] = ls[0];
-    warp_backsub4<T>(Wl + ls[0] * (size_t)ldw, Wl + ls[1] * (size_t)ldw, Wl + ls[2] * (size_t)ldw,
-                     Wl + ls[3] * (size_t)ldw, nc, k,
+    warp_backsub4<T>(colp(ls[0]), colp(ls[1]), colp(ls[2]), colp(ls[3]), nc, k,
                      [&](int c) {
-                       const int pc2 = order[c];
-                       T* col = Wl + (size_t)(pc2 / CL) * ldw;
+                       const int pc2 = order[c], l2 = pc2 / CL;
+                       if (OVF && l2 >= ms) return (const T*)(W + (size_t)pc2 * d);
+                       T* col = Wl + (size_t)l2 * ldw;
                        return (const T*)(CL > 1 ? cluster.map_shared_rank(col, pc2 % CL) : col);
                      },
                      [&](int c) { return T(rd[c]); }, lane);
@@ -973,7 +990,8 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
       int pos = 0;
       for (int c = lane; c < j; c += 32) pos += skel[c] ? 0 : 1;
       for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
-      for (int r = lane; r < k; r += 32) X[r + (long long)pos * k] = Wl[r + ls[q] * (size_t)ldw];
+      const T* col = colp(ls[q]);
+      for (int r = lane; r < k; r += 32) X[r + (long long)pos * k] = col[r];
       if (lane == 0) jb.piv[k + pos] = j;
     }
   }
@@ -988,14 +1006,21 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
 template <typename T, int CL>
 static int launch_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
                           int* order, cudaStream_t s) {
-  const size_t smem = id_smem_bytes(max_d, max_m, CL, sizeof(T));
-  if (smem > kIdSmemBudget) return -1;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_cpqr_id_smem<T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIdSmemBudget);
-    if (CL > 8) cudaFuncSetAttribute(k_cpqr_id_smem<T, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  // owned columns per CTA kept in shared memory; the rest stay in the job's W
+  const size_t col = sizeof(T) * (size_t)id_smem_ld(max_d);
+  const size_t fixed = col + (size_t)max_m + 64;
+  if (fixed + col > kIdSmemBudget) return -1;
+  const int mo_max = (std::max(max_m, 1) + CL - 1) / CL;
+  const int ms = (int)std::min<size_t>((size_t)mo_max, (kIdSmemBudget - fixed) / col);
+  const size_t smem = fixed + col * (size_t)ms;
+  const bool ovf = ms < mo_max;
+  auto kern = ovf ? k_cpqr_id_smem<T, CL, true> : k_cpqr_id_smem<T, CL, false>;
+  static bool attr[2] = {false, false};
+  if (!attr[ovf]) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIdSmemBudget);
+    if (CL > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaGetLastError();
-    attr = true;
+    attr[ovf] = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * CL, 1, 1);
@@ -1010,7 +1035,7 @@ static int launch_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, do
   cfg.attrs = at;
   cfg.numAttrs = 1;
   const int max_k = std::max(std::min(max_m, max_d), 1);
-  if (cudaLaunchKernelEx(&cfg, k_cpqr_id_smem<T, CL>, jobs, eps, rdiag, order, std::max(max_m, 1), max_k) !=
+  if (cudaLaunchKernelEx(&cfg, kern, jobs, eps, rdiag, order, std::max(max_m, 1), max_k, ms) !=
       cudaSuccess) {
     cudaGetLastError();
     return -1;

@@ -822,7 +822,7 @@ static hssmf_status batched_id_impl(int njobs, const void* Y, const long long* y
     r = cfg > 0 ? HssKern<T>::batched_id_rr(dj, njobs, max_m, max_d, eps, rdiag, order, cfg, s) : -1;
   } else if (use_cluster < 0) {  // shared-memory-resident matrices on a cluster sized for the largest job
     const int cl = HssKern<T>::id_smem_cluster_size(max_d, max_m);
-    r = cl > 0 ? HssKern<T>::batched_id_smem(dj, njobs, max_m, max_d, eps, rdiag, order, cl, s) : -1;
+    r = HssKern<T>::batched_id_smem(dj, njobs, max_m, max_d, eps, rdiag, order, cl > 0 ? cl : 16, s);
   } else if (use_cluster > 0) {
     r = HssKern<T>::batched_id_cluster(dj, njobs, max_m, max_d, eps, rdiag, order, s, use_cluster >= 16 ? 16 : 8);
   } else {

@@ -123,3 +123,24 @@ def test_register_resident_id_exact_low_rank_and_zero():
     U[piv[9:], :] = Xg.T
     assert np.linalg.norm(Y1[:, piv[:9]] @ U.T - Y1) <= 1e-5 * np.linalg.norm(Y1)
     assert res[1][0] == 0
+
+
+@pytest.mark.parametrize("prec,shape", [(1, (832, 1400)), (0, (400, 1100))])
+def test_shared_memory_id_with_global_overflow(prec, shape):
+    """Matrices larger than 16 CTAs' shared memory: the columns past the
+    capacity stay in global memory; same ID as the oracle's."""
+    d_, m_ = shape
+    Ys = [_decaying(d_, m_, 60.0, 11)]
+    eps = 1e-6 if prec == 0 else 1e-4
+    (k, piv, Xg), = _run_ids(Ys, eps, prec, -1)
+    Y = Ys[0]
+    ko, pivo, Ro = hss.cpqr_rank(Y, eps)
+    assert abs(k - ko) <= 1
+    kk = min(k, ko)
+    assert np.array_equal(piv[:kk], pivo[:kk])
+    assert sorted(piv.tolist()) == list(range(m_))
+    U = np.zeros((m_, k))
+    U[piv[:k], :] = np.eye(k)
+    U[piv[k:], :] = Xg.T
+    err = np.linalg.norm(Y[:, piv[:k]] @ U.T - Y) / np.linalg.norm(Y)
+    assert err <= 50 * eps
