@@ -37,6 +37,9 @@ struct Tile {  // one output tile of one job (64 x 64 SIMT, 128 x 128 tensor cor
 
 constexpr int GEMM_TILE = 64;
 constexpr int GEMM_TILE_TC = 128;
+constexpr int GEMV_MAX_N = 4;  // products with N <= this use the GEMV kernel
+// rows per GEMV tile: op(A) = A / op(A) = A^T
+constexpr int GEMV_ROWS_N = 32, GEMV_ROWS_T = 8;
 
 inline int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }
 

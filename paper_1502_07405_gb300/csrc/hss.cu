@@ -344,20 +344,24 @@ struct Ctx {  // per-call helpers
     gj.push_back(j);
     H.flops += 2.0 * M * N * std::max(K, 0);
   }
-  // FP32 products with a long K (the sampling products U R, the Schur
-  // expansions) run on the tensor cores in 128 x 128 tiles; short-K products
-  // and FP64 run on the CUDA-core kernel (64 x 64 tiles, several CTAs per SM)
-  static bool on_tensor_cores(const GemmJob& j) {
-    return std::is_same<T, float>::value && j.K >= 256 && j.M >= 128 && j.N >= 16;
-  }
+  // Matrix-vector products (N <= GEMV_MAX_N, the solves) run on the
+  // memory-bound GEMV kernel; other FP32 products on the tensor cores (128 x
+  // 128 tiles), FP64 products on the DFMA kernel (64 x 64 tiles)
+  enum { K_GEMV = 0, K_TILES = 1 };
   void flush_gemm() {
     if (gj.empty()) return;
+    constexpr bool tc = std::is_same<T, float>::value;
     for (int pass = 0; pass < 2; ++pass) {
-      const bool tc = pass == 1;
-      const int tile = tc ? GEMM_TILE_TC : GEMM_TILE;
       std::vector<Tile> tiles;
       for (size_t i = 0; i < gj.size(); ++i) {
-        if (on_tensor_cores(gj[i]) != tc) continue;
+        const bool mv = gj[i].N <= GEMV_MAX_N;
+        if (mv != (pass == K_GEMV)) continue;
+        if (mv) {
+          const int rows = gj[i].ta ? GEMV_ROWS_T : GEMV_ROWS_N;
+          for (int a = 0; a < ceil_div(gj[i].M, rows); ++a) tiles.push_back(Tile{(int)i, a, 0});
+          continue;
+        }
+        const int tile = tc ? GEMM_TILE_TC : GEMM_TILE;
         int tm = ceil_div(gj[i].M, tile), tn = ceil_div(gj[i].N, tile);
         for (int b = 0; b < tn; ++b)
           for (int a = 0; a < tm; ++a) tiles.push_back(Tile{(int)i, a, b});
@@ -366,7 +370,9 @@ struct Ctx {  // per-call helpers
       const GemmJob* dj = H.ring.put(gj, s);
       const Tile* dt = H.ring.put(tiles, s);
       if (!dj || !dt) { oom = true; gj.clear(); return; }
-      if (tc)
+      if (pass == K_GEMV)
+        Kern<T>::gemv(dj, dt, (int)tiles.size(), s);
+      else if (tc)
         gemm_tc(dj, dt, (int)tiles.size(), c.d_status, s);
       else
         Kern<T>::gemm(dj, dt, (int)tiles.size(), s);

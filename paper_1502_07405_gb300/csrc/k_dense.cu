@@ -86,6 +86,83 @@ void Kern<T>::gemm(const GemmJob* jobs, const Tile* tiles, int ntiles, cudaStrea
 }
 
 // ---------------------------------------------------------------------------
+// Batched matrix-vector products (N <= GEMV_MAX_N right-hand columns) of the
+// same job list: memory-bound, so every element of op(A) is read once with
+// coalesced loads and used for all N columns.  op(A) = A: a CTA takes 32 rows
+// (lanes), its 8 warps split K and combine in shared memory; op(A) = A^T: a
+// warp per row, lanes over the contiguous K.  Deterministic sums.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemv(const GemmJob* __restrict__ jobs, const Tile* __restrict__ tiles) {
+  const Tile tl = tiles[blockIdx.x];
+  const GemmJob jb = jobs[tl.job];
+  const T* A = static_cast<const T*>(jb.A);
+  const T* B = static_cast<const T*>(jb.B);
+  T* C = static_cast<T*>(jb.C);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int N = jb.N;
+  const long long bk = jb.tb ? jb.ldb : 1, bc = jb.tb ? 1 : jb.ldb;  // op(B)(k, c) = B[k bk + c bc]
+  T acc[GEMV_MAX_N];
+#pragma unroll
+  for (int c = 0; c < GEMV_MAX_N; ++c) acc[c] = T(0);
+  int r;
+  if (!jb.ta) {
+    __shared__ T red[8][GEMV_MAX_N][33];
+    r = tl.tm * 32 + lane;
+    if (r < jb.M) {
+#pragma unroll 8
+      for (int k = wid; k < jb.K; k += 8) {
+        const T a = A[r + (long long)k * jb.lda];
+#pragma unroll
+        for (int c = 0; c < GEMV_MAX_N; ++c)
+          if (c < N) acc[c] += a * B[k * bk + c * bc];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < GEMV_MAX_N; ++c) red[wid][c][lane] = acc[c];
+    __syncthreads();
+    if (wid != 0) return;
+#pragma unroll
+    for (int c = 0; c < GEMV_MAX_N; ++c) {
+      T s2 = T(0);
+      for (int w = 0; w < 8; ++w) s2 += red[w][c][lane];
+      acc[c] = s2;
+    }
+  } else {
+    r = tl.tm * 8 + wid;
+    if (r >= jb.M) return;
+    const T* a_r = A + (long long)r * jb.lda;
+#pragma unroll 4
+    for (int k = lane; k < jb.K; k += 32) {
+      const T a = a_r[k];
+#pragma unroll
+      for (int c = 0; c < GEMV_MAX_N; ++c)
+        if (c < N) acc[c] += a * B[k * bk + c * bc];
+    }
+#pragma unroll
+    for (int c = 0; c < GEMV_MAX_N; ++c)
+      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane != 0) return;
+  }
+  if (r >= jb.M) return;
+  const T alpha = T(jb.alpha), beta = T(jb.beta);
+  const long long row = jb.crow ? jb.crow[r] : r;
+#pragma unroll
+  for (int c = 0; c < GEMV_MAX_N; ++c) {
+    if (c >= N) break;
+    T* cp = C + row + (long long)c * jb.ldc;
+    *cp = (jb.beta == 0.0) ? alpha * acc[c] : alpha * acc[c] + beta * *cp;
+  }
+}
+
+template <typename T>
+void Kern<T>::gemv(const GemmJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  k_gemv<T><<<ntiles, 256, 0, s>>>(jobs, tiles);
+  count_launch();
+}
+
+// ---------------------------------------------------------------------------
 // Front assembly (A3): F_i = A_i (+) U_child0 (+) U_child1, written once per
 // element as a gather over the children's update matrices (children in
 // order: deterministic, no atomics), then the entries of A_i of the tile's

@@ -40,6 +40,9 @@ struct DevSym {  // device copies of the symbolic structure
 template <typename T>
 struct Kern {
   static void gemm(const GemmJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s);
+  // jobs with N <= GEMV_MAX_N; tile tm = row block (GEMV_ROWS_N rows, or
+  // GEMV_ROWS_T for op(A) = A^T)
+  static void gemv(const GemmJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s);
   // dense fronts ---------------------------------------------------------
   static void assemble(const DevSym& ds, T* arena, const double* values, const Tile* tiles,
                        int ntiles, cudaStream_t s);
