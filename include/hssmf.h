@@ -153,11 +153,12 @@ hssmf_status hssmf_get_upd(const hssmf_ctx* ctx, int f, int* upd);
 /* Per-phase device times of the last factor + solve (CUDA events, ms), in
  * this order: 0 dense-front assembly and partial LU, 1 sampling (R, A_i R,
  * child-update GEMMs), 2 element extraction, 3 pre-ID sample updates,
- * 4 interpolative decompositions, 5 post-ID updates, 6 ULV factorization,
- * 7 nested bases, Theta^* Phi and update matrices, 8 multifrontal solve
- * (all preconditioner applications), 9 outer-iteration kernels.  Writes
- * min(n, 10) values; phase timing is recorded only after
- * hssmf_set_profiling(ctx, 1). */
+ * 4 interpolative-decomposition steps outside the ID kernels (job set-up
+ * gaps, rank read-back), 5 post-ID updates, 6 ULV factorization, 7 nested
+ * bases, Theta^* Phi and update matrices, 8 multifrontal solve (all
+ * preconditioner applications), 9 outer-iteration kernels, 10 the ID kernel
+ * launches themselves.  Writes min(n, 11) values; phase timing is recorded
+ * only after hssmf_set_profiling(ctx, 1). */
 hssmf_status hssmf_get_phase_times(const hssmf_ctx* ctx, double* ms, int n);
 hssmf_status hssmf_set_profiling(hssmf_ctx* ctx, int on);
 

@@ -200,7 +200,7 @@ class Solver:
         return s.as_dict()
 
     PHASES = ("dense", "sample", "extract", "pre_id", "id", "post_id", "ulv", "schur", "solve",
-              "outer")
+              "outer", "id_kernels")
 
     def set_profiling(self, on=True):
         self._check(lib.hssmf_set_profiling(self._h, int(bool(on))))

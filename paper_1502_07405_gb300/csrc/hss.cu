@@ -658,6 +658,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           tm[t] = std::max(tm[t], j.m);
           td[t] = std::max(td[t], j.d);
         }
+        c.prof.mark(PH_IDK, X.s);
         for (auto& kv : rr_tier) {
           const int mm = rr_md[kv.first].first, dd = rr_md[kv.first].second;
           double* rdiag = (double*)H.rnd.alloc(sizeof(double) * kv.second.size() * std::max(std::min(mm, dd), 1));
@@ -708,6 +709,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           if (HssKern<T>::batched_id(dj, (int)tier[0].size(), tm[0], td[0], eps, X.s) < 0)
             return c.fail(HSSMF_ERR_ARG, "an HSS node is too large for the ID kernel");
         }
+        c.prof.mark(PH_ID, X.s);
         hssmf_status st = c.cuda_check(cudaMemcpyAsync(H.h_ranks, H.d_ranks, sizeof(int) * ij.size(),
                                                        cudaMemcpyDeviceToHost, X.s), "ranks");
         if (st) return st;
@@ -719,6 +721,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           FrontRt& F = *idn[i].F;
           NodeRt& N = F.nd[idn[i].t];
           const int kr = H.h_ranks[2 * i], kc = H.h_ranks[2 * i + 1], d = F.d;
+          if (kr < 0 || kc < 0) return c.fail(HSSMF_ERR_TIMEOUT, "a bounded wait in an ID kernel ran out");
           for (int side = 0; side < 2; ++side) {  // algorithmic work of the two IDs
             const double mm = side ? N.mc : N.m, kk = side ? kc : kr;
             c.id_bytes += sizeof(T) * (mm * d + kk * (mm - kk));

@@ -1003,18 +1003,294 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
   if (CL > 1) cluster.sync();
 }
 
+// ---------------------------------------------------------------------------
+// The shared-memory ID on a cluster (CL >= 2) without cluster-wide barriers
+// in the step loop: every CTA pushes its proposal (norm, column) into a slot
+// of every peer's shared memory and arrives on the peer's mbarrier (release
+// at cluster scope); the owner of the pivot column broadcasts it with bulk
+// asynchronous copies (shared::cta -> shared::cluster) that complete on each
+// receiver's mbarrier through its transaction count.  Per step: one CTA
+// barrier and two mbarrier waits.  Slots, vectors and barriers alternate by
+// step parity; every wait is bounded, a wait that runs out makes the ID
+// report rank -1.
+// ---------------------------------------------------------------------------
+namespace push {
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t mapa(uint32_t a, int cta) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(cta));
+  return r;
+}
+__device__ __forceinline__ void init(uint32_t bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void arrive_expect(uint32_t bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void arrive_remote(uint32_t rbar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(rbar) : "memory");
+}
+__device__ __forceinline__ bool wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void st(uint32_t a, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st(uint32_t a, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st(uint32_t a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void copy(uint32_t dst, uint32_t src, unsigned bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "r"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+}  // namespace push
+
+template <typename T, int CL, bool OVF>
+__global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_push(const IdJob* __restrict__ jobs, double eps,
+                                                                 double* rdiag_all, int* order_all, int max_m,
+                                                                 int max_k, int ms) {
+  static_assert(CL >= 2 && CL <= 16, "cluster of 2..16 CTAs");
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int jid = blockIdx.x / CL;
+  const IdJob jb = jobs[jid];
+  const int d = jb.d, m = jb.m;
+  const int ldw = id_smem_ld(d);
+  const T* Y = (const T*)jb.Y;
+  T* W = (T*)jb.W;
+  double* rdiag = rdiag_all + (long long)jid * max_k;
+  int* order = order_all + (long long)jid * max_m;
+  extern __shared__ __align__(16) unsigned char sraw[];
+  const int mo = (m - rank + CL - 1) / CL;
+  const int mo_max = (m + CL - 1) / CL;
+  const int msh = min(mo_max, ms);
+  T* Wl = (T*)sraw;                      // ldw x msh
+  T* vbuf = Wl + (size_t)ldw * msh;      // 2 x ldw: pivot column of the step, by parity
+  T* vstage = vbuf + 2 * (size_t)ldw;    // ldw: staging of a pivot column kept in global memory
+  unsigned char* skel = (unsigned char*)(vstage + ldw);
+  __shared__ T s_bv[IDS_THREADS / 32];
+  __shared__ int s_bi[IDS_THREADS / 32];
+  __shared__ T s_cv[2][16];
+  __shared__ int s_cj[2][16];
+  __shared__ __align__(8) unsigned long long bar_c[2], bar_v[2];
+  __shared__ int s_fail;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  auto colp = [&](int l) -> T* {
+    if (!OVF || l < ms) return Wl + (size_t)l * ldw;
+    return W + (size_t)(rank + CL * l) * d;
+  };
+  {
+    T bv = T(-1);
+    int bi = m;
+    for (int g = wid; 4 * g < mo; g += nw) {
+      for (int q = 0; q < 4; ++q) {
+        const int l = 4 * g + q;
+        if (l >= mo) break;
+        const int j = rank + CL * l;
+        T sp = T(0);
+        T* col = colp(l);
+        for (int r = lane; r < d; r += 32) {
+          const T x = Y[r + (long long)j * d];
+          col[r] = x;
+          sp += x * x;
+        }
+        for (int r = d + lane; r < ldw; r += 32) col[r] = T(0);  // (rows past d travel with the column)
+        sp = wsum<T>(sp);
+        if (sp > bv) { bv = sp; bi = j; }
+      }
+    }
+    if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
+  }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) skel[j] = 0;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 2; ++q) {
+      push::init(push::saddr(&bar_c[q]), CL);
+      push::init(push::saddr(&bar_v[q]), 1);
+    }
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  push::fence_async();
+  cluster.sync();  // every CTA's barriers exist before the first push
+  constexpr int E = 16 / sizeof(T);
+  auto vbytes = [&](int i) { return (unsigned)((ldw - (i - i % E)) * sizeof(T)); };
+  // exchange of the proposals of step i; false if a wait ran out
+  auto pivot = [&](int i, T& b, int& p) -> bool {
+    const int par = i & 1;
+    __syncthreads();
+    if (s_fail) return false;
+    if (wid == 0) {
+      T c = s_bv[lane];
+      int ci = s_bi[lane];
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, c, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
+        if (ov > c || (ov == c && oi < ci)) { c = ov; ci = oi; }
+      }
+      if (lane == 0) push::arrive_expect(push::saddr(&bar_v[par]), vbytes(i));  // before any pivot column can come
+      __syncwarp();
+      if (lane < CL) {
+        push::st(push::mapa(push::saddr(&s_cv[par][rank]), lane), c);
+        push::st(push::mapa(push::saddr(&s_cj[par][rank]), lane), ci);
+        push::arrive_remote(push::mapa(push::saddr(&bar_c[par]), lane));
+      }
+    }
+    // a wait that ran out only marks the failure (every thread keeps the same
+    // control flow); the CTA stops at the next step's barrier
+    if (!push::wait(push::saddr(&bar_c[par]), (i >> 1) & 1)) s_fail = 1;
+    b = lane < CL ? s_cv[par][lane] : T(-1);
+    p = lane < CL ? s_cj[par][lane] : m;
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, b, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, p, o);
+      if (ov > b || (ov == b && oi < p)) { b = ov; p = oi; }
+    }
+    return true;
+  };
+  T b;
+  int p;
+  bool ok = pivot(0, b, p);
+  const T thr = id_threshold<T>(eps, b);
+  const int kmax = min(d, m);
+  int k = kmax;
+  for (int i = 0; i < kmax; ++i) {
+    const int par = i & 1;
+    if (i > 0) ok = pivot(i, b, p);
+    const bool stop = !ok || (i == 0 ? !(b > T(0)) : !(b > thr)) || p >= m;
+    if (stop) {
+      k = i;
+      break;
+    }
+    const T nrm = sqrt(b);
+    const int owner = p % CL, lp = p / CL;
+    const int i0 = i - i % E;
+    if (rank == owner) {  // broadcast the raw pivot column, rows from the 16-byte boundary at or below i
+      const T* src = Wl + (size_t)lp * ldw + i0;
+      if (OVF && lp >= ms) {
+        for (int r = i0 + threadIdx.x; r < ldw; r += blockDim.x) vstage[r] = r < d ? W[(size_t)p * d + r] : T(0);
+        push::fence_async();
+        __syncthreads();
+        src = vstage + i0;
+      }
+      if (threadIdx.x == 0) {
+        const uint32_t s0 = push::saddr(src), dv = push::saddr(vbuf + (size_t)par * ldw + i0);
+        const uint32_t bv = push::saddr(&bar_v[par]);
+        for (int q = 0; q < CL; ++q) push::copy(push::mapa(dv, q), s0, vbytes(i), push::mapa(bv, q));
+        if (OVF) {  // vstage is rewritten by a later step only after these reads
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        }
+      }
+    }
+    if (threadIdx.x == 0) skel[p] = 1;  // (seen by every warp after the next CTA barrier)
+    if (!push::wait(push::saddr(&bar_v[par]), (i >> 1) & 1)) s_fail = 1;
+    const T* v = vbuf + (size_t)par * ldw;
+    const T alpha = v[i];
+    const T beta = alpha >= T(0) ? -nrm : nrm;
+    const T vi = alpha - beta;
+    const T tau = T(-1) / (beta * vi);
+    if (rank == 0 && threadIdx.x == 0) {
+      rdiag[i] = (double)beta;
+      order[i] = p;
+    }
+    T bv = T(-1);
+    int bi = m;
+    for (int g = wid; 4 * g < mo; g += nw) {
+      int ls[4];
+      int nc = 0;
+      for (int q = 0; q < 4; ++q) {
+        const int l = 4 * g + q;
+        const int j = rank + CL * l;
+        if (l < mo && j != p && !skel[j]) ls[nc++] = l;
+      }
+      if (nc == 0) continue;
+      for (int q = nc; q < 4; ++q) ls[q] = ls[0];
+      T nn[4];
+      if (!OVF || ls[nc - 1] < ms)
+        warp_reflect4v<T>(Wl + ls[0] * (size_t)ldw, Wl + ls[1] * (size_t)ldw, Wl + ls[2] * (size_t)ldw,
+                          Wl + ls[3] * (size_t)ldw, nc, v, vi, i, d, tau, lane, nn);
+      else
+        warp_reflect4v<T>(colp(ls[0]), colp(ls[1]), colp(ls[2]), colp(ls[3]), nc, v, vi, i, d, tau, lane, nn);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = rank + CL * ls[q];
+        if (q < nc && (nn[q] > bv || (nn[q] == bv && j < bi))) { bv = nn[q]; bi = j; }
+      }
+    }
+    if (lane == 0) { s_bv[wid] = bv; s_bi[wid] = bi; }
+    push::fence_async();  // the updated columns may be sent by a bulk copy next step
+  }
+  cluster.sync();
+  const bool failed = s_fail != 0;
+  const double* rd = rdiag;
+  T* X = (T*)jb.X;
+  for (int g = wid; !failed && 4 * g < mo; g += nw) {
+    int ls[4];
+    int nc = 0;
+    for (int q = 0; q < 4; ++q) {
+      const int l = 4 * g + q;
+      if (l < mo && !skel[rank + CL * l]) ls[nc++] = l;
+    }
+    if (nc == 0) continue;
+    for (int q = nc; q < 4; ++q) ls[q] = ls[0];
+    warp_backsub4<T>(colp(ls[0]), colp(ls[1]), colp(ls[2]), colp(ls[3]), nc, k,
+                     [&](int c) {
+                       const int pc2 = order[c], l2 = pc2 / CL;
+                       if (OVF && l2 >= ms) return (const T*)(W + (size_t)pc2 * d);
+                       return (const T*)cluster.map_shared_rank(Wl + (size_t)l2 * ldw, pc2 % CL);
+                     },
+                     [&](int c) { return T(rd[c]); }, lane);
+    for (int q = 0; q < nc; ++q) {
+      const int j = rank + CL * ls[q];
+      int pos = 0;
+      for (int c = lane; c < j; c += 32) pos += skel[c] ? 0 : 1;
+      for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+      const T* col = colp(ls[q]);
+      for (int r = lane; r < k; r += 32) X[r + (long long)pos * k] = col[r];
+      if (lane == 0) jb.piv[k + pos] = j;
+    }
+  }
+  if (rank == 0) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) jb.piv[i] = order[i];
+    if (threadIdx.x == 0) *jb.rank = failed ? -1 : k;
+  }
+  cluster.sync();  // peers may still read this CTA's R1 columns
+}
+
 template <typename T, int CL>
 static int launch_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
                           int* order, cudaStream_t s) {
   // owned columns per CTA kept in shared memory; the rest stay in the job's W
+  // (clusters: two pivot-column buffers and a staging column besides)
   const size_t col = sizeof(T) * (size_t)id_smem_ld(max_d);
-  const size_t fixed = col + (size_t)max_m + 64;
+  const size_t fixed = (CL > 1 ? 3 : 1) * col + (size_t)max_m + 64;
   if (fixed + col > kIdSmemBudget) return -1;
   const int mo_max = (std::max(max_m, 1) + CL - 1) / CL;
   const int ms = (int)std::min<size_t>((size_t)mo_max, (kIdSmemBudget - fixed) / col);
   const size_t smem = fixed + col * (size_t)ms;
   const bool ovf = ms < mo_max;
-  auto kern = ovf ? k_cpqr_id_smem<T, CL, true> : k_cpqr_id_smem<T, CL, false>;
+  void (*kern)(const IdJob*, double, double*, int*, int, int, int);
+  if constexpr (CL > 1)
+    kern = ovf ? k_cpqr_id_push<T, CL, true> : k_cpqr_id_push<T, CL, false>;
+  else
+    kern = ovf ? k_cpqr_id_smem<T, CL, true> : k_cpqr_id_smem<T, CL, false>;
   static bool attr[2] = {false, false};
   if (!attr[ovf]) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIdSmemBudget);
@@ -1035,8 +1311,7 @@ static int launch_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, do
   cfg.attrs = at;
   cfg.numAttrs = 1;
   const int max_k = std::max(std::min(max_m, max_d), 1);
-  if (cudaLaunchKernelEx(&cfg, kern, jobs, eps, rdiag, order, std::max(max_m, 1), max_k, ms) !=
-      cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, kern, jobs, eps, rdiag, order, std::max(max_m, 1), max_k, ms) != cudaSuccess) {
     cudaGetLastError();
     return -1;
   }

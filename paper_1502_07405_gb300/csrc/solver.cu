@@ -831,6 +831,8 @@ static hssmf_status batched_id_impl(int njobs, const void* Y, const long long* y
   if (r < 0) st = HSSMF_ERR_ARG;
   if (!st) cudaMemcpyAsync(rank_host, rk, sizeof(int) * njobs, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) st = HSSMF_ERR_CUDA;
+  for (int j = 0; !st && j < njobs; ++j)
+    if (rank_host[j] < 0) st = HSSMF_ERR_TIMEOUT;
   cudaFree(dj);
   cudaFree(buf);
   return st;

@@ -28,7 +28,7 @@ struct HssState;  // HSS-front factor data (hss.cu)
 
 enum Phase {
   PH_DENSE = 0, PH_SAMPLE, PH_EXTRACT, PH_PREID, PH_ID, PH_POSTID, PH_ULV, PH_SCHUR, PH_SOLVE,
-  PH_OUTER, PH_COUNT
+  PH_OUTER, PH_IDK, PH_COUNT  // PH_IDK: the ID kernels alone (PH_ID keeps the rest of that step)
 };
 
 // Phase timeline: an event is recorded at every phase change; the time
