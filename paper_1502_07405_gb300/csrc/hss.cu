@@ -392,9 +392,14 @@ struct Ctx {  // per-call helpers
   }
   void flush_copy() {
     if (cj.empty()) return;
+    std::vector<Tile> tiles;
+    for (size_t i = 0; i < cj.size(); ++i)
+      for (int b = 0; b < ceil_div(cj[i].cols, 32); ++b)
+        for (int a = 0; a < ceil_div(cj[i].rows, 32); ++a) tiles.push_back(Tile{(int)i, a, b});
     const CopyJob* d = H.ring.put(cj, s);
-    if (!d) { oom = true; cj.clear(); return; }
-    HssKern<T>::copy(d, (int)cj.size(), s);
+    const Tile* t = H.ring.put(tiles, s);
+    if (!d || !t) { oom = true; cj.clear(); return; }
+    HssKern<T>::copy(d, t, (int)tiles.size(), s);
     cj.clear();
   }
   template <class J, class F>

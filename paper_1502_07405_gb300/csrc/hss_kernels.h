@@ -123,7 +123,8 @@ struct UlvBwdJob {
 
 template <typename T>
 struct HssKern {
-  static void copy(const CopyJob* jobs, int njobs, cudaStream_t s);
+  // tiles: 32 x 32 destination tiles (job, tm, tn)
+  static void copy(const CopyJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s);
   static void int_gather(const IntGatherJob* jobs, int njobs, cudaStream_t s);
   static void philox(const PhiloxJob* jobs, int njobs, int max_rows, unsigned long long seed,
                      cudaStream_t s);

@@ -260,35 +260,61 @@ __device__ __forceinline__ float gauss_t<float>(unsigned long long seed, unsigne
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Gather/transposing copies.  Grid (job, 32 chunks).
+// Gather/transposing copies over 32 x 32 tiles of the destination (tile list
+// entries (job, tm, tn)); transposed sources go through a shared-memory tile
+// so that both the reads and the writes are coalesced.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_copy(const CopyJob* __restrict__ jobs) {
-  const CopyJob jb = jobs[blockIdx.x];
-  const T* src = (const T*)jb.src;
+__global__ void __launch_bounds__(256) k_copy(const CopyJob* __restrict__ jobs, const Tile* __restrict__ tiles) {
+  const Tile tl = tiles[blockIdx.x];
+  const CopyJob jb = jobs[tl.job];
+  __shared__ T tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i0 = tl.tm * 32, j0 = tl.tn * 32;
   T* dst = (T*)jb.dst;
-  const long long tot = (long long)jb.rows * jb.cols;
-  for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.y * blockDim.x) {
-    int i = (int)(e % jb.rows), j = (int)(e / jb.rows);
-    int si = jb.rmap ? jb.rmap[i] : i;
+  // source element (si, sj) of the concatenated source: its address
+  auto src_at = [&](int i, int j) -> const T* {
+    const int si = jb.rmap ? jb.rmap[i] : i;
     int sj = jb.cmap ? jb.cmap[j] : j;
-    const T* sp = src;
+    const T* sp = (const T*)jb.src;
     long long lds = jb.lds;
     if (jb.src2 && sj >= jb.split) {
       sp = (const T*)jb.src2;
       lds = jb.lds2;
       sj -= jb.split;
     }
-    T v = jb.src_trans ? sp[sj + (long long)si * lds] : sp[si + (long long)sj * lds];
-    dst[i + (long long)j * jb.ldd] = jb.scale_neg ? -v : v;
+    return jb.src_trans ? sp + sj + (long long)si * lds : sp + si + (long long)sj * lds;
+  };
+  if (!jb.src_trans) {
+    const int i = i0 + tx;
+    for (int jj = ty; jj < 32; jj += 8) {
+      const int j = j0 + jj;
+      if (i < jb.rows && j < jb.cols) {
+        const T v = *src_at(i, j);
+        dst[i + (long long)j * jb.ldd] = jb.scale_neg ? -v : v;
+      }
+    }
+    return;
+  }
+  for (int ii = ty; ii < 32; ii += 8) {  // lanes along the source's contiguous index (j)
+    const int i = i0 + ii, j = j0 + tx;
+    if (i < jb.rows && j < jb.cols) tile[ii][tx] = *src_at(i, j);
+  }
+  __syncthreads();
+  const int i = i0 + tx;
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int j = j0 + jj;
+    if (i < jb.rows && j < jb.cols) {
+      const T v = tile[tx][jj];
+      dst[i + (long long)j * jb.ldd] = jb.scale_neg ? -v : v;
+    }
   }
 }
 
 template <typename T>
-void HssKern<T>::copy(const CopyJob* jobs, int njobs, cudaStream_t s) {
-  if (njobs <= 0) return;
-  k_copy<T><<<dim3(njobs, 32), 256, 0, s>>>(jobs);
+void HssKern<T>::copy(const CopyJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  k_copy<T><<<ntiles, 256, 0, s>>>(jobs, tiles);
   count_launch();
 }
 
@@ -1868,8 +1894,8 @@ __global__ void __launch_bounds__(256) k_lu_panel(const LuJob* __restrict__ jobs
     }
     __syncthreads();
     const int p = s_p;
-    if (p != j)
-      for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    if (p != j)  // the panel columns now; the others in k_lu_trsm after the panel
+      for (int c = k0 + threadIdx.x; c < k1; c += blockDim.x) {
         T t = A[j + c * ld];
         A[j + c * ld] = A[p + c * ld];
         A[p + c * ld] = t;
@@ -1893,7 +1919,9 @@ void HssKern<T>::lu_panel(const LuJob* jobs, int njobs, int k0, int nb, unsigned
   count_launch();
 }
 
-// U row block right of the panel: rows [k0, k1), columns [k1, m) <- L_panel^-1 (unit lower, nb <= 32).
+// After a panel: the panel's row interchanges on every column outside it
+// (one thread per column, in order), then the U row block right of the panel:
+// rows [k0, k1), columns [k1, m) <- L_panel^-1 (unit lower, nb <= 32).
 template <typename T>
 __global__ void __launch_bounds__(128) k_lu_trsm(const LuJob* __restrict__ jobs, int k0, int nb) {
   const LuJob jb = jobs[blockIdx.y];
@@ -1903,13 +1931,25 @@ __global__ void __launch_bounds__(128) k_lu_trsm(const LuJob* __restrict__ jobs,
   T* A = (T*)jb.A;
   const long long ld = m;
   __shared__ T L[32][33];
+  __shared__ int pv[32];
   for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
     int i = e & 31, j = e >> 5;
     L[i][j] = (i < w && j < w) ? A[(k0 + i) + (k0 + j) * ld] : T(0);
   }
+  if (threadIdx.x < w) pv[threadIdx.x] = jb.piv[k0 + threadIdx.x];
   __syncthreads();
-  const int c = k1 + blockIdx.x * 128 + threadIdx.x;
+  int c = blockIdx.x * 128 + threadIdx.x;  // columns outside [k0, k1)
+  if (c >= k0) c += w;
   if (c >= m) return;
+  for (int i = 0; i < w; ++i) {
+    const int p = pv[i];
+    if (p != k0 + i) {
+      const T t = A[(k0 + i) + c * ld];
+      A[(k0 + i) + c * ld] = A[p + c * ld];
+      A[p + c * ld] = t;
+    }
+  }
+  if (c < k1) return;
   T x[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) x[i] = (i < w) ? A[(k0 + i) + c * ld] : T(0);
@@ -1925,8 +1965,9 @@ __global__ void __launch_bounds__(128) k_lu_trsm(const LuJob* __restrict__ jobs,
 
 template <typename T>
 void HssKern<T>::lu_trsm(const LuJob* jobs, int njobs, int k0, int nb, int max_m, cudaStream_t s) {
-  if (njobs <= 0 || max_m <= k0 + nb) return;
-  k_lu_trsm<T><<<dim3((max_m - k0 - nb + 127) / 128, njobs), 128, 0, s>>>(jobs, k0, nb);
+  // (every panel, the last included: the interchanges reach the columns on its left)
+  if (njobs <= 0 || k0 >= max_m || max_m - std::min(nb, max_m - k0) <= 0) return;
+  k_lu_trsm<T><<<dim3((max_m - std::min(nb, max_m - k0) + 127) / 128, njobs), 128, 0, s>>>(jobs, k0, nb);
   count_launch();
 }
 
