@@ -190,7 +190,9 @@ int hssmf_get_id_trace(const hssmf_ctx* ctx, int* rec, int max_records);
  * use_cluster = -1 keeps every matrix in the shared memory of a cluster of
  * 1..16 CTAs sized for the largest job (past 16 CTAs the columns that do not
  * fit stay in global memory);
- * use_cluster = -2 (prec 1 only) keeps every matrix in the registers of a
+ * use_cluster = -100 - c (c = 2, 4, 8, 16) runs the shared-memory kernel on
+ * clusters of c CTAs whatever the size; use_cluster = -2 (prec 1 only) keeps
+ * every matrix in the registers of a
  * cluster of 1..16 CTAs, for d <= 512 and m <= 2048 (d <= 256) or m <= 1024
  * (d <= 512), else HSSMF_ERR_ARG.
  * Y is not modified.  Synchronizes the stream. */

@@ -820,6 +820,8 @@ static hssmf_status batched_id_impl(int njobs, const void* Y, const long long* y
   if (use_cluster == -2) {  // register-resident matrices (FP32) on a cluster sized for the largest job
     const int cfg = HssKern<T>::id_rr_config(max_d, max_m);
     r = cfg > 0 ? HssKern<T>::batched_id_rr(dj, njobs, max_m, max_d, eps, rdiag, order, cfg, s) : -1;
+  } else if (use_cluster <= -102 && use_cluster >= -116) {  // shared-memory kernel on a given cluster size
+    r = HssKern<T>::batched_id_smem(dj, njobs, max_m, max_d, eps, rdiag, order, -use_cluster - 100, s);
   } else if (use_cluster < 0) {  // shared-memory-resident matrices on a cluster sized for the largest job
     const int cl = HssKern<T>::id_smem_cluster_size(max_d, max_m);
     r = HssKern<T>::batched_id_smem(dj, njobs, max_m, max_d, eps, rdiag, order, cl > 0 ? cl : 16, s);
