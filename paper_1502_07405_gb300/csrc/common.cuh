@@ -29,10 +29,15 @@ struct GemmJob {
   // (one split term instead of three)
   int a_exact, b_exact;
   double alpha, beta;
+  // tensor-core split-K (ksplit > 1): tile (tm, tn) of split ks writes its
+  // partial sums to ws + ((tm + tn tiles_m) ksplit + ks) 128^2, reduced in
+  // split order by gemm_tc_reduce
+  float* ws;
+  int ksplit, tiles_m;
 };
 
-struct Tile {  // one output tile of one job (64 x 64 SIMT, 128 x 128 tensor cores)
-  int job, tm, tn;
+struct Tile {  // one output tile of one job (64 x 64 SIMT, 128 x 128 tensor cores); ks: K split
+  int job, tm, tn, ks;
 };
 
 constexpr int GEMM_TILE = 64;

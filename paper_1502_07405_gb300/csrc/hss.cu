@@ -205,6 +205,7 @@ struct ViewGuard {  // transposed view of the listed fronts for a scope
 
 struct HssState {
   Pool fac, lvl, rnd, sol;
+  Pool gws;  // split-K partial tiles of one GEMM launch (reused by the next)
   bool transposed_ready = false;  // ULV of the transposed F11 trees built
   Ring ring;
   int* d_ranks = nullptr;
@@ -296,6 +297,7 @@ void hss_release(hssmf_ctx& c) {
   H.lvl.release();
   H.rnd.release();
   H.sol.release();
+  H.gws.release();
   H.ring.release();
   if (H.d_ranks) cudaFree(H.d_ranks);
   if (H.h_ranks) cudaFreeHost(H.h_ranks);
@@ -352,32 +354,69 @@ struct Ctx {  // per-call helpers
     if (gj.empty()) return;
     constexpr bool tc = std::is_same<T, float>::value;
     for (int pass = 0; pass < 2; ++pass) {
-      std::vector<Tile> tiles;
+      std::vector<Tile> tiles, rtiles;
+      if (pass == K_TILES && tc) split_k();
       for (size_t i = 0; i < gj.size(); ++i) {
         const bool mv = gj[i].N <= GEMV_MAX_N;
         if (mv != (pass == K_GEMV)) continue;
         if (mv) {
           const int rows = gj[i].ta ? GEMV_ROWS_T : GEMV_ROWS_N;
-          for (int a = 0; a < ceil_div(gj[i].M, rows); ++a) tiles.push_back(Tile{(int)i, a, 0});
+          for (int a = 0; a < ceil_div(gj[i].M, rows); ++a) tiles.push_back(Tile{(int)i, a, 0, 0});
           continue;
         }
         const int tile = tc ? GEMM_TILE_TC : GEMM_TILE;
-        int tm = ceil_div(gj[i].M, tile), tn = ceil_div(gj[i].N, tile);
-        for (int b = 0; b < tn; ++b)
-          for (int a = 0; a < tm; ++a) tiles.push_back(Tile{(int)i, a, b});
+        const int tm = ceil_div(gj[i].M, tile), tn = ceil_div(gj[i].N, tile);
+        const int ks = std::max(gj[i].ksplit, 1);
+        for (int q = 0; q < ks; ++q)
+          for (int b = 0; b < tn; ++b)
+            for (int a = 0; a < tm; ++a) tiles.push_back(Tile{(int)i, a, b, q});
+        if (ks > 1)
+          for (int b = 0; b < tn; ++b)
+            for (int a = 0; a < tm; ++a) rtiles.push_back(Tile{(int)i, a, b, 0});
       }
       if (tiles.empty()) continue;
       const GemmJob* dj = H.ring.put(gj, s);
       const Tile* dt = H.ring.put(tiles, s);
-      if (!dj || !dt) { oom = true; gj.clear(); return; }
-      if (pass == K_GEMV)
+      const Tile* dr = rtiles.empty() ? nullptr : H.ring.put(rtiles, s);
+      if (!dj || !dt || (!rtiles.empty() && !dr)) { oom = true; gj.clear(); return; }
+      if (pass == K_GEMV) {
         Kern<T>::gemv(dj, dt, (int)tiles.size(), s);
-      else if (tc)
+      } else if (tc) {
         gemm_tc(dj, dt, (int)tiles.size(), c.d_status, s);
-      else
+        if (dr) gemm_tc_reduce(dj, dr, (int)rtiles.size(), s);
+      } else {
         Kern<T>::gemm(dj, dt, (int)tiles.size(), s);
+      }
     }
     gj.clear();
+  }
+  // Tensor-core launches with fewer tiles than about two CTAs per SM split
+  // the K range of their long-K jobs (partials summed in split order)
+  void split_k() {
+    static int nsm = 0;
+    if (!nsm) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
+    }
+    long long t0 = 0;
+    for (const GemmJob& j : gj)
+      if (j.N > GEMV_MAX_N) t0 += (long long)ceil_div(j.M, GEMM_TILE_TC) * ceil_div(j.N, GEMM_TILE_TC);
+    const long long target = 2LL * nsm;
+    if (t0 == 0 || t0 >= target) return;
+    const int S = (int)std::min<long long>(8, (target + t0 - 1) / t0);
+    H.gws.reset();
+    for (GemmJob& j : gj) {
+      if (j.N <= GEMV_MAX_N || j.K < 512) continue;
+      const int sj = std::min(S, j.K / 256);
+      if (sj < 2) continue;
+      const int tm = ceil_div(j.M, GEMM_TILE_TC), tn = ceil_div(j.N, GEMM_TILE_TC);
+      float* ws = (float*)H.gws.alloc(sizeof(float) * (size_t)tm * tn * sj * GEMM_TILE_TC * GEMM_TILE_TC);
+      if (!ws) continue;  // no room: this job runs unsplit
+      j.ws = ws;
+      j.ksplit = sj;
+      j.tiles_m = tm;
+    }
   }
   void copy(const void* src, long long lds, int trans, void* dst, long long ldd, int rows, int cols,
             const int* rmap = nullptr, const int* cmap = nullptr, const void* src2 = nullptr,

@@ -23,6 +23,7 @@
 // rows crow(i) of C.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -146,33 +147,46 @@ __device__ __forceinline__ void split8(const float* x, int nt, uint4* t0, uint4*
   }
 }
 
-// Loads rows [r0, r0 + 128) x K range [k0, k0 + TC_K) of an operand whose
-// element (r, k) sits at P[r * sr + k * sk] (one of sr, sk is 1; rc = rows
-// contiguous), rows < R and k < K valid: k beyond K is stored as zero, rows
-// beyond R are not written (their products land in output rows or columns
-// that are never stored).  Each thread handles TC_K / 16 chunks of 8
-// consecutive k of one row; lanes walk the contiguous direction of the
-// operand.
-__device__ __forceinline__ void load_tile(const float* __restrict__ P, long long sr, long long sk,
-                                          bool rc, int r0, int R, int k0, int K, int nt,
-                                          char* dst) {
+// A 128 x TC_K operand tile in registers: each thread holds TC_CH chunks of
+// 8 consecutive k of one row.  Element (r, k) of the operand sits at
+// P[r * sr + k * sk] (one of sr, sk is 1; rc = rows contiguous); lanes walk
+// the contiguous direction.  Rows < R and k < K are valid; k beyond K reads
+// as zero, rows beyond R are not stored (their products land in output rows
+// or columns that are never stored).
+constexpr int TC_CH = TC_M * TC_K / 8 / TC_THREADS;
+
+__device__ __forceinline__ void chunk_pos(bool rc, int q4, int& r, int& kc) {
+  const int q = threadIdx.x + TC_THREADS * q4;
+  // rows contiguous: 32 consecutive rows per warp, same k chunk;
+  // k contiguous: 8 rows x 4 chunks per warp (one row group per store phase)
+  r = rc ? (q & 127) : ((q & 7) | ((q >> 5) << 3)) & 127;
+  kc = rc ? (q >> 7) : ((q >> 3) & 3) | ((q >> 9) << 2);
+}
+
+__device__ __forceinline__ void tile_fetch(const float* __restrict__ P, long long sr, long long sk, bool rc,
+                                           int r0, int R, int k0, int K, float (&x)[TC_CH][8]) {
   static_assert(TC_K == 32 || TC_K == 64, "stage depth");
 #pragma unroll
-  for (int q4 = 0; q4 < TC_M * TC_K / 8 / TC_THREADS; ++q4) {
-    const int q = threadIdx.x + TC_THREADS * q4;
-    // rows contiguous: 32 consecutive rows per warp, same k chunk;
-    // k contiguous: 8 rows x 4 chunks per warp (one row group per store phase)
-    const int r = rc ? (q & 127) : ((q & 7) | ((q >> 5) << 3)) & 127;
-    const int kc = rc ? (q >> 7) : ((q >> 3) & 3) | ((q >> 9) << 2);
-    const int gr = r0 + r;
-    if (gr >= R) continue;
-    const int kb = k0 + 8 * kc;
-    float x[8];
+  for (int q4 = 0; q4 < TC_CH; ++q4) {
+    int r, kc;
+    chunk_pos(rc, q4, r, kc);
+    const int gr = r0 + r, kb = k0 + 8 * kc;
     const float* p = P + (long long)gr * sr;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = (kb + j < K) ? __ldg(p + (long long)(kb + j) * sk) : 0.f;
+    for (int j = 0; j < 8; ++j) x[q4][j] = (gr < R && kb + j < K) ? __ldg(p + (long long)(kb + j) * sk) : 0.f;
+  }
+}
+
+// Splits the fetched chunks into nt BF16 terms and stores them into the
+// stage's term tiles (canonical K-major layout).
+__device__ __forceinline__ void tile_store(const float (&x)[TC_CH][8], bool rc, int r0, int R, int nt, char* dst) {
+#pragma unroll
+  for (int q4 = 0; q4 < TC_CH; ++q4) {
+    int r, kc;
+    chunk_pos(rc, q4, r, kc);
+    if (r0 + r >= R) continue;
     uint4 t0, t1, t2;
-    split8(x, nt, &t0, &t1, &t2);
+    split8(x[q4], nt, &t0, &t1, &t2);
     const int o = tile_off(r, 8 * kc);
     *reinterpret_cast<uint4*>(dst + o) = t0;
     if (nt > 1) {
@@ -202,6 +216,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
   const long long b_sr = jb.tb ? 1 : jb.ldb, b_sk = jb.tb ? jb.ldb : 1;
   const int nmma = min(TC_N, (N - n0 + 15) & ~15);
   const uint32_t idesc = instr_desc(nmma);
+  // K range of this tile's split
+  const int S = jb.ksplit > 1 ? jb.ksplit : 1;
+  int kbeg = 0, kend = K;
+  if (S > 1) {
+    const int kc = ((K + S - 1) / S + TC_K - 1) / TC_K * TC_K;
+    kbeg = min(K, tl.ks * kc);
+    kend = min(K, kbeg + kc);
+  }
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -218,15 +240,34 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
 
-  const int nk = (K + TC_K - 1) / TC_K;
+  const int nk = (kend - kbeg + TC_K - 1) / TC_K;
   bool ok = true;
+  // the global loads of stage t + 1 are issued before stage t is split and
+  // stored, so that they are in flight during its MMAs
+  float xa[TC_CH][8], xb[TC_CH][8];
+  if (nk > 0) {
+    tile_fetch(A, a_sr, a_sk, jb.ta == 0, m0, M, kbeg, kend, xa);
+    tile_fetch(B, b_sr, b_sk, jb.tb != 0, n0, N, kbeg, kend, xb);
+  }
   for (int t = 0; t < nk; ++t) {
     const int st = t & 1;
     char* sa = smem + st * TC_STAGE_BYTES;
     char* sb = sa + 3 * TC_TERM_BYTES;
+    float ya[TC_CH][8], yb[TC_CH][8];
+    if (t + 1 < nk) {
+      tile_fetch(A, a_sr, a_sk, jb.ta == 0, m0, M, kbeg + (t + 1) * TC_K, kend, ya);
+      tile_fetch(B, b_sr, b_sk, jb.tb != 0, n0, N, kbeg + (t + 1) * TC_K, kend, yb);
+    }
     if (t >= TC_STAGES) ok = ok && mbar_wait(smem_u32(&s_bar[st]), ((t - TC_STAGES) >> 1) & 1);
-    load_tile(A, a_sr, a_sk, jb.ta == 0, m0, M, t * TC_K, K, na, sa);
-    load_tile(B, b_sr, b_sk, jb.tb != 0, n0, N, t * TC_K, K, nb, sb);
+    tile_store(xa, jb.ta == 0, m0, M, na, sa);
+    tile_store(xb, jb.tb != 0, n0, N, nb, sb);
+#pragma unroll
+    for (int q4 = 0; q4 < TC_CH; ++q4)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        xa[q4][j] = ya[q4][j];
+        xb[q4][j] = yb[q4][j];
+      }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -266,7 +307,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
 #pragma unroll
       for (int e = 0; e < 32; ++e) v[e] = 0.f;
     }
-    if (gi < M) {
+    if (S > 1) {  // raw partial sums, column-major 128 x 128 per split
+      float* wp = jb.ws + ((size_t)(tl.tm + tl.tn * jb.tiles_m) * S + tl.ks) * (TC_M * TC_N) + i;
+#pragma unroll
+      for (int e = 0; e < 32; ++e) wp[(size_t)(c0 + e) * TC_M] = v[e];
+    } else if (gi < M) {
 #pragma unroll
       for (int e = 0; e < 32; ++e) {
         const int gj = n0 + c0 + e;
@@ -299,6 +344,35 @@ void gemm_tc(const GemmJob* jobs, const Tile* tiles, int ntiles, unsigned* statu
   count_launch();
 }
 
+// Sum of the K-split partial tiles in split order (deterministic), then
+// C[crow(i), j] = alpha sum + beta C.  One CTA per output tile (ks = 0).
+__global__ void __launch_bounds__(256) k_gemm_tc_reduce(const GemmJob* __restrict__ jobs,
+                                                        const Tile* __restrict__ tiles) {
+  const Tile tl = tiles[blockIdx.x];
+  const GemmJob jb = jobs[tl.job];
+  const int S = jb.ksplit;
+  const int m0 = tl.tm * TC_M, n0 = tl.tn * TC_N;
+  const float* wp = jb.ws + (size_t)(tl.tm + tl.tn * jb.tiles_m) * S * (TC_M * TC_N);
+  float* C = (float*)jb.C;
+  const float alpha = (float)jb.alpha, beta = (float)jb.beta;
+  for (int e = threadIdx.x; e < TC_M * TC_N; e += blockDim.x) {
+    const int i = e % TC_M, c = e / TC_M;
+    const int gi = m0 + i, gj = n0 + c;
+    if (gi >= jb.M || gj >= jb.N) continue;
+    float sum = 0.f;
+    for (int q = 0; q < S; ++q) sum += wp[(size_t)q * (TC_M * TC_N) + e];
+    const long long row = jb.crow ? jb.crow[gi] : gi;
+    float* cp = C + row + (long long)gj * jb.ldc;
+    *cp = (jb.beta == 0.0) ? alpha * sum : alpha * sum + beta * *cp;
+  }
+}
+
+void gemm_tc_reduce(const GemmJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  k_gemm_tc_reduce<<<ntiles, 256, 0, s>>>(jobs, tiles);
+  count_launch();
+}
+
 }  // namespace hssmf
 
 extern "C" hssmf_status hssmf_gemm_f32(int transa, int transb, int m, int n, int k, float alpha,
@@ -318,23 +392,45 @@ extern "C" hssmf_status hssmf_gemm_f32(int transa, int transb, int m, int n, int
   j.ta = transa != 0; j.tb = transb != 0;
   j.b_exact = b_exact != 0;
   j.alpha = alpha; j.beta = beta;
-  std::vector<Tile> tiles;
-  for (int b = 0; b < ceil_div(n, GEMM_TILE_TC); ++b)
-    for (int a = 0; a < ceil_div(m, GEMM_TILE_TC); ++a) tiles.push_back(Tile{0, a, b});
-  const size_t bytes = 256 + sizeof(GemmJob) + sizeof(Tile) * tiles.size();
+  // split K when the output has fewer tiles than about two CTAs per SM
+  int nsm = 148, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int tm = ceil_div(m, GEMM_TILE_TC), tn = ceil_div(n, GEMM_TILE_TC);
+  int S = 1;
+  if (k >= 512 && (long long)tm * tn < 2LL * nsm)
+    S = std::max(1, std::min({8, (int)((2LL * nsm + tm * tn - 1) / ((long long)tm * tn)), k / 256}));
+  std::vector<Tile> tiles, rtiles;
+  for (int q = 0; q < S; ++q)
+    for (int b = 0; b < tn; ++b)
+      for (int a = 0; a < tm; ++a) tiles.push_back(Tile{0, a, b, q});
+  if (S > 1)
+    for (int b = 0; b < tn; ++b)
+      for (int a = 0; a < tm; ++a) rtiles.push_back(Tile{0, a, b, 0});
+  const size_t ws_bytes = S > 1 ? sizeof(float) * (size_t)tm * tn * S * GEMM_TILE_TC * GEMM_TILE_TC : 0;
+  const size_t bytes = 256 + sizeof(GemmJob) + sizeof(Tile) * (tiles.size() + rtiles.size()) + 256 + ws_bytes;
   char* d = nullptr;
   if (cudaMalloc(&d, bytes) != cudaSuccess) return HSSMF_ERR_CUDA;
   unsigned* st = (unsigned*)d;
   GemmJob* dj = (GemmJob*)(d + 256);
   Tile* dt = (Tile*)(d + 256 + sizeof(GemmJob));
+  Tile* dr = dt + tiles.size();
+  if (S > 1) {
+    j.ws = (float*)(((uintptr_t)(dr + rtiles.size()) + 255) & ~(uintptr_t)255);
+    j.ksplit = S;
+    j.tiles_m = tm;
+  }
   hssmf_status r = HSSMF_OK;
   unsigned hs = 0;
   if (cudaMemsetAsync(st, 0, sizeof(unsigned), s) != cudaSuccess ||
       cudaMemcpyAsync(dj, &j, sizeof(j), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(dt, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      cudaMemcpyAsync(dt, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      (S > 1 && cudaMemcpyAsync(dr, rtiles.data(), sizeof(Tile) * rtiles.size(), cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess))
     r = HSSMF_ERR_CUDA;
   if (r == HSSMF_OK) {
     gemm_tc(dj, dt, (int)tiles.size(), st, s);
+    if (S > 1) gemm_tc_reduce(dj, dr, (int)rtiles.size(), s);
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(&hs, st, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

@@ -69,6 +69,8 @@ struct Kern {
 // (three-term BF16 split, FP32 accumulation in tensor memory); status gets
 // ST_TIMEOUT if a bounded wait ran out.
 void gemm_tc(const GemmJob* jobs, const Tile* tiles, int ntiles, unsigned* status, cudaStream_t s);
+// C = alpha sum_ks partial_ks + beta C for the split-K jobs (one tile per output tile)
+void gemm_tc_reduce(const GemmJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s);
 
 // FP64 outer-iteration kernels ------------------------------------------------
 void spmv(const DevSym& ds, const double* values, const double* x, double* y, int nrhs,
