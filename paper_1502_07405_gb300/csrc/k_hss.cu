@@ -826,10 +826,13 @@ constexpr size_t kIdSmemBudget = 200 * 1024;
 // column stride of the resident matrix: 16-byte aligned columns
 __host__ __device__ inline int id_smem_ld(int d) { return (d + 3) & ~3; }
 
+// shared memory of the ID kernels: the owned columns, the pivot-column
+// buffers (one on a single CTA; two and a staging column on a cluster) and
+// the skeleton flags
 __host__ __device__ inline size_t id_smem_bytes(int d, int m, int cl, int esz) {
   const size_t mo = (size_t)(m + cl - 1) / cl;
   const size_t ld = (size_t)id_smem_ld(d);
-  return (size_t)esz * mo * ld + (size_t)esz * ld + (size_t)m + 64;
+  return (size_t)esz * mo * ld + (size_t)(cl > 1 ? 3 : 1) * esz * ld + (size_t)m + 64;
 }
 
 // Per step (every CTA of the cluster, 32 warps): the warps' proposals (the
