@@ -217,8 +217,11 @@ hssmf_status hssmf_batched_id(int prec, int njobs, const void* Y, const long lon
  *   - HSSMF_ERR_ARG for negative sizes, null arrays or leading dimensions
  *     below the stored rows; m, n or k = 0 is valid (C = beta C).
  *   - HSSMF_ERR_TIMEOUT if a bounded wait inside the kernel ran out.
- *   - Allocates and frees device scratch for the job and its tile list on
- *     every call; synchronizes the stream. */
+ *   - The operands are split once into BF16 term arrays and the product runs
+ *     as a TMA-fed tcgen05 pipeline (K split when the output has few tiles).
+ *   - Device scratch (term arrays, job and tile lists) is kept by the library
+ *     between calls and reused; calls are serialized; synchronizes the
+ *     stream. */
 hssmf_status hssmf_gemm_f32(int transa, int transb, int m, int n, int k, float alpha,
                             const float* A, long long lda, const float* B, long long ldb,
                             float beta, float* C, long long ldc, int b_exact, void* cuda_stream);

@@ -26,9 +26,11 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/hssmf.h"
+#include "gemm_tma.h"
 #include "kernels.h"
 
 namespace hssmf {
@@ -375,6 +377,44 @@ void gemm_tc_reduce(const GemmJob* jobs, const Tile* tiles, int ntiles, cudaStre
 
 }  // namespace hssmf
 
+namespace {
+// device scratch of hssmf_gemm_f32 calls: blocks kept across calls (every call
+// synchronizes its stream before returning, so the next call may reuse them);
+// a request takes the smallest free block that holds it, else a new block
+std::mutex g_scratch_mu;
+std::vector<std::pair<void*, size_t>> g_scratch;
+struct CallScratch : hssmf::TmaScratch {
+  std::vector<bool> used;
+  std::vector<std::pair<void*, size_t>> pinned;  // host staging of the job arrays
+  cudaStream_t s;
+  explicit CallScratch(cudaStream_t st) : used(g_scratch.size(), false), s(st) {}
+  void* alloc(size_t bytes) override {
+    bytes = std::max<size_t>((bytes + 255) & ~(size_t)255, 256);
+    int best = -1;
+    for (size_t i = 0; i < g_scratch.size(); ++i)
+      if (!used[i] && g_scratch[i].second >= bytes && (best < 0 || g_scratch[i].second < g_scratch[best].second))
+        best = (int)i;
+    if (best < 0) {
+      void* p = nullptr;
+      if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      g_scratch.push_back({p, bytes});
+      used.push_back(false);
+      best = (int)g_scratch.size() - 1;
+    }
+    used[best] = true;
+    return g_scratch[best].first;
+  }
+  const void* put(const void* host, size_t bytes) override {
+    void* p = alloc(bytes);
+    if (p && bytes && cudaMemcpyAsync(p, host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return nullptr;
+    return p;
+  }
+};
+}  // namespace
+
 extern "C" hssmf_status hssmf_gemm_f32(int transa, int transb, int m, int n, int k, float alpha,
                                        const float* A, long long lda, const float* B, long long ldb,
                                        float beta, float* C, long long ldc, int b_exact, void* cuda_stream) {
@@ -392,6 +432,25 @@ extern "C" hssmf_status hssmf_gemm_f32(int transa, int transb, int m, int n, int
   j.ta = transa != 0; j.tb = transb != 0;
   j.b_exact = b_exact != 0;
   j.alpha = alpha; j.beta = beta;
+  if (k > 0 && gemm_tma_available()) {  // split operands + TMA/tcgen05 pipeline
+    unsigned* st = nullptr;
+    if (cudaMalloc(&st, sizeof(unsigned)) != cudaSuccess) return HSSMF_ERR_CUDA;
+    unsigned hs = 0;
+    hssmf_status r = HSSMF_OK;
+    {
+      std::lock_guard<std::mutex> lock(g_scratch_mu);
+      CallScratch mem(s);
+      if (cudaMemsetAsync(st, 0, sizeof(unsigned), s) != cudaSuccess) r = HSSMF_ERR_CUDA;
+      if (!r && gemm_tma_batch(std::vector<GemmJob>{j}, mem, st, s) < 0) r = HSSMF_ERR_CUDA;
+      if (!r && (cudaGetLastError() != cudaSuccess ||
+                 cudaMemcpyAsync(&hs, st, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess))
+        r = HSSMF_ERR_CUDA;
+      if (cudaStreamSynchronize(s) != cudaSuccess) r = HSSMF_ERR_CUDA;
+    }
+    cudaFree(st);
+    if (!r && (hs & ST_TIMEOUT)) r = HSSMF_ERR_TIMEOUT;
+    return r;
+  }
   // split K when the output has fewer tiles than about two CTAs per SM
   int nsm = 148, dev = 0;
   cudaGetDevice(&dev);
