@@ -162,6 +162,18 @@ hssmf_status hssmf_get_upd(const hssmf_ctx* ctx, int f, int* upd);
 hssmf_status hssmf_get_phase_times(const hssmf_ctx* ctx, double* ms, int n);
 hssmf_status hssmf_set_profiling(hssmf_ctx* ctx, int on);
 
+/* Gradient of a loss L(x) with respect to the stored entries of A, for
+ * x = A^-1 b (the adjoint of hssmf_solve): with lambda = A^-T dL/dx (from
+ * hssmf_solve_T), dL/dA_ij = -sum_c lambda_i,c x_j,c, written in the order
+ * of the CSR pattern given to hssmf_analyze_grid (natural numbering):
+ * out[p] for the entry (row(p), colind[p]).  lambda and x are n x nrhs
+ * column-major device arrays with leading dimension ld; out is a device
+ * array of nnz doubles.  The paper has no counterpart; the differentiation
+ * interface of the library.  HSSMF_ERR_ARG before a factorization, for host
+ * pointers or ld < n; synchronizes the stream. */
+hssmf_status hssmf_pattern_grad(hssmf_ctx* ctx, const double* lambda, const double* x, int nrhs, int ld,
+                                double* out);
+
 /* Records of every interpolative decomposition of the last factorization
  * run with profiling on (Algorithm 1 with the adaptive scheme of Section
  * 2.2.1): 9 ints per node attempt -- front, HSS node, adaptive round of the

@@ -83,6 +83,8 @@ lib.hssmf_get_upd.argtypes = [_P, _I, _IP]
 lib.hssmf_get_phase_times.argtypes = [_P, C.POINTER(C.c_double), _I]
 lib.hssmf_set_profiling.argtypes = [_P, _I]
 lib.hssmf_get_id_trace.argtypes = [_P, _IP, _I]
+lib.hssmf_pattern_grad.argtypes = [_P, _P, _P, _I, _I, _P]
+lib.hssmf_pattern_grad.restype = C.c_int
 lib.hssmf_get_id_trace.restype = C.c_int
 lib.hssmf_last_error.argtypes = [_P]
 lib.hssmf_last_error.restype = C.c_char_p
@@ -133,6 +135,7 @@ class Solver:
         s = C.c_void_p(0 if stream is None else int(stream))
         self._check(lib.hssmf_create(C.byref(self._h), C.byref(self.opts), s), ctx=False)
         self.n = 0
+        self.nnz = 0
 
     def _check(self, st, ctx=True):
         if st != OK:
@@ -157,6 +160,7 @@ class Solver:
         n = len(rp) - 1
         self._check(lib.hssmf_analyze_grid(self._h, nx, ny, nz, n, _int_ptr(rp), _int_ptr(ci)))
         self.n = n
+        self.nnz = int(rp[-1])
 
     def factor(self, values):
         p, keep = _buf(values)
@@ -209,6 +213,14 @@ class Solver:
         buf = (C.c_double * len(self.PHASES))()
         self._check(lib.hssmf_get_phase_times(self._h, buf, len(self.PHASES)))
         return dict(zip(self.PHASES, list(buf)))
+
+    def pattern_grad(self, lam, x, out):
+        """out[p] = -sum_c lam[row(p), c] x[col(p), c] on the CSR pattern (CUDA
+        float64 tensors; lam and x column-major n x nrhs, out of length nnz)."""
+        nrhs = 1 if lam.dim() == 1 else lam.shape[1]
+        self._check(lib.hssmf_pattern_grad(self._h, C.c_void_p(lam.data_ptr()), C.c_void_p(x.data_ptr()),
+                                           int(nrhs), int(self.n), C.c_void_p(out.data_ptr())))
+        return out
 
     ID_TRACE_FIELDS = ("front", "node", "round", "d", "m", "mc", "kr", "kc", "accepted")
 

@@ -280,6 +280,28 @@ __global__ void k_spmv(const int* __restrict__ rowptr, const int* __restrict__ c
   }
 }
 
+// out[p] = -sum_c lambda[row(p) + c ld] x[col(p) + c ld] over the natural
+// CSR pattern: the gradient of L(x(A)) with respect to the stored entries of
+// A, given x = A^-1 b and lambda = A^-T dL/dx.  One thread per row.
+__global__ void k_pattern_grad(const int* __restrict__ rowptr, const int* __restrict__ colind,
+                               const double* __restrict__ lam, const double* __restrict__ x, long long ld,
+                               int n, int nrhs, double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const int j = colind[p];
+      double s = 0.0;
+      for (int c = 0; c < nrhs; ++c) s += lam[i + c * ld] * x[j + c * ld];
+      out[p] = -s;
+    }
+  }
+}
+
+void pattern_grad(const DevSym& ds, const double* lam, const double* x, long long ld, int nrhs, double* out,
+                  cudaStream_t s) {
+  k_pattern_grad<<<grid_for(ds.n), 256, 0, s>>>(ds.rowptr, ds.colind, lam, x, ld, ds.n, nrhs, out);
+  count_launch();
+}
+
 void spmv(const DevSym& ds, const double* values, const double* x, double* y, int nrhs,
           int transpose, cudaStream_t s) {
   k_spmv<<<grid_for((long long)ds.n * nrhs), 256, 0, s>>>(ds.rowptr, ds.colind, ds.tpos, values, x,

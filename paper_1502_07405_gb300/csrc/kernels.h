@@ -72,6 +72,10 @@ void gemm_tc(const GemmJob* jobs, const Tile* tiles, int ntiles, unsigned* statu
 // C = alpha sum_ks partial_ks + beta C for the split-K jobs (one tile per output tile)
 void gemm_tc_reduce(const GemmJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s);
 
+// out[p] = -sum_c lam[row(p) + c ld] x[col(p) + c ld] (gradient on the pattern)
+void pattern_grad(const DevSym& ds, const double* lam, const double* x, long long ld, int nrhs, double* out,
+                  cudaStream_t s);
+
 // FP64 outer-iteration kernels ------------------------------------------------
 void spmv(const DevSym& ds, const double* values, const double* x, double* y, int nrhs,
           int transpose, cudaStream_t s);

@@ -860,6 +860,22 @@ hssmf_status hssmf_get_phase_times(const hssmf_ctx* c, double* ms, int n) {
   return HSSMF_OK;
 }
 
+hssmf_status hssmf_pattern_grad(hssmf_ctx* c, const double* lambda, const double* x, int nrhs, int ld,
+                                double* out) {
+  if (!c) return HSSMF_ERR_ARG;
+  if (!c->on_device) return c->fail(HSSMF_ERR_ARG, "pattern_grad needs a factorization (device structure)");
+  if (!lambda || !x || !out || nrhs < 1 || ld < c->sym.n) return c->fail(HSSMF_ERR_ARG, "bad pattern_grad arguments");
+  cudaPointerAttributes a[3];
+  const void* ptr[3] = {lambda, x, out};
+  for (int q = 0; q < 3; ++q)
+    if (cudaPointerGetAttributes(&a[q], ptr[q]) != cudaSuccess || a[q].type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      return c->fail(HSSMF_ERR_ARG, "pattern_grad takes device arrays");
+    }
+  pattern_grad(c->ds, lambda, x, ld, nrhs, out, c->stream);
+  return c->cuda_check(cudaStreamSynchronize(c->stream), "pattern_grad");
+}
+
 int hssmf_get_id_trace(const hssmf_ctx* c, int* rec, int max_records) {
   if (!c) return -1;
   const int n = (int)(c->id_trace.size() / 9);

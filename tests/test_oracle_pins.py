@@ -410,3 +410,27 @@ def test_gmres_restarted_monotone_and_exact_preconditioner():
     assert its == 1
     x, its, rel = krylov.iterative_refinement(A, lambda v: Ainv @ v, b, rtol=1e-12)
     assert its <= 2
+
+
+def test_dense_adjoint_matches_central_differences():
+    """The oracle's adjoint gradient (dL/db, dL/dA on the pattern) equals
+    central finite differences of L(x) = ||x - xt||^2 on a small
+    nonsymmetric system."""
+    from oracle import adjoint
+    A = problems.grid_convdiff2d(5, 3.0, -2.0).to_scipy().tocsr()
+    n = A.shape[0]
+    rng = np.random.default_rng(3)
+    b = rng.uniform(-1, 1, n)
+    xt = rng.standard_normal(n)
+    loss = lambda Am, bb: float(np.sum((np.linalg.solve(Am.toarray(), bb) - xt) ** 2))
+    x, gb, gv = adjoint.dense_adjoint(A, b, lambda x: 2.0 * (x - xt))
+    h = 1e-6
+    for i in rng.choice(n, 5, replace=False):
+        e = np.zeros(n); e[i] = h
+        fd = (loss(A, b + e) - loss(A, b - e)) / (2 * h)
+        assert abs(fd - gb[i]) <= 1e-6 * max(1.0, abs(fd))
+    for p in rng.choice(A.nnz, 8, replace=False):
+        Ap, Am = A.copy(), A.copy()
+        Ap.data[p] += h; Am.data[p] -= h
+        fd = (loss(Ap, b) - loss(Am, b)) / (2 * h)
+        assert abs(fd - gv[p]) <= 1e-6 * max(1.0, abs(fd))
