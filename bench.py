@@ -39,6 +39,14 @@ WORKLOAD = dict(dims=(64, 64, 64), hss_min_front=1024, hss_tol=1e-4, d0=128, dd=
 WORKLOAD_NAME = ("3D 7-point Poisson 64^3 (n=262144), geometric ND (8^3 leaves), HSS on fronts >= 1024, "
                  "eps=1e-4, d0=128, dd=64, 1 RHS U[-1,1] seed 1, GMRES(30) to rel. residual 1e-10")
 CPU_SAMPLE_SIDE = 32  # oracle sample: the same problem family on a 32^3 grid
+# --config grf100: the 100^3 anisotropic variable-coefficient diffusion (kappa =
+# exp(Gaussian random field, correlation length 8 cells, sigma 1), anisotropy
+# 1:1:10, harmonic-mean faces), HSS on fronts >= 2048 at eps 1e-2; 1 and 64 RHS
+GRF100 = dict(dims=(100, 100, 100), hss_min_front=2048, hss_tol=1e-2, d0=128, dd=64, seed=0, rhs_seed=1, nrhs=1,
+              grf=True, multi_rhs=64)
+GRF100_NAME = ("3D anisotropic variable-coefficient diffusion 100^3 (n=1e6), kappa=exp(GRF corr 8, sigma 1), "
+               "anisotropy 1:1:10, HSS on fronts >= 2048, eps=1e-2, d0=128, dd=64, 1 RHS U[-1,1] seed 1, "
+               "GMRES(30) to rel. residual 1e-10")
 METRIC = "factor+solve time to rel. residual 1e-10 (mixed FP32/FP64 vs FP64), 1 GB300"
 
 
@@ -130,9 +138,17 @@ def _peaks():
 
 def _problem():
     import problems
-    A = problems.grid_poisson(WORKLOAD["dims"])
+    if WORKLOAD.get("grf"):
+        A = problems.grid_anisotropic_grf(WORKLOAD["dims"][0], 8.0, 1.0, (1.0, 1.0, 10.0), seed=WORKLOAD["seed"])
+    else:
+        A = problems.grid_poisson(WORKLOAD["dims"])
     b = problems.rhs_uniform(A.n, WORKLOAD["nrhs"], WORKLOAD["rhs_seed"])
     return A, b
+
+
+def problems_rhs(n, nrhs):
+    import problems
+    return problems.rhs_uniform(n, nrhs, WORKLOAD["rhs_seed"])
 
 
 def _solver(A, precision):
@@ -213,6 +229,20 @@ def run_ours(args):
     phases = s.get_phase_times()
     stp = s.get_stats()
     s.set_profiling(False)
+    # the same factorization with 32 (64 for grf100) right-hand sides (solve time, GMRES per column)
+    nmulti = WORKLOAD.get("multi_rhs", 32)
+    b32 = problems_rhs(A.n, nmulti)
+    b32t = torch.tensor(np.ascontiguousarray(b32.T), device="cuda").t()  # column-major view
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    x32 = s.solve(b32t)
+    e1.record()
+    torch.cuda.synchronize()
+    t32 = e0.elapsed_time(e1)
+    r32 = np.linalg.norm(b32 - A.to_scipy() @ x32.cpu().numpy(), axis=0) / np.linalg.norm(b32, axis=0)
+    rhs32 = {"nrhs": nmulti, "solve_ms": round(t32, 2), "max_relres": float(r32.max()),
+             "iterations_max": s.get_stats()["iterations"]}
     # e2e through the C ABI with host buffers --------------------------------
     vals_h = np.ascontiguousarray(A.values)
     b_h = np.asfortranarray(b)
@@ -271,12 +301,13 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(b.nbytes)},
         "roofline": roof,
         "solve_roofline": solve_roof,
+        "multi_rhs": rhs32,
         "clocks": clk,
     }
     if ws > 1:
         line["systems_per_s"] = round(ws / (ms * 1e-3), 4)
     if rank == 0:
-        if ws == 1 and not args.no_cpu:
+        if ws == 1 and not args.no_cpu and not WORKLOAD.get("grf"):
             line["cpu_baseline"] = cpu_baseline(st["factor_flops"])
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -373,7 +404,14 @@ def main():
                     help="forms to time (profiling runs use one)")
     ap.add_argument("--small", action="store_true",
                     help="32^3 grid instead of 64^3 (profiling captures only; not a bench line)")
+    ap.add_argument("--config", choices=["poisson64", "grf100"], default="poisson64",
+                    help="workload: the 64^3 Poisson benchmark (default) or the 100^3 anisotropic one")
     args = ap.parse_args()
+    global WORKLOAD_NAME
+    if args.config == "grf100":
+        WORKLOAD.clear()
+        WORKLOAD.update(GRF100)
+        WORKLOAD_NAME = GRF100_NAME
     if args.small:
         WORKLOAD["dims"] = (32, 32, 32)
     if args.impl == "reference":

@@ -22,6 +22,8 @@ __all__ = [
     "grid_poisson",
     "grid_convdiff2d",
     "grid_shifted_laplacian3d",
+    "grid_anisotropic_grf",
+    "gaussian_random_field",
     "rhs_uniform",
     "CSR",
 ]
@@ -136,6 +138,54 @@ def grid_shifted_laplacian3d(side, sigma):
         raise ValueError("sigma needs one value per cell")
     rows = np.repeat(np.arange(n), np.diff(rowptr))
     vals = np.where(kinds == 0, 6.0 + sigma[rows], -1.0)
+    return CSR(n, rowptr, cols, vals)
+
+
+def gaussian_random_field(side, corr_len=8.0, sigma=1.0, seed=0):
+    """A seeded stationary Gaussian random field on side^3 cells: white noise
+    filtered in Fourier space by a Gaussian kernel of correlation length
+    corr_len cells (periodic), shifted and scaled to mean 0 and standard
+    deviation sigma.  Returned in natural order (x fastest)."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal((side, side, side))
+    k = 2.0 * np.pi * np.fft.fftfreq(side)
+    kr = 2.0 * np.pi * np.fft.rfftfreq(side)
+    k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + kr[None, None, :] ** 2
+    g = np.fft.irfftn(np.fft.rfftn(w) * np.exp(-0.5 * k2 * corr_len ** 2), s=w.shape)
+    g = (g - g.mean()) / max(g.std(), 1e-300) * sigma
+    # array axes (a, b, c) -> grid (z, y, x): natural index x + side (y + side z)
+    return np.ascontiguousarray(g).reshape(-1)
+
+
+def grid_anisotropic_grf(side, corr_len=8.0, sigma=1.0, aniso=(1.0, 1.0, 10.0), seed=0):
+    """-div(K grad u) on the side^3 interior grid, 7-point finite volumes,
+    homogeneous Dirichlet conditions: cell coefficient kappa = exp(g) with g
+    a Gaussian random field (gaussian_random_field), the face between two
+    cells the harmonic mean of their coefficients times the anisotropy factor
+    of the face's axis (x, y, z), a boundary face the cell's own coefficient
+    times that factor.  Symmetric positive definite; unscaled (h = 1)."""
+    offs = _offsets(3, 7)
+    n, rowptr, cols, kinds, _ = _stencil_pattern((side, side, side), offs)
+    kappa = np.exp(gaussian_random_field(side, corr_len, sigma, seed))
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    axis_of = np.array([-1, 0, 0, 1, 1, 2, 2])  # offsets: self, -x, +x, -y, +y, -z, +z
+    a = np.asarray(aniso, dtype=np.float64)
+    off = kinds != 0
+    ki, kj = kappa[rows[off]], kappa[cols[off]]
+    face = 2.0 * ki * kj / (ki + kj) * a[axis_of[kinds[off]]]
+    vals = np.zeros(len(cols))
+    vals[off] = -face
+    # diagonal: all six faces of the cell (interior faces from the row's
+    # off-diagonal entries, boundary faces from the cell's own coefficient)
+    diag = np.zeros(n)
+    np.add.at(diag, rows[off], face)
+    idx = np.arange(n)
+    x, y, z = idx % side, (idx // side) % side, idx // (side * side)
+    nb = [(x == 0).astype(float) + (x == side - 1), (y == 0).astype(float) + (y == side - 1),
+          (z == 0).astype(float) + (z == side - 1)]
+    for ax in range(3):
+        diag += nb[ax] * kappa * a[ax]
+    vals[kinds == 0] = diag[rows[kinds == 0]]
     return CSR(n, rowptr, cols, vals)
 
 

@@ -434,3 +434,22 @@ def test_dense_adjoint_matches_central_differences():
         Ap.data[p] += h; Am.data[p] -= h
         fd = (loss(Ap, b) - loss(Am, b)) / (2 * h)
         assert abs(fd - gv[p]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_anisotropic_grf_operator():
+    """The variable-coefficient operator: symmetric positive definite;
+    constant coefficient (sigma -> 0) gives the anisotropic 7-point Laplacian
+    (faces 1, 1, 10); interior rows of any coefficient sum to zero; the
+    random field has mean 0 and standard deviation sigma."""
+    A = problems.grid_anisotropic_grf(6, sigma=1.0, seed=4).to_scipy()
+    assert abs(A - A.T).max() == 0.0
+    assert np.linalg.eigvalsh(A.toarray()).min() > 0
+    c = problems.grid_anisotropic_grf(6, sigma=1e-14, seed=4).to_scipy().toarray()
+    i = 1 + 6 * (1 + 6 * 1)  # interior cell (1, 1, 1)
+    assert abs(c[i, i] - 24.0) < 1e-9
+    assert abs(c[i, i - 1] + 1.0) < 1e-9 and abs(c[i, i - 6] + 1.0) < 1e-9 and abs(c[i, i - 36] + 10.0) < 1e-9
+    interior = [x + 6 * (y + 6 * z) for x in range(1, 5) for y in range(1, 5) for z in range(1, 5)]
+    rs = np.asarray(A.sum(axis=1)).ravel()
+    assert np.abs(rs[interior]).max() < 1e-12
+    g = problems.gaussian_random_field(16, 4.0, 2.0, seed=9)
+    assert abs(g.mean()) < 1e-12 and abs(g.std() - 2.0) < 1e-12
