@@ -161,3 +161,30 @@ def test_solve_T_gmres_to_1e10(prec):
     s3 = _gpu(A3, dims3, hss_tol=1e-3, hss_min_front=256, d0=64, dd=32, precision=prec)
     x3 = s3.solve_T(b3)
     assert np.all(_relres(A3, x3, b3) <= 1e-10)
+
+
+@pytest.mark.parametrize("kind", ["poisson", "grf"])
+def test_fp64_single_application_reproduces_oracle_3d(kind):
+    """With the same seed, the FP64 form takes the oracle's decisions (ranks,
+    skeletons, adaptive rounds) node by node, so one application of the
+    compressed factorization (eps 1e-4, up to 3 adaptive rounds) agrees with
+    the oracle's to rounding, not just in quality.  The FP32 form takes its own
+    rounding-driven pivot choices: its residual is only held to 2x."""
+    side = 20
+    A = problems.grid_anisotropic_grf(side, 8.0, 1.0, (1.0, 1.0, 10.0), seed=0) if kind == "grf" \
+        else problems.grid_poisson((side,) * 3)
+    dims = (side,) * 3
+    b = problems.rhs_uniform(A.n, 1, 1)
+    kw = dict(hss_tol=1e-4, d0=64, dd=32, hss_min_front=256, hss_leaf=64)
+    fo = _oracle(A, dims, **kw)
+    xo = mf.apply_inverse(fo, b)
+    ro = _relres(A, xo, b)[0]
+    assert ro > 1e-5  # the compression is inexact at this tolerance
+    s = _gpu(A, dims, maxit=0, precision=0, **kw)
+    x = s.solve(b)
+    assert s.get_stats()["n_hss_fronts"] == len(mf.hss_stats(fo))
+    assert s.get_stats()["max_rank"] == max(r for _, _, r, _, _ in mf.hss_stats(fo))
+    assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
+    s32 = _gpu(A, dims, maxit=0, precision=1, **kw)
+    r32 = _relres(A, s32.solve(b), b)[0]
+    assert r32 <= 2.0 * ro, (r32, ro)

@@ -144,3 +144,24 @@ def test_shared_memory_id_with_global_overflow(prec, shape):
     U[piv[k:], :] = Xg.T
     err = np.linalg.norm(Y[:, piv[:k]] @ U.T - Y) / np.linalg.norm(Y)
     assert err <= 50 * eps
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_largest_node_shape_all_kernel_families(prec):
+    """The largest node shape of the 100^3 workload (d = 2048 samples, m = 4000
+    columns, rank ~1800 at eps 1e-4) on the shared-memory cluster kernel with
+    global overflow (-1), the single-CTA kernel (0) and the 16-CTA
+    L2-resident cluster kernel (16): the rank is LAPACK's column-pivoted QR
+    count under the same rule (FP32: within one) and the interpolation error
+    stays at the tolerance."""
+    sl = pytest.importorskip("scipy.linalg")
+    eps = 1e-4
+    Y = _decaying(2048, 4000, 375.0, 7)
+    dg = np.abs(np.diag(sl.qr(Y, mode="r", pivoting=True)[0]))
+    kref = int((dg > eps * dg[0]).sum())
+    for mode in (-1, 0, 16):
+        (k, piv, X), = _run_ids([Y], eps, prec, mode)
+        assert abs(k - kref) <= (0 if prec == 0 else 1), (mode, k, kref)
+        assert sorted(piv.tolist()) == list(range(Y.shape[1]))
+        err = np.linalg.norm(Y[:, piv[k:]] - Y[:, piv[:k]] @ X) / np.linalg.norm(Y)
+        assert err <= 2 * eps, (mode, err)
