@@ -49,6 +49,16 @@ GRF100 = dict(dims=(100, 100, 100), hss_min_front=2048, hss_tol=1e-4, d0=128, dd
 GRF100_NAME = ("3D anisotropic variable-coefficient diffusion 100^3 (n=1e6), kappa=exp(GRF corr 8, sigma 1), "
                "anisotropy 1:1:10, HSS on fronts >= 2048, eps={eps:g}, d0=128, dd=64, 1 RHS U[-1,1] seed 1, "
                "GMRES(30) to rel. residual 1e-10")
+# --config batch256: 256 independent upwinded 2D convection-diffusion systems
+# (sides uniform on 32..256, one velocity per system with components uniform on
+# [-50, 50], nu 1), factored and solved together, 16 RHS each, eps 1e-6, HSS on
+# fronts >= 256, refinement to 1e-10 in every system
+BATCH256 = dict(nsys=256, hss_min_front=256, hss_tol=1e-6, d0=128, dd=64, seed=0, rhs_seed=1, nrhs=16,
+                batch=True, multi_rhs=0)
+BATCH256_NAME = ("batch of 256 upwinded 2D convection-diffusion systems (sides U{{32..256}}, velocity U[-50,50]^2 per "
+                 "system, nu 1, seed 0; n={n}), one elimination forest with levels batched over all systems, HSS on "
+                 "fronts >= 256, eps=1e-6, d0=128, dd=64, 16 RHS U[-1,1] seed 1, iterative refinement to rel. "
+                 "residual 1e-10 in every system and column")
 METRIC = "factor+solve time to rel. residual 1e-10 (mixed FP32/FP64 vs FP64), 1 GB300"
 
 
@@ -140,6 +150,12 @@ def _peaks():
 
 def _problem():
     import problems
+    if WORKLOAD.get("batch"):
+        sides, _, A = problems.batch_convdiff2d(WORKLOAD["nsys"], seed=WORKLOAD["seed"])
+        WORKLOAD["grids"] = [(k, k, 1) for k in sides]
+        WORKLOAD["sys_off"] = [0] + list(__import__("numpy").cumsum([k * k for k in sides]))
+        b = problems.rhs_uniform(A.n, WORKLOAD["nrhs"], WORKLOAD["rhs_seed"])
+        return A, b
     if WORKLOAD.get("grf"):
         A = problems.grid_anisotropic_grf(WORKLOAD["dims"][0], 8.0, 1.0, (1.0, 1.0, 10.0), seed=WORKLOAD["seed"])
     else:
@@ -159,8 +175,34 @@ def _solver(A, precision):
                            d0=WORKLOAD["d0"], dd=WORKLOAD["dd"], seed=WORKLOAD["seed"],
                            precision=precision)
     s = P.Solver(o)
-    s.analyze_grid(WORKLOAD["dims"], A.rowptr, A.colind)
+    if WORKLOAD.get("batch"):
+        s.analyze_grids(WORKLOAD["grids"], A.rowptr, A.colind)
+    else:
+        s.analyze_grid(WORKLOAD["dims"], A.rowptr, A.colind)
     return s
+
+
+def _relres(A, x, b):
+    """Largest relative residual over the right-hand sides (and, for a batch,
+    over the systems)."""
+    import numpy as np
+    x = x.reshape(A.n, -1)
+    b = b.reshape(A.n, -1)
+    r = b - A.to_scipy() @ x
+    if not WORKLOAD.get("batch"):
+        return float((np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0)).max())
+    off = WORKLOAD["sys_off"]
+    return float(max((np.linalg.norm(r[off[g]:off[g + 1]], axis=0) /
+                      np.linalg.norm(b[off[g]:off[g + 1]], axis=0)).max() for g in range(len(off) - 1)))
+
+
+def _device_rhs(b):
+    """b as a device tensor: a vector, or a column-major view for several RHS."""
+    import numpy as np
+    import torch
+    if b.shape[1] == 1:
+        return torch.tensor(np.ascontiguousarray(b[:, 0]), device="cuda")
+    return torch.tensor(np.ascontiguousarray(b.T), device="cuda").t()
 
 
 def _time_steps(s, vals, bt, steps, warmup, ws):
@@ -218,8 +260,7 @@ def _time_fp64(s, vals, bt, steps, ws, A, b):
         torch.cuda.synchronize()
         out.append(_barrier_max(e0.elapsed_time(e1), ws))
     if info is not None:
-        xr = x.cpu().numpy()
-        info["relres"] = float(np.linalg.norm(b - A.to_scipy() @ xr) / np.linalg.norm(b))
+        info["relres"] = _relres(A, x.cpu().numpy(), b)
         info["note"] = "GMRES(30) reached maxit before 1e-10; fp64_ms_per_step times factor + maxit iterations"
     return out, info
 
@@ -235,7 +276,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     A, b = _problem()
     vals = torch.tensor(A.values, device="cuda")
-    bt = torch.tensor(np.ascontiguousarray(b[:, 0]), device="cuda")
+    bt = _device_rhs(b)
     if args.form == "fp64":  # profiling of the plain FP64 form alone
         s64 = _solver(A, 0)
         t64, _ = _time_steps(s64, vals, bt, args.steps, args.warmup, ws)
@@ -254,8 +295,7 @@ def run_ours(args):
     times, x = _time_steps(s, vals, bt, args.steps, 0, ws)
     clk = clocks.stop()
     st = s.get_stats()
-    xr = x.cpu().numpy()
-    relres = float(np.linalg.norm(b[:, 0] - A.to_scipy() @ xr) / np.linalg.norm(b[:, 0]))
+    relres = _relres(A, x.cpu().numpy(), b)
     if args.form == "mixed":  # profiling of the mixed form alone
         if rank == 0:
             print(json.dumps({"form": "mixed", "ms_per_step": times, "relres": relres,
@@ -272,18 +312,19 @@ def run_ours(args):
     s.set_profiling(False)
     # the same factorization with 32 (64 for grf100) right-hand sides (solve time, GMRES per column)
     nmulti = WORKLOAD.get("multi_rhs", 32)
-    b32 = problems_rhs(A.n, nmulti)
-    b32t = torch.tensor(np.ascontiguousarray(b32.T), device="cuda").t()  # column-major view
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    x32 = s.solve(b32t)
-    e1.record()
-    torch.cuda.synchronize()
-    t32 = e0.elapsed_time(e1)
-    r32 = np.linalg.norm(b32 - A.to_scipy() @ x32.cpu().numpy(), axis=0) / np.linalg.norm(b32, axis=0)
-    rhs32 = {"nrhs": nmulti, "solve_ms": round(t32, 2), "max_relres": float(r32.max()),
-             "iterations_max": s.get_stats()["iterations"]}
+    rhs32 = None
+    if nmulti:
+        b32 = problems_rhs(A.n, nmulti)
+        b32t = torch.tensor(np.ascontiguousarray(b32.T), device="cuda").t()  # column-major view
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x32 = s.solve(b32t)
+        e1.record()
+        torch.cuda.synchronize()
+        t32 = e0.elapsed_time(e1)
+        rhs32 = {"nrhs": nmulti, "solve_ms": round(t32, 2), "max_relres": _relres(A, x32.cpu().numpy(), b32),
+                 "iterations_max": s.get_stats()["iterations"]}
     # e2e through the C ABI with host buffers --------------------------------
     vals_h = np.ascontiguousarray(A.values)
     b_h = np.asfortranarray(b)
@@ -299,7 +340,7 @@ def run_ours(args):
     # plain FP64 form ---------------------------------------------------------
     s64 = _solver(A, 0)
     fp64_steps = args.fp64_steps if args.fp64_steps is not None else max(1, min(args.steps, 3))
-    t64, fp64_conv = _time_fp64(s64, vals, bt, fp64_steps, ws, A, b[:, 0])
+    t64, fp64_conv = _time_fp64(s64, vals, bt, fp64_steps, ws, A, b)
     st64 = s64.get_stats()
     s64.close()
     ms = float(np.median(times))
@@ -328,7 +369,9 @@ def run_ours(args):
         "metric": METRIC, "value": round(ms, 2), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 factor + f64 GMRES", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "form": "mixed (FP32 HSS factorization preconditioning FP64 GMRES)",
+        "config": {"workload": WORKLOAD_NAME.format(n=A.n) if WORKLOAD.get("batch") else WORKLOAD_NAME,
+                   "form": ("mixed (FP32 factorization, FP64 refinement)" if WORKLOAD.get("batch")
+                            else "mixed (FP32 HSS factorization preconditioning FP64 GMRES)"),
                    "l2": "no flush: factor storage and inputs are GBs, far larger than L2",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "fp64_ms_per_step": round(float(np.median(t64)), 2),
@@ -352,7 +395,7 @@ def run_ours(args):
     if ws > 1:
         line["systems_per_s"] = round(ws / (ms * 1e-3), 4)
     if rank == 0:
-        if ws == 1 and not args.no_cpu and not WORKLOAD.get("grf"):
+        if ws == 1 and not args.no_cpu and not WORKLOAD.get("grf") and not WORKLOAD.get("batch"):
             line["cpu_baseline"] = cpu_baseline(st["factor_flops"])
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -449,13 +492,18 @@ def main():
                     help="forms to time (profiling runs use one)")
     ap.add_argument("--small", action="store_true",
                     help="32^3 grid instead of 64^3 (profiling captures only; not a bench line)")
-    ap.add_argument("--config", choices=["poisson64", "grf100"], default="poisson64",
-                    help="workload: the 64^3 Poisson benchmark (default) or the 100^3 anisotropic one")
+    ap.add_argument("--config", choices=["poisson64", "grf100", "batch256"], default="poisson64",
+                    help="workload: the 64^3 Poisson benchmark (default), the 100^3 anisotropic one, or the "
+                         "batch of 256 convection-diffusion systems")
     ap.add_argument("--hss-tol", type=float, default=None, help="override the workload's HSS tolerance")
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 form (default min(steps, 3))")
     args = ap.parse_args()
     global WORKLOAD_NAME
-    if args.config == "grf100":
+    if args.config == "batch256":
+        WORKLOAD.clear()
+        WORKLOAD.update(BATCH256)
+        WORKLOAD_NAME = BATCH256_NAME
+    elif args.config == "grf100":
         WORKLOAD.clear()
         WORKLOAD.update(GRF100)
         if args.hss_tol is not None:

@@ -110,6 +110,20 @@ hssmf_status hssmf_create(hssmf_ctx** ctx, const hssmf_opts* opts, void* cuda_st
 hssmf_status hssmf_analyze_grid(hssmf_ctx* ctx, int nx, int ny, int nz, int n,
                                 const int* rowptr_host, const int* colind_host);
 
+/* Symbolic phase for nsys independent grid problems solved together as one
+ * block-diagonal matrix.  dims holds 3 sides per grid (host, 3 * nsys ints);
+ * grid s owns the natural indices after those of grids 0..s-1, numbered
+ * x + nx*(y + ny*z) inside the grid; n is the total size.  No pattern edge
+ * may join two grids (HSSMF_ERR_ARG).  Each grid is ordered as by
+ * hssmf_analyze_grid; the elimination forest is their trees side by side
+ * and every level of the factorization and of the solve is one batch over
+ * the fronts of all grids at that height.  hssmf_solve then runs iterative
+ * refinement (FP64 residuals, the factorization as M^-1) on all grids at
+ * once until every grid's relative residual is <= rtol for every column
+ * (HSSMF_ERR_NOCONV after maxit applications); nsys * nrhs <= 131072. */
+hssmf_status hssmf_analyze_grids(hssmf_ctx* ctx, int nsys, const int* dims_host, int n,
+                                 const int* rowptr_host, const int* colind_host);
+
 /* Numerical factorization (Sections 3.2 and 4): values are the nnz matrix
  * entries in the CSR order given to analyze (host or device, FP64).
  * Fronts below hss_min_front are assembled by extend-add and partially
@@ -125,7 +139,9 @@ hssmf_status hssmf_factor(hssmf_ctx* ctx, const double* values);
  * sweep, Section 3.3).  Otherwise iterative refinement (no HSS front) or
  * right-preconditioned GMRES(restart) with modified Gram-Schmidt and
  * x0 = 0 (HSS fronts present) runs every column until its true relative
- * residual is <= rtol; HSSMF_ERR_NOCONV if one does not within maxit. */
+ * residual is <= rtol; HSSMF_ERR_NOCONV if one does not within maxit.
+ * After hssmf_analyze_grids with nsys > 1: refinement with per-grid
+ * residuals (see there). */
 hssmf_status hssmf_solve(hssmf_ctx* ctx, const double* B, double* X, int nrhs, int ldb);
 
 /* Same for A^T X = B (Section 3.3 applied to A^T): dense fronts apply

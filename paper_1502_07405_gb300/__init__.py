@@ -74,6 +74,7 @@ lib.hssmf_default_opts.argtypes = [C.POINTER(Options)]
 lib.hssmf_default_opts.restype = None
 lib.hssmf_create.argtypes = [C.POINTER(_P), C.POINTER(Options), _P]
 lib.hssmf_analyze_grid.argtypes = [_P, _I, _I, _I, _I, _IP, _IP]
+lib.hssmf_analyze_grids.argtypes = [_P, _I, _IP, _I, _IP, _IP]
 lib.hssmf_factor.argtypes = [_P, _P]
 lib.hssmf_solve.argtypes = [_P, _P, _P, _I, _I]
 lib.hssmf_solve_T.argtypes = [_P, _P, _P, _I, _I]
@@ -90,7 +91,7 @@ lib.hssmf_last_error.argtypes = [_P]
 lib.hssmf_last_error.restype = C.c_char_p
 lib.hssmf_destroy.argtypes = [_P]
 lib.hssmf_destroy.restype = None
-for _f in ("hssmf_create", "hssmf_analyze_grid", "hssmf_factor", "hssmf_solve", "hssmf_solve_T",
+for _f in ("hssmf_create", "hssmf_analyze_grid", "hssmf_analyze_grids", "hssmf_factor", "hssmf_solve", "hssmf_solve_T",
            "hssmf_get_stats", "hssmf_get_symbolic", "hssmf_get_upd", "hssmf_get_phase_times",
            "hssmf_set_profiling"):
     getattr(lib, _f).restype = C.c_int
@@ -159,6 +160,18 @@ class Solver:
         ci = np.ascontiguousarray(colind, dtype=np.int32)
         n = len(rp) - 1
         self._check(lib.hssmf_analyze_grid(self._h, nx, ny, nz, n, _int_ptr(rp), _int_ptr(ci)))
+        self.n = n
+        self.nnz = int(rp[-1])
+
+    def analyze_grids(self, dims_list, rowptr, colind):
+        """Several independent grids as one block-diagonal system (grid s
+        owns the natural indices after grids 0..s-1)."""
+        dims = np.ascontiguousarray([(list(d) + [1, 1])[:3] for d in dims_list], dtype=np.int32).reshape(-1)
+        rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(colind, dtype=np.int32)
+        n = len(rp) - 1
+        self._check(lib.hssmf_analyze_grids(self._h, len(dims_list), _int_ptr(dims), n, _int_ptr(rp),
+                                            _int_ptr(ci)))
         self.n = n
         self.nnz = int(rp[-1])
 

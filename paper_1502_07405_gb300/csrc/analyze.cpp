@@ -17,6 +17,10 @@
 // I^upd, ascending.  The F22 cluster tree halves the I^upd list at
 // floor(n/2) until a node has <= hss_leaf indices; the front tree is
 // root -> [F11 tree, F22 tree] (the F11 tree alone without I^upd).
+// Several independent grids (a block-diagonal matrix, grid s owning the
+// natural indices [sys_off[s], sys_off[s+1])) are ordered one after the other:
+// the elimination forest is the concatenation of their trees in postorder and
+// a front's level is its height, so one level schedule covers every system.
 #include "analyze.h"
 
 #include <algorithm>
@@ -41,11 +45,12 @@ struct Builder {
   int nx, ny, nz, nd_leaf, hss_leaf;
   std::vector<int> perm;
   std::vector<FrontSym> fronts;
+  int base = 0;  // natural index of vertex (0, 0, 0) of the grid being ordered
 
   void box_vertices(const Box& b) {
     for (int z = b[2]; z < b[5]; ++z)
       for (int y = b[1]; y < b[4]; ++y)
-        for (int x = b[0]; x < b[3]; ++x) perm.push_back(x + nx * (y + ny * z));
+        for (int x = b[0]; x < b[3]; ++x) perm.push_back(base + x + nx * (y + ny * z));
   }
 
   // Recursive bisection of a box into pieces; appends vertices and adds the
@@ -121,38 +126,68 @@ int halving(ClusterTree& t, int lo, int hi, int b) {
 
 std::string analyze_grid(int nx, int ny, int nz, int n, const int* rowptr, const int* colind,
                          int nd_leaf, int hss_leaf, Symbolic& out) {
-  if (nx < 1 || ny < 1 || nz < 1 || (long)nx * ny * nz != n) return "grid dims do not match n";
+  const int dims[3] = {nx, ny, nz};
+  return analyze_grids(1, dims, n, rowptr, colind, nd_leaf, hss_leaf, out);
+}
+
+std::string analyze_grids(int nsys, const int* dims, int n, const int* rowptr, const int* colind,
+                          int nd_leaf, int hss_leaf, Symbolic& out) {
+  if (nsys < 1 || !dims) return "at least one grid is required";
+  std::vector<int> off(nsys + 1, 0);
+  for (int s = 0; s < nsys; ++s) {
+    const int* d = dims + 3 * s;
+    if (d[0] < 1 || d[1] < 1 || d[2] < 1) return "grid sides must be positive";
+    const long long ns = (long long)d[0] * d[1] * d[2];
+    if (off[s] + ns > 0x7fffffffLL) return "total grid size exceeds 2^31 - 1";
+    off[s + 1] = off[s] + (int)ns;
+  }
+  if (off[nsys] != n) return "grid dims do not match n";
   if (nd_leaf < 1 || hss_leaf < 1) return "nd_leaf and hss_leaf must be positive";
   if (!rowptr || !colind) return "null CSR pattern";
   if (rowptr[0] != 0) return "rowptr[0] must be 0";
   for (int i = 0; i < n; ++i)
     if (rowptr[i + 1] < rowptr[i]) return "rowptr not monotone";
   out = Symbolic();
-  out.nx = nx; out.ny = ny; out.nz = nz; out.n = n;
+  out.nx = dims[0]; out.ny = dims[1]; out.nz = dims[2]; out.n = n;
+  out.nsys = nsys;
+  out.sys_off = off;
   out.nnz = rowptr[n];
   out.nd_leaf = nd_leaf;
   out.hss_leaf = hss_leaf;
-  // pattern checks: in range, ascending, grid neighbours, structurally symmetric
+  // pattern checks: in range, ascending, neighbours in the same grid,
+  // structurally symmetric
   out.tpos.assign(out.nnz, -1);
-  for (int i = 0; i < n; ++i) {
-    int xi = i % nx, yi = (i / nx) % ny, zi = i / (nx * ny);
-    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-      int j = colind[p];
-      if (j < 0 || j >= n) return "column index out of range";
-      if (p > rowptr[i] && colind[p - 1] >= j) return "column indices not ascending";
-      int xj = j % nx, yj = (j / nx) % ny, zj = j / (nx * ny);
-      if (std::abs(xi - xj) > 1 || std::abs(yi - yj) > 1 || std::abs(zi - zj) > 1)
-        return "pattern edge joins vertices that are not grid neighbours";
-      const int* b = colind + rowptr[j];
-      const int* e = colind + rowptr[j + 1];
-      const int* f = std::lower_bound(b, e, i);
-      if (f == e || *f != i) return "pattern is not structurally symmetric";
-      out.tpos[p] = (int)(f - colind);
+  for (int s = 0; s < nsys; ++s) {
+    const int nx = dims[3 * s], ny = dims[3 * s + 1], b0 = off[s], b1 = off[s + 1];
+    for (int i = b0; i < b1; ++i) {
+      const int li = i - b0;
+      const int xi = li % nx, yi = (li / nx) % ny, zi = li / (nx * ny);
+      for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        int j = colind[p];
+        if (j < 0 || j >= n) return "column index out of range";
+        if (p > rowptr[i] && colind[p - 1] >= j) return "column indices not ascending";
+        if (j < b0 || j >= b1) return "pattern edge joins two grids";
+        const int lj = j - b0;
+        const int xj = lj % nx, yj = (lj / nx) % ny, zj = lj / (nx * ny);
+        if (std::abs(xi - xj) > 1 || std::abs(yi - yj) > 1 || std::abs(zi - zj) > 1)
+          return "pattern edge joins vertices that are not grid neighbours";
+        const int* b = colind + rowptr[j];
+        const int* e = colind + rowptr[j + 1];
+        const int* f = std::lower_bound(b, e, i);
+        if (f == e || *f != i) return "pattern is not structurally symmetric";
+        out.tpos[p] = (int)(f - colind);
+      }
     }
   }
-  Builder B{nx, ny, nz, nd_leaf, hss_leaf, {}, {}};
+  Builder B{dims[0], dims[1], dims[2], nd_leaf, hss_leaf, {}, {}};
   B.perm.reserve(n);
-  B.rec(Box{0, 0, 0, nx, ny, nz});
+  for (int s = 0; s < nsys; ++s) {
+    B.nx = dims[3 * s];
+    B.ny = dims[3 * s + 1];
+    B.nz = dims[3 * s + 2];
+    B.base = off[s];
+    B.rec(Box{0, 0, 0, B.nx, B.ny, B.nz});
+  }
   out.perm = std::move(B.perm);
   out.fronts = std::move(B.fronts);
   if ((int)out.perm.size() != n) return "internal: ordering size mismatch";

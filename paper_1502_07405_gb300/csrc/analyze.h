@@ -42,7 +42,9 @@ struct FrontSym {
 };
 
 struct Symbolic {
-  int nx = 0, ny = 0, nz = 0, n = 0, nnz = 0;
+  int nx = 0, ny = 0, nz = 0, n = 0, nnz = 0;  // grid sides: those of the first grid
+  int nsys = 1;                 // independent grids (block-diagonal systems)
+  std::vector<int> sys_off;     // natural index range of grid s: [sys_off[s], sys_off[s+1])
   int nd_leaf = 8, hss_leaf = 128;
   std::vector<int> perm;   // perm[new] = natural
   std::vector<int> iperm;  // iperm[natural] = new
@@ -54,5 +56,10 @@ struct Symbolic {
 // Returns an empty string on success, else an error message.
 std::string analyze_grid(int nx, int ny, int nz, int n, const int* rowptr, const int* colind,
                          int nd_leaf, int hss_leaf, Symbolic& out);
+// nsys grids (dims: 3 sides per grid) of one block-diagonal matrix, grid s
+// owning the natural indices after those of grids 0..s-1: one elimination
+// forest with a common level schedule.
+std::string analyze_grids(int nsys, const int* dims, int n, const int* rowptr, const int* colind,
+                          int nd_leaf, int hss_leaf, Symbolic& out);
 
 }  // namespace hssmf

@@ -151,6 +151,7 @@ struct FrontRt {
   void* Rch[2] = {nullptr, nullptr};
   long long gidx_off = 0;
   long long pos_off[2] = {-1, -1};  // ints offset of the children's positions in I_i
+  long long rch_off[2] = {-1, -1};  // ints offset of the children's I^upd, grid-local (keys of R)
   std::vector<NodeRt> nd;
   std::vector<int> height;
   int tree_h = 0;
@@ -242,13 +243,20 @@ hssmf_status hss_prepare(hssmf_ctx& c) {
     F.nf = f.nf();
     F.ns = f.ns();
     F.nu = f.nu();
+    // R is keyed by the row's index inside its own grid, so a grid factored
+    // in a batch draws the same sketch as when factored alone
+    const int base = S.sys_off.empty()
+                         ? 0
+                         : *(std::upper_bound(S.sys_off.begin(), S.sys_off.end(), f.sep_begin) - 1);
     F.gidx_off = (long long)c.ints_host.size();
-    for (int v = f.sep_begin; v < f.sep_end; ++v) c.ints_host.push_back(v);
-    c.ints_host.insert(c.ints_host.end(), f.upd.begin(), f.upd.end());
+    for (int v = f.sep_begin; v < f.sep_end; ++v) c.ints_host.push_back(v - base);
+    for (int g : f.upd) c.ints_host.push_back(g - base);
     for (int k = 0; k < f.nchild; ++k) {
       const FrontSym& ch = S.fronts[f.child[k]];
       F.pos_off[k] = (long long)c.ints_host.size();
       c.ints_host.insert(c.ints_host.end(), ch.pos_in_parent.begin(), ch.pos_in_parent.end());
+      F.rch_off[k] = (long long)c.ints_host.size();
+      for (int g : ch.upd) c.ints_host.push_back(g - base);
     }
     const ClusterTree& t = f.tree;
     F.nd.assign(t.size(), NodeRt());
@@ -452,7 +460,8 @@ struct Ctx {  // per-call helpers
 };
 
 // Columns [dprev, d) of R, R(I^upd_child, :), S^r and S^c of every listed
-// front (eq. FtimesR; eq. Rmerge holds because R depends only on global rows).
+// front (eq. FtimesR; eq. Rmerge holds because R depends only on the row's
+// index, taken inside its grid).
 template <typename T>
 void sample_fronts(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
   hssmf_ctx& c = X.c;
@@ -470,7 +479,7 @@ void sample_fronts(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     for (int k = 0; k < f.nchild; ++k) {
       const DFront& ch = c.fronts_host[f.child[k]];
       if (ch.nu == 0) continue;
-      pj.push_back(PhiloxJob{X.ints(ch.upd_off), F->Rch[k], ch.nu, ch.nu, c0, c1, 0});
+      pj.push_back(PhiloxJob{X.ints(F->rch_off[k]), F->Rch[k], ch.nu, ch.nu, c0, c1, 0});
       max_rows = std::max(max_rows, ch.nu);
     }
     sj.push_back(SampleAJob{F->Sr, F->Sc, F->R, F->nf, F->f, c0, c1, 0});

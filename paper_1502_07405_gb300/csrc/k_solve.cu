@@ -350,6 +350,28 @@ void dots(const double* x, const double* y, int n, int nrhs, double* partial, do
   count_launch(2);
 }
 
+// Squared 2-norms of the row segments [off[g], off[g+1]) of every column:
+// one CTA per (segment, column), deterministic block sums.
+__global__ void k_seg_norm2(const double* __restrict__ x, int n, const int* __restrict__ off, int nseg,
+                            double* __restrict__ out) {
+  __shared__ double sh[33];
+  const int g = blockIdx.x, j = blockIdx.y;
+  const double* xj = x + (long long)j * n;
+  double s = 0.0;
+  for (int i = off[g] + threadIdx.x; i < off[g + 1]; i += blockDim.x) {
+    const double v = xj[i];
+    s += v * v;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[g + (long long)nseg * j] = s;
+}
+
+void seg_norms2(const double* x, int n, int nrhs, const int* off, int nseg, double* out, cudaStream_t s) {
+  if (nseg <= 0 || nrhs <= 0) return;
+  k_seg_norm2<<<dim3(nseg, nrhs), 256, 0, s>>>(x, n, off, nseg, out);
+  count_launch();
+}
+
 __global__ void k_sqrt_dev(double* a, long long astride, int nrhs) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < nrhs) a[c * astride] = sqrt(a[c * astride]);

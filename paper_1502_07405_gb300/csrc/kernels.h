@@ -86,6 +86,9 @@ void residual(const DevSym& ds, const double* values, const double* b, long long
 // at least 64 * nrhs doubles
 void dots(const double* x, const double* y, int n, int nrhs, double* partial, double* out,
           long long ostride, cudaStream_t s);
+// out[g + nseg * j] = sum over rows off[g] <= i < off[g+1] of x[i + j*n]^2
+// (off on device, nseg + 1 entries; deterministic)
+void seg_norms2(const double* x, int n, int nrhs, const int* off, int nseg, double* out, cudaStream_t s);
 // y[:, j] += alpha_sign * a[j * astride] * x[:, j] for active columns (a on device)
 void axpy_dev(double* y, const double* x, const double* a, long long astride, double alpha_sign,
               int n, int nrhs, const int* active, cudaStream_t s);

@@ -258,8 +258,9 @@ hssmf_status hssmf_ctx::ensure_device() {
   d_piv = (int*)dalloc(sizeof(int) * std::max<long long>(piv_total_host, 1));
   d_arena = dalloc(esz * std::max<long long>(arena_elems, 1));
   d_jobs = (GemmJob*)dalloc(sizeof(GemmJob) * std::max<size_t>(dense_jobs_host.size(), 1));
+  d_sysoff = (int*)dalloc(sizeof(int) * (S.sys_off.size() + 1));
   if (!d_status || !d_perm || !d_rowptr || !d_colind || !d_tpos || !d_values || !d_fronts ||
-      !d_ints || !d_flist || !d_tiles || !d_piv || !d_arena || !d_jobs)
+      !d_ints || !d_flist || !d_tiles || !d_piv || !d_arena || !d_jobs || !d_sysoff)
     return fail(HSSMF_ERR_OOM, "device allocation of the factor storage failed");
   std::vector<GemmJob> jobs = dense_jobs_host;
   const uintptr_t base = (uintptr_t)d_arena;
@@ -278,6 +279,7 @@ hssmf_status hssmf_ctx::ensure_device() {
   if ((st = upload(d_flist, flist_host.data(), sizeof(int) * flist_host.size()))) return st;
   if ((st = upload(d_tiles, tiles_host.data(), sizeof(Tile) * tiles_host.size()))) return st;
   if ((st = upload(d_jobs, jobs.data(), sizeof(GemmJob) * jobs.size()))) return st;
+  if ((st = upload(d_sysoff, S.sys_off.data(), sizeof(int) * S.sys_off.size()))) return st;
   ds.fronts = d_fronts;
   ds.ints = d_ints;
   ds.perm = d_perm;
@@ -389,8 +391,10 @@ hssmf_status hssmf_ctx::apply(const double* b, double* x, int nrhs, int transpos
 hssmf_status hssmf_ctx::ensure_krylov(int nrhs) {
   const int n = sym.n, m = std::max(opts.gmres_restart, 1);
   const size_t nn = (size_t)n * nrhs;
+  // refinement (no HSS front, or a batch of grids) keeps no Krylov basis
+  const bool basis = n_hss > 0 && sym.nsys == 1 && opts.maxit > 0;
   // layout (in doubles); the allocation is the exact sum of these sizes
-  const size_t sizes[] = {nn * (m + 1), nn * m, nn, nn, nn, nn, nn,
+  const size_t sizes[] = {basis ? nn * (m + 1) : 0, basis ? nn * m : 0, nn, nn, nn, nn, nn,
                           (size_t)(m + 1) * m * nrhs, (size_t)m * nrhs, (size_t)m * nrhs,
                           (size_t)(m + 1) * nrhs, (size_t)m * nrhs, 64 * (size_t)nrhs,
                           8 * (size_t)nrhs};
@@ -456,6 +460,15 @@ hssmf_status hssmf_ctx::outer_solve(const double* B, long long ldb, double* X, l
   if ((st = ensure_krylov(nrhs))) return st;
   copy_cols(k_b, n, B, ldb, n, nrhs, stream);
   count_launch();
+  if (sym.nsys > 1) {
+    if ((st = batched_refine(nrhs, transpose))) {
+      copy_cols(X, ldx, k_x, n, n, nrhs, stream);
+      return st;
+    }
+    copy_cols(X, ldx, k_x, n, n, nrhs, stream);
+    count_launch();
+    return HSSMF_OK;
+  }
   std::vector<double> bn, rn;
   dots(k_b, k_b, n, nrhs, k_part, k_s, 1, stream);
   if ((st = read_cols(k_s, 1, nrhs, bn))) return st;
@@ -584,6 +597,59 @@ hssmf_status hssmf_ctx::outer_solve(const double* B, long long ldb, double* X, l
   return HSSMF_OK;
 }
 
+// Independent grids (a block-diagonal system): iterative refinement
+// x <- x + M^-1 (b - A x) on all of them at once, stopped when the relative
+// residual of every grid and right-hand side is <= rtol.  A Krylov method
+// over the stacked vector would couple the grids through shared
+// coefficients; refinement needs only the per-grid norms.  b is in k_b, the
+// solution is left in k_x.
+hssmf_status hssmf_ctx::batched_refine(int nrhs, int transpose) {
+  const int n = sym.n, ns = sym.nsys;
+  const size_t nv = (size_t)ns * nrhs;
+  if (nv > ((size_t)1 << 20) / sizeof(double) || nrhs > 65535)
+    return fail(HSSMF_ERR_ARG, "grids x right-hand sides above 131072 (or nrhs above 65535) in one refinement");
+  if (nv > seg_cap) {
+    k_seg = (double*)dalloc(sizeof(double) * nv);
+    if (!k_seg) return fail(HSSMF_ERR_OOM, "refinement norm buffer");
+    seg_cap = nv;
+  }
+  hssmf_status st;
+  std::vector<double> bn, rn;
+  seg_norms2(k_b, n, nrhs, d_sysoff, ns, k_seg, stream);
+  if ((st = read_cols(k_seg, 1, (int)nv, bn))) return st;
+  std::vector<int> act(nrhs, 1);
+  if ((st = apply(k_b, k_x, nrhs, transpose))) return st;
+  int it = 1;
+  for (;;) {
+    residual(ds, d_values, k_b, n, k_x, k_r, nrhs, transpose, stream);
+    seg_norms2(k_r, n, nrhs, d_sysoff, ns, k_seg, stream);
+    if ((st = read_cols(k_seg, 1, (int)nv, rn))) return st;
+    last_relres = 0.0;
+    bool all = true;
+    for (int c = 0; c < nrhs; ++c) {
+      act[c] = 0;
+      for (int g = 0; g < ns; ++g) {
+        const size_t v = (size_t)g + (size_t)ns * c;
+        const double rel = bn[v] > 0 ? std::sqrt(rn[v] / bn[v]) : (rn[v] > 0 ? INFINITY : 0.0);
+        last_relres = std::max(last_relres, rel);
+        if (!(rel <= opts.rtol)) act[c] = 1;
+      }
+      all = all && !act[c];
+    }
+    if (all) break;
+    if (it >= opts.maxit) {
+      last_iters = it;
+      return fail(HSSMF_ERR_NOCONV, "iterative refinement did not reach rtol in every grid");
+    }
+    if ((st = upload(k_active, act.data(), sizeof(int) * nrhs))) return st;
+    if ((st = apply(k_r, k_w, nrhs, transpose))) return st;
+    add_cols(k_x, k_w, n, nrhs, k_active, stream);
+    ++it;
+  }
+  last_iters = it;
+  return HSSMF_OK;
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -626,6 +692,12 @@ hssmf_status hssmf_create(hssmf_ctx** out, const hssmf_opts* opts, void* stream)
 
 hssmf_status hssmf_analyze_grid(hssmf_ctx* c, int nx, int ny, int nz, int n, const int* rowptr,
                                 const int* colind) {
+  const int dims[3] = {nx, ny, nz};
+  return hssmf_analyze_grids(c, 1, dims, n, rowptr, colind);
+}
+
+hssmf_status hssmf_analyze_grids(hssmf_ctx* c, int nsys, const int* dims, int n, const int* rowptr,
+                                 const int* colind) {
   if (!c) return HSSMF_ERR_ARG;
   auto t0 = std::chrono::steady_clock::now();
   if (c->on_device) cudaStreamSynchronize(c->stream);
@@ -634,7 +706,7 @@ hssmf_status hssmf_analyze_grid(hssmf_ctx* c, int nx, int ny, int nz, int n, con
   c->reset_device_pointers();
   c->on_device = false;
   c->analyzed = c->factored = false;
-  std::string e = analyze_grid(nx, ny, nz, n, rowptr, colind, c->opts.nd_leaf, c->opts.hss_leaf, c->sym);
+  std::string e = analyze_grids(nsys, dims, n, rowptr, colind, c->opts.nd_leaf, c->opts.hss_leaf, c->sym);
   if (!e.empty()) return c->fail(HSSMF_ERR_ARG, e);
   hssmf_status st;
   const Symbolic& S = c->sym;

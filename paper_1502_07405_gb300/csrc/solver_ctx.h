@@ -130,6 +130,10 @@ struct hssmf_ctx {
          *k_g = nullptr, *k_y = nullptr, *k_part = nullptr, *k_s = nullptr;
   int* k_active = nullptr;
   void* h_pin = nullptr;
+  // per-system residual norms of a batch of independent grids
+  int* d_sysoff = nullptr;
+  double* k_seg = nullptr;
+  size_t seg_cap = 0;
   // statistics
   hssmf_stats stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -168,6 +172,9 @@ struct hssmf_ctx {
     kry_bytes = 0;
     kry_nrhs = -1;
     h_pin = nullptr;
+    d_sysoff = nullptr;
+    k_seg = nullptr;
+    seg_cap = 0;
   }
   hssmf_status upload(void* dst, const void* src, size_t bytes);
   hssmf_status read_status();
@@ -182,4 +189,5 @@ struct hssmf_ctx {
   hssmf_status read_cols(const double* dev, long long stride, int nrhs, std::vector<double>& out);
   hssmf_status outer_solve(const double* B, long long ldb, double* X, long long ldx, int nrhs,
                            int transpose);
+  hssmf_status batched_refine(int nrhs, int transpose);
 };

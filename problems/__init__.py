@@ -25,6 +25,8 @@ __all__ = [
     "grid_anisotropic_grf",
     "gaussian_random_field",
     "rhs_uniform",
+    "block_diag",
+    "batch_convdiff2d",
     "CSR",
 ]
 
@@ -195,3 +197,32 @@ def rhs_uniform(n, nrhs=1, seed=1):
     rng = np.random.default_rng(seed)
     b = rng.uniform(-1.0, 1.0, size=(nrhs, n)).T
     return np.asfortranarray(b)
+
+
+def block_diag(mats):
+    """The block-diagonal matrix of a list of CSR matrices (system s takes the
+    natural indices after those of systems 0..s-1)."""
+    n = sum(m.n for m in mats)
+    rowptr = [np.zeros(1, dtype=np.int64)]
+    cols, vals = [], []
+    r0 = c0 = 0
+    for m in mats:
+        rowptr.append(m.rowptr[1:].astype(np.int64) + r0)
+        cols.append(m.colind.astype(np.int64) + c0)
+        vals.append(m.values)
+        r0 += m.nnz
+        c0 += m.n
+    return CSR(n, np.concatenate(rowptr), np.concatenate(cols), np.concatenate(vals))
+
+
+def batch_convdiff2d(nsys, side_lo=32, side_hi=256, vmax=50.0, nu=1.0, seed=0):
+    """nsys independent upwinded 2D convection-diffusion systems
+    (``grid_convdiff2d``): grid sides uniform on {side_lo..side_hi}, one
+    constant velocity per system with components uniform on [-vmax, vmax],
+    all drawn from one seeded stream.  Returns (sides, velocities, the
+    block-diagonal CSR)."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(side_lo, side_hi + 1, size=nsys)
+    vel = rng.uniform(-vmax, vmax, size=(nsys, 2))
+    mats = [grid_convdiff2d(int(k), float(v[0]), float(v[1]), nu) for k, v in zip(sides, vel)]
+    return [int(k) for k in sides], vel, block_diag(mats)

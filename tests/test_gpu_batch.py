@@ -1,0 +1,83 @@
+"""Batches of independent grids (hssmf_analyze_grids): one elimination forest
+whose levels are batched over every grid, R keyed by the row index inside its
+grid, and refinement stopped per grid.  Upwinded 2D convection-diffusion
+systems of uneven sizes, HSS on the larger fronts."""
+import numpy as np
+import pytest
+
+import problems
+from oracle import krylov, multifrontal as mf
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GRIDS = [(20, (3.0, -7.0)), (33, (-40.0, 12.0)), (48, (25.0, 49.0)), (64, (-10.0, -30.0)), (40, (0.5, -0.5))]
+KW = dict(hss_tol=1e-6, hss_min_front=48, d0=16, dd=8, hss_leaf=16)  # 157 HSS fronts, 2-4 adaptive rounds
+
+
+def _batch():
+    mats = [problems.grid_convdiff2d(k, vx, vy) for k, (vx, vy) in GRIDS]
+    return mats, problems.block_diag(mats)
+
+
+def _solver(**kw):
+    import paper_1502_07405_gb300 as P
+    return P.Solver(P.Options.defaults(**kw))
+
+
+def _batched(A, **kw):
+    s = _solver(**kw)
+    s.analyze_grids([(k, k, 1) for k, _ in GRIDS], A.rowptr, A.colind)
+    s.factor(A.values)
+    return s
+
+
+def test_fp64_batched_application_equals_each_grid_alone_and_the_oracle():
+    mats, A = _batch()
+    s = _batched(A, maxit=0, precision=0, **KW)
+    assert s.get_stats()["n_hss_fronts"] > 0
+    b = problems.rhs_uniform(A.n, 2, 1)
+    x = s.solve(b)
+    off = 0
+    for (k, _), m in zip(GRIDS, mats):
+        bs = np.asfortranarray(b[off:off + m.n])
+        t = _solver(maxit=0, precision=0, **KW)
+        t.analyze_grid((k, k, 1), m.rowptr, m.colind)
+        t.factor(m.values)
+        xs = t.solve(bs)
+        assert np.linalg.norm(x[off:off + m.n] - xs) <= 1e-13 * np.linalg.norm(xs)
+        fo = mf.factor(m.to_scipy(), (k, k, 1), mf.Options(hss_tol=KW["hss_tol"], d0=KW["d0"], dd=KW["dd"],
+                                                           hss_min_front=KW["hss_min_front"],
+                                                           hss_leaf=KW["hss_leaf"]))
+        xo = mf.apply_inverse(fo, bs)
+        assert np.linalg.norm(xs - xo) <= 1e-9 * np.linalg.norm(xo)
+        off += m.n
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_refinement_reaches_1e10_in_every_grid(prec):
+    mats, A = _batch()
+    s = _batched(A, precision=prec, **KW)
+    b = problems.rhs_uniform(A.n, 3, 7)
+    x = s.solve(b)
+    st = s.get_stats()
+    assert st["iterations"] >= 2  # eps = 1e-6 is not exact
+    off = 0
+    for m in mats:
+        r = b[off:off + m.n] - m.to_scipy() @ x[off:off + m.n]
+        rel = np.linalg.norm(r, axis=0) / np.linalg.norm(b[off:off + m.n], axis=0)
+        assert np.all(rel <= 1e-10), rel
+        off += m.n
+    # device tensors, column-major view of a (nrhs, n) tensor
+    bt = torch.tensor(np.ascontiguousarray(b.T), device="cuda").t()
+    xt = s.solve(bt)
+    assert np.allclose(xt.cpu().numpy(), x, rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+def test_batched_refinement_reports_nonconvergence():
+    import paper_1502_07405_gb300 as P
+    mats, A = _batch()
+    s = _batched(A, precision=1, maxit=2, **dict(KW, hss_tol=1e-1))
+    with pytest.raises(P.HssmfError) as e:
+        s.solve(problems.rhs_uniform(A.n, 1, 1))
+    assert e.value.status == P.ERR_NOCONV

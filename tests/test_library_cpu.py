@@ -85,3 +85,42 @@ def test_factor_before_analyze_is_an_error():
     with pytest.raises(P.HssmfError) as e:
         s.factor(np.zeros(5))
     assert e.value.status == P.ERR_ARG
+
+
+def test_batched_grids_are_the_individual_analyses_side_by_side():
+    """analyze_grids over several grids = each grid's own ordering (offset by
+    the grids before it), fronts in order with parents shifted, one root per
+    grid, and each grid's I^upd sizes unchanged."""
+    P = _lib()
+    grids = [(20, 13, 1), (9, 9, 1), (6, 7, 5), (33, 17, 1)]
+    mats = [problems.grid_poisson(g) for g in grids]
+    A = problems.block_diag(mats)
+    s = P.Solver(P.Options.defaults(hss_leaf=32))
+    s.analyze_grids(grids, A.rowptr, A.colind)
+    nf_total = s.get_stats()["n_fronts"]
+    perm, sb, se, par, nu = s.get_symbolic(nf_total)
+    off = fo = 0
+    for g, m in zip(grids, mats):
+        t = P.Solver(P.Options.defaults(hss_leaf=32))
+        t.analyze_grid(g, m.rowptr, m.colind)
+        nf = t.get_stats()["n_fronts"]
+        p1, sb1, se1, par1, nu1 = t.get_symbolic(nf)
+        assert np.array_equal(perm[off:off + m.n], p1 + off)
+        assert np.array_equal(sb[fo:fo + nf], sb1 + off)
+        assert np.array_equal(se[fo:fo + nf], se1 + off)
+        assert np.array_equal(par[fo:fo + nf], np.where(par1 >= 0, par1 + fo, -1))
+        assert np.array_equal(nu[fo:fo + nf], nu1)
+        off += m.n
+        fo += nf
+    assert fo == nf_total and off == A.n
+    assert int((par < 0).sum()) == len(grids)
+
+
+def test_batched_grids_reject_coupled_grids():
+    P = _lib()
+    A = problems.grid_poisson((8, 8, 1))
+    s = P.Solver(P.Options.defaults())
+    with pytest.raises(P.HssmfError):  # one 8x8 grid declared as two 8x4 grids: edges cross
+        s.analyze_grids([(8, 4, 1), (8, 4, 1)], A.rowptr, A.colind)
+    with pytest.raises(P.HssmfError):  # sizes do not add up
+        s.analyze_grids([(8, 8, 1), (2, 2, 1)], A.rowptr, A.colind)
