@@ -300,7 +300,7 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_panel_trsm(const DFront* __restrict__ fr,
                                                     T* __restrict__ ar,
                                                     const int* __restrict__ flist, int k0, int nb) {
-  const DFront f = fr[flist[blockIdx.y]];
+  const DFront f = fr[flist[blockIdx.x]];
   if (k0 >= f.ns) return;
   const int k1 = min(k0 + nb, f.ns);
   const int w = k1 - k0;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(128) k_panel_trsm(const DFront* __restrict__ f
     L[i][j] = (i < w && j < w) ? F[(k0 + i) + (k0 + j) * ld] : T(0);
   }
   __syncthreads();
-  const int c = k1 + blockIdx.x * 128 + threadIdx.x;
+  const int c = k1 + blockIdx.y * 128 + threadIdx.x;
   if (c >= f.nf) return;
   T x[32];
 #pragma unroll
@@ -331,7 +331,7 @@ template <typename T>
 void Kern<T>::panel_trsm(const DevSym& ds, T* arena, const int* flist, int nfr, int k0, int nb,
                          int max_chunks, cudaStream_t s) {
   if (nfr <= 0 || max_chunks <= 0) return;
-  dim3 g(max_chunks, nfr);
+  dim3 g(nfr, max_chunks);  // fronts on x (no 65535 limit)
   k_panel_trsm<T><<<g, 128, 0, s>>>(ds.fronts, arena, flist, k0, nb);
   count_launch();
 }

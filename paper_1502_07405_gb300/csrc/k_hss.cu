@@ -1927,7 +1927,7 @@ void HssKern<T>::lu_panel(const LuJob* jobs, int njobs, int k0, int nb, unsigned
 // rows [k0, k1), columns [k1, m) <- L_panel^-1 (unit lower, nb <= 32).
 template <typename T>
 __global__ void __launch_bounds__(128) k_lu_trsm(const LuJob* __restrict__ jobs, int k0, int nb) {
-  const LuJob jb = jobs[blockIdx.y];
+  const LuJob jb = jobs[blockIdx.x];
   const int m = jb.m;
   if (k0 >= m) return;
   const int k1 = min(k0 + nb, m), w = k1 - k0;
@@ -1941,7 +1941,7 @@ __global__ void __launch_bounds__(128) k_lu_trsm(const LuJob* __restrict__ jobs,
   }
   if (threadIdx.x < w) pv[threadIdx.x] = jb.piv[k0 + threadIdx.x];
   __syncthreads();
-  int c = blockIdx.x * 128 + threadIdx.x;  // columns outside [k0, k1)
+  int c = blockIdx.y * 128 + threadIdx.x;  // columns outside [k0, k1)
   if (c >= k0) c += w;
   if (c >= m) return;
   for (int i = 0; i < w; ++i) {
@@ -1970,7 +1970,7 @@ template <typename T>
 void HssKern<T>::lu_trsm(const LuJob* jobs, int njobs, int k0, int nb, int max_m, cudaStream_t s) {
   // (every panel, the last included: the interchanges reach the columns on its left)
   if (njobs <= 0 || k0 >= max_m || max_m - std::min(nb, max_m - k0) <= 0) return;
-  k_lu_trsm<T><<<dim3((max_m - std::min(nb, max_m - k0) + 127) / 128, njobs), 128, 0, s>>>(jobs, k0, nb);
+  k_lu_trsm<T><<<dim3(njobs, (max_m - std::min(nb, max_m - k0) + 127) / 128), 128, 0, s>>>(jobs, k0, nb);
   count_launch();
 }
 

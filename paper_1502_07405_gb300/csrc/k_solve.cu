@@ -50,14 +50,15 @@ void Kern<T>::permute_out(const T* xp, double* x, long long ldx, const int* perm
 // ---------------------------------------------------------------------------
 // Forward solve, assembly of the front right-hand side: W_f = [b(I^sep); 0]
 // (+) the children's updated I^upd parts (extend-add of vectors, children in
-// order).  Grid (row chunk of 256, front).
+// order).  Grid (front, row chunk of 256): fronts on x, which has no 65535
+// limit.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_solve_gather(const DFront* __restrict__ fr, const int* __restrict__ ints,
                                T* __restrict__ W, const T* __restrict__ bp,
                                const int* __restrict__ flist, int n, int nrhs) {
-  const DFront f = fr[flist[blockIdx.y]];
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const DFront f = fr[flist[blockIdx.x]];
+  const int r = blockIdx.y * blockDim.x + threadIdx.x;
   if (r >= f.nf) return;
   int ir[2] = {-1, -1};
   for (int k = 0; k < f.nchild; ++k) ir[k] = ints[f.inv_off + (long long)k * f.nf + r];
@@ -76,7 +77,7 @@ template <typename T>
 void Kern<T>::solve_gather(const DevSym& ds, T* W, const T* bp, const int* flist, int nfr,
                            int max_rows, int nrhs, cudaStream_t s) {
   if (nfr <= 0) return;
-  dim3 g((max_rows + 255) / 256, nfr);
+  dim3 g(nfr, (max_rows + 255) / 256);
   k_solve_gather<T><<<g, 256, 0, s>>>(ds.fronts, ds.ints, W, bp, flist, ds.n, nrhs);
   count_launch();
 }
@@ -163,13 +164,13 @@ void Kern<T>::solve_fwd_dense(const DevSym& ds, const T* arena, const int* piv, 
   count_launch();
 }
 
-// Backward solve: W_f(ns + i) = x(I^upd(i)).  Grid (chunk, front).
+// Backward solve: W_f(ns + i) = x(I^upd(i)).  Grid (front, chunk).
 template <typename T>
 __global__ void k_solve_bwd_gather(const DFront* __restrict__ fr, const int* __restrict__ ints,
                                    T* __restrict__ W, const T* __restrict__ xp,
                                    const int* __restrict__ flist, int n, int nrhs) {
-  const DFront f = fr[flist[blockIdx.y]];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const DFront f = fr[flist[blockIdx.x]];
+  const int i = blockIdx.y * blockDim.x + threadIdx.x;
   if (i >= f.nu) return;
   const int g = ints[f.upd_off + i];
   for (int j = 0; j < nrhs; ++j) W[f.w_off + f.ns + i + (long long)j * f.nf] = xp[g + (long long)j * n];
@@ -179,7 +180,7 @@ template <typename T>
 void Kern<T>::solve_bwd_gather(const DevSym& ds, T* W, const T* xp, const int* flist, int nfr,
                                int max_nu, int nrhs, cudaStream_t s) {
   if (nfr <= 0 || max_nu <= 0) return;
-  dim3 g((max_nu + 255) / 256, nfr);
+  dim3 g(nfr, (max_nu + 255) / 256);
   k_solve_bwd_gather<T><<<g, 256, 0, s>>>(ds.fronts, ds.ints, W, xp, flist, ds.n, nrhs);
   count_launch();
 }

@@ -10,7 +10,14 @@ namespace hssmf {
 
 // Kernels launched by this library since load (read by the stats).
 extern std::atomic<long long> g_launches;
-inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// Set when a launch is rejected (bad configuration, no resources); launchers
+// that probe a configuration clear the error state themselves, so every launch
+// is checked here, right after it is issued.
+extern std::atomic<int> g_launch_error;
+inline void count_launch(int k = 1) {
+  g_launches.fetch_add(k, std::memory_order_relaxed);
+  if (cudaPeekAtLastError() != cudaSuccess) g_launch_error.store(1, std::memory_order_relaxed);
+}
 
 // Per-front table uploaded once after analyze (all offsets in elements).
 struct DFront {

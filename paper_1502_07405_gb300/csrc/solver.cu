@@ -24,6 +24,7 @@
 
 namespace hssmf {
 std::atomic<long long> g_launches{0};
+std::atomic<int> g_launch_error{0};
 }
 
 using namespace hssmf;
@@ -79,6 +80,10 @@ hssmf_status hssmf_ctx::upload(void* dst, const void* src, size_t bytes) {
 }
 
 hssmf_status hssmf_ctx::read_status() {
+  if (g_launch_error.exchange(0)) {
+    cudaGetLastError();
+    return fail(HSSMF_ERR_CUDA, "a kernel launch was rejected");
+  }
   unsigned st = 0;
   hssmf_status s = cuda_check(cudaMemcpyAsync(&st, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, stream), "status");
   if (s) return s;
@@ -795,6 +800,7 @@ static hssmf_status solve_common(hssmf_ctx* c, const double* B, double* X, int n
   cudaEventRecord(c->ev1, c->stream);
   hssmf_status st3 = c->read_status();
   c->prof.finish(c->stream);
+  if (st3 == HSSMF_ERR_CUDA) return st3;  // a rejected launch explains any other failure
   if (st) return st;
   if (st2) return st2;
   if (st3) return st3;

@@ -81,3 +81,34 @@ def test_batched_refinement_reports_nonconvergence():
     with pytest.raises(P.HssmfError) as e:
         s.solve(problems.rhs_uniform(A.n, 1, 1))
     assert e.value.status == P.ERR_NOCONV
+
+
+def test_more_than_65535_fronts_in_one_level():
+    """70000 independent 8 x 8 grids: level 0 holds 70000 fronts, above the
+    65535 limit of a grid's y and z dimensions, so every per-front launch
+    must index fronts along x.  Each grid is a scaled Poisson matrix (scale
+    1 + grid index mod 7), dense fronts only: one application solves every
+    grid to rounding and the refinement stops at once."""
+    ng, side = 70000, 8
+    base = problems.grid_poisson((side, side, 1))
+    nb, zb = base.n, base.nnz
+    scale = 1.0 + (np.arange(ng) % 7)
+    rowptr = np.concatenate([[0], (base.rowptr[1:][None, :] + zb * np.arange(ng)[:, None]).ravel()])
+    colind = (base.colind[None, :] + nb * np.arange(ng)[:, None]).ravel()
+    values = (base.values[None, :] * scale[:, None]).ravel()
+    A = problems.CSR(ng * nb, rowptr, colind, values)
+    b = problems.rhs_uniform(A.n, 1, 3)
+    s = _solver(precision=0)
+    s.analyze_grids([(side, side, 1)] * ng, A.rowptr, A.colind)
+    st = s.get_stats()
+    assert st["n_fronts"] >= ng and st["n_hss_fronts"] == 0
+    s.factor(A.values)
+    x = s.solve(b)
+    r = (b - A.to_scipy() @ x)[:, 0].reshape(ng, nb)
+    rel = np.linalg.norm(r, axis=1) / np.linalg.norm(b[:, 0].reshape(ng, nb), axis=1)
+    assert rel.max() <= 1e-12, rel.max()
+    # the same grids solved one by one agree (spot check)
+    for g in (0, 1, 65535, 65536, ng - 1):
+        m = problems.grid_poisson((side, side, 1), scale=scale[g])
+        xs = np.linalg.solve(m.to_scipy().toarray(), b[g * nb:(g + 1) * nb, 0])
+        assert np.allclose(x[g * nb:(g + 1) * nb, 0], xs, rtol=1e-12, atol=1e-14)
