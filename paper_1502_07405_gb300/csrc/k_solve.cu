@@ -156,11 +156,96 @@ __global__ void __launch_bounds__(256) k_solve_fwd_dense(const DFront* __restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// Several right-hand sides: one warp per column, the column staged in shared
+// memory, so a substitution step needs only the warp (no CTA barrier) and the
+// CTA's 8 warps share the front's factor through L1.  Same substitution
+// forms as the one-CTA-per-column kernels above and below.
+// ---------------------------------------------------------------------------
+constexpr int WC_WARPS = 8;
+constexpr size_t kWarpColSmem = 160 * 1024;
+
+template <typename T>
+__device__ __forceinline__ T warp_allsum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_solve_fwd_dense_wc(const DFront* __restrict__ fr,
+                                                            const T* __restrict__ ar,
+                                                            const int* __restrict__ piv,
+                                                            T* __restrict__ W,
+                                                            const int* __restrict__ flist, int nrhs,
+                                                            int max_nf, int transpose) {
+  const DFront f = fr[flist[blockIdx.x]];
+  if (f.is_hss) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int j = blockIdx.y * WC_WARPS + wid;
+  if (j >= nrhs) return;
+  extern __shared__ __align__(16) unsigned char wc_raw[];
+  T* xw = reinterpret_cast<T*>(wc_raw) + (size_t)wid * max_nf;
+  const T* F = ar + f.off;
+  const long long ld = f.nf;
+  T* x = W + f.w_off + (long long)j * f.nf;
+  for (int r = lane; r < f.nf; r += 32) xw[r] = x[r];
+  __syncwarp();
+  if (!transpose) {
+    if (lane == 0)
+      for (int i = 0; i < f.ns; ++i) {
+        const int p = piv[f.piv_off + i];
+        if (p != i) { const T t = xw[i]; xw[i] = xw[p]; xw[p] = t; }
+      }
+    __syncwarp();
+    for (int c = 0; c < f.ns; ++c) {  // unit lower, column-oriented over all nf rows
+      const T xc = xw[c];
+      const T* Fc = F + c * ld;
+      for (int r = c + 1 + lane; r < f.nf; r += 32) xw[r] -= Fc[r] * xc;
+      __syncwarp();
+    }
+  } else {
+    for (int c = 0; c < f.ns; ++c) {  // U11^T: y_c = (b_c - U(0:c, c) . y) / U(c, c)
+      const T* Fc = F + c * ld;
+      T part = T(0);
+      for (int r = lane; r < c; r += 32) part += Fc[r] * xw[r];
+      part = warp_allsum(part);
+      if (lane == 0) xw[c] = (xw[c] - part) / Fc[c];
+      __syncwarp();
+    }
+    for (int c = f.ns; c < f.nf; ++c) {  // b_u -= U12^T y
+      const T* Fc = F + c * ld;
+      T part = T(0);
+      for (int r = lane; r < f.ns; r += 32) part += Fc[r] * xw[r];
+      part = warp_allsum(part);
+      if (lane == 0) xw[c] -= part;
+    }
+    __syncwarp();
+  }
+  for (int r = lane; r < f.nf; r += 32) x[r] = xw[r];
+}
+
+template <typename T>
+static bool warp_cols_fit(int max_nf, int nrhs) {
+  return nrhs >= 4 && max_nf > 0 && (size_t)WC_WARPS * max_nf * sizeof(T) <= kWarpColSmem;
+}
+
 template <typename T>
 void Kern<T>::solve_fwd_dense(const DevSym& ds, const T* arena, const int* piv, T* W,
-                              const int* flist, int nfr, int nrhs, int transpose, cudaStream_t s) {
+                              const int* flist, int nfr, int max_nf, int nrhs, int transpose, cudaStream_t s) {
   if (nfr <= 0) return;
-  k_solve_fwd_dense<T><<<dim3(nfr, std::min(nrhs, 64)), 256, 0, s>>>(ds.fronts, arena, piv, W, flist, nrhs, transpose);
+  if (warp_cols_fit<T>(max_nf, nrhs)) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_solve_fwd_dense_wc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpColSmem);
+      attr = true;
+    }
+    const size_t smem = (size_t)WC_WARPS * max_nf * sizeof(T);
+    k_solve_fwd_dense_wc<T><<<dim3(nfr, (nrhs + WC_WARPS - 1) / WC_WARPS), 256, smem, s>>>(
+        ds.fronts, arena, piv, W, flist, nrhs, max_nf, transpose);
+  } else {
+    k_solve_fwd_dense<T><<<dim3(nfr, std::min(nrhs, 64)), 256, 0, s>>>(ds.fronts, arena, piv, W, flist, nrhs,
+                                                                      transpose);
+  }
   count_launch();
 }
 
@@ -250,10 +335,83 @@ __global__ void __launch_bounds__(256) k_solve_bwd_dense(const DFront* __restric
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) k_solve_bwd_dense_wc(const DFront* __restrict__ fr,
+                                                            const T* __restrict__ ar,
+                                                            const int* __restrict__ piv,
+                                                            T* __restrict__ W, T* __restrict__ xp,
+                                                            const int* __restrict__ flist, int n, int nrhs,
+                                                            int max_nf, int transpose) {
+  const DFront f = fr[flist[blockIdx.x]];
+  if (f.is_hss) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int j = blockIdx.y * WC_WARPS + wid;
+  if (j >= nrhs) return;
+  extern __shared__ __align__(16) unsigned char wc_raw[];
+  T* xw = reinterpret_cast<T*>(wc_raw) + (size_t)wid * max_nf;
+  const T* F = ar + f.off;
+  const long long ld = f.nf;
+  const T* x = W + f.w_off + (long long)j * f.nf;
+  for (int r = lane; r < f.nf; r += 32) xw[r] = x[r];
+  __syncwarp();
+  if (!transpose) {
+    for (int r = lane; r < f.ns; r += 32) {  // y -= U12 x_u
+      T acc = T(0);
+      for (int c = f.ns; c < f.nf; ++c) acc += F[r + c * ld] * xw[c];
+      xw[r] -= acc;
+    }
+    __syncwarp();
+    for (int c = f.ns - 1; c >= 0; --c) {  // U11, column-oriented
+      const T* Fc = F + c * ld;
+      const T xc = xw[c] / Fc[c];
+      __syncwarp();
+      if (lane == 0) xw[c] = xc;
+      for (int r = lane; r < c; r += 32) xw[r] -= Fc[r] * xc;
+      __syncwarp();
+    }
+  } else {
+    for (int r = 0; r < f.ns; ++r) {  // y -= L21^T x_u
+      const T* Fr = F + r * ld;
+      T part = T(0);
+      for (int c = f.ns + lane; c < f.nf; c += 32) part += Fr[c] * xw[c];
+      part = warp_allsum(part);
+      if (lane == 0) xw[r] -= part;
+    }
+    __syncwarp();
+    for (int c = f.ns - 1; c >= 0; --c) {  // L11^T unit upper: x_c -= L(c+1:ns, c) . x(c+1:ns)
+      const T* Fc = F + c * ld;
+      T part = T(0);
+      for (int r = c + 1 + lane; r < f.ns; r += 32) part += Fc[r] * xw[r];
+      part = warp_allsum(part);
+      if (lane == 0) xw[c] -= part;
+      __syncwarp();
+    }
+    if (lane == 0)
+      for (int i = f.ns - 1; i >= 0; --i) {
+        const int p = piv[f.piv_off + i];
+        if (p != i) { const T t = xw[i]; xw[i] = xw[p]; xw[p] = t; }
+      }
+    __syncwarp();
+  }
+  for (int r = lane; r < f.ns; r += 32) xp[f.sep_begin + r + (long long)j * n] = xw[r];
+}
+
+template <typename T>
 void Kern<T>::solve_bwd_dense(const DevSym& ds, const T* arena, const int* piv, T* W, T* xp,
-                              const int* flist, int nfr, int nrhs, int transpose, cudaStream_t s) {
+                              const int* flist, int nfr, int max_nf, int nrhs, int transpose, cudaStream_t s) {
   if (nfr <= 0) return;
-  k_solve_bwd_dense<T><<<dim3(nfr, std::min(nrhs, 64)), 256, 0, s>>>(ds.fronts, arena, piv, W, xp, flist, ds.n, nrhs, transpose);
+  if (warp_cols_fit<T>(max_nf, nrhs)) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_solve_bwd_dense_wc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpColSmem);
+      attr = true;
+    }
+    const size_t smem = (size_t)WC_WARPS * max_nf * sizeof(T);
+    k_solve_bwd_dense_wc<T><<<dim3(nfr, (nrhs + WC_WARPS - 1) / WC_WARPS), 256, smem, s>>>(
+        ds.fronts, arena, piv, W, xp, flist, ds.n, nrhs, max_nf, transpose);
+  } else {
+    k_solve_bwd_dense<T><<<dim3(nfr, std::min(nrhs, 64)), 256, 0, s>>>(ds.fronts, arena, piv, W, xp, flist, ds.n,
+                                                                      nrhs, transpose);
+  }
   count_launch();
 }
 

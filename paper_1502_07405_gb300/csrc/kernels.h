@@ -64,12 +64,13 @@ struct Kern {
                           cudaStream_t s);
   static void solve_gather(const DevSym& ds, T* W, const T* bp, const int* flist, int nfr,
                            int max_rows, int nrhs, cudaStream_t s);
+  // max_nf: largest dense front of the list (sizes the shared-memory staging)
   static void solve_fwd_dense(const DevSym& ds, const T* arena, const int* piv, T* W,
-                              const int* flist, int nfr, int nrhs, int transpose, cudaStream_t s);
+                              const int* flist, int nfr, int max_nf, int nrhs, int transpose, cudaStream_t s);
   static void solve_bwd_gather(const DevSym& ds, T* W, const T* xp, const int* flist, int nfr,
                                int max_nu, int nrhs, cudaStream_t s);
   static void solve_bwd_dense(const DevSym& ds, const T* arena, const int* piv, T* W, T* xp,
-                              const int* flist, int nfr, int nrhs, int transpose, cudaStream_t s);
+                              const int* flist, int nfr, int max_nf, int nrhs, int transpose, cudaStream_t s);
 };
 
 // FP32 GEMM over a tile list of 128 x 128 tiles on the tensor cores

@@ -176,6 +176,7 @@ hssmf_status hssmf_ctx::build_plan() {
       flist.push_back(f);
       L.max_nf = std::max(L.max_nf, fr[f].nf);
       L.max_nu = std::max(L.max_nu, fr[f].nu);
+      if (!is_hss[f]) L.max_nf_dense = std::max(L.max_nf_dense, fr[f].nf);
     }
     L.dense_off = (int)flist.size();
     L.ndense = (int)L.dense.size();
@@ -365,7 +366,8 @@ hssmf_status hssmf_ctx::apply_impl(const double* b, double* x, int nrhs, int tra
   for (size_t h = 0; h < plan.size(); ++h) {  // forward, bottom-up
     const LevelPlan& L = plan[h];
     Kern<T>::solve_gather(ds, W, bp, d_flist + L.all_off, L.nall, L.max_nf, nrhs, stream);
-    Kern<T>::solve_fwd_dense(ds, ar, d_piv, W, d_flist + L.dense_off, L.ndense, nrhs, transpose, stream);
+    Kern<T>::solve_fwd_dense(ds, ar, d_piv, W, d_flist + L.dense_off, L.ndense, L.max_nf_dense, nrhs, transpose,
+                             stream);
     if (!L.hss.empty()) {
       hssmf_status st = hss_solve_fwd_level<T>(*this, (int)h, W, nrhs, transpose);
       if (st) return st;
@@ -374,7 +376,8 @@ hssmf_status hssmf_ctx::apply_impl(const double* b, double* x, int nrhs, int tra
   for (int h = (int)plan.size() - 1; h >= 0; --h) {  // backward, top-down
     const LevelPlan& L = plan[h];
     Kern<T>::solve_bwd_gather(ds, W, xp, d_flist + L.all_off, L.nall, L.max_nu, nrhs, stream);
-    Kern<T>::solve_bwd_dense(ds, ar, d_piv, W, xp, d_flist + L.dense_off, L.ndense, nrhs, transpose, stream);
+    Kern<T>::solve_bwd_dense(ds, ar, d_piv, W, xp, d_flist + L.dense_off, L.ndense, L.max_nf_dense, nrhs,
+                             transpose, stream);
     if (!L.hss.empty()) {
       hssmf_status st = hss_solve_bwd_level<T>(*this, h, W, xp, nrhs, transpose);
       if (st) return st;

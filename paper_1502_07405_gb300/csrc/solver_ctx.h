@@ -19,7 +19,7 @@ struct StepPlan {  // one panel step of the dense partial LU of a level
 struct LevelPlan {
   std::vector<int> dense, hss;
   int all_off = 0, nall = 0, dense_off = 0, ndense = 0, hss_off = 0;
-  int max_nf = 0, max_nu = 0;
+  int max_nf = 0, max_nu = 0, max_nf_dense = 0;
   int asm_off = 0, asm_n = 0;
   std::vector<StepPlan> steps;
 };

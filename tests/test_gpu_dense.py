@@ -30,12 +30,14 @@ def _oracle_x(A, dims, b, transpose=False):
     return mf.apply_inverse(fz, b, transpose=transpose)
 
 
+@pytest.mark.parametrize("nrhs", [2, 11])
 @pytest.mark.parametrize("dims", [(64, 64, 1), (8, 8, 1), (33, 17, 1), (9, 7, 5), (16, 16, 16)])
-def test_direct_solve_matches_oracle(dims):
+def test_direct_solve_matches_oracle(dims, nrhs):
     """maxit = 0: one forward + backward sweep; uncompressed FP64 agrees with
-    the oracle to relative error 1e-10 (elementwise over all n)."""
+    the oracle to relative error 1e-10 (elementwise over all n).  11 columns:
+    the warp-per-column sweeps (two CTAs of 8 columns, the second ragged)."""
     A = problems.grid_poisson(dims)
-    b = problems.rhs_uniform(A.n, 2, 1)
+    b = problems.rhs_uniform(A.n, nrhs, 1)
     s = _solver(A, dims, maxit=0)
     s.factor(A.values)
     x = s.solve(b)
@@ -72,10 +74,11 @@ def _nonsym(dims, seed):
     return problems.CSR(A.n, A.rowptr, A.colind, v)
 
 
+@pytest.mark.parametrize("nrhs", [3, 11])
 @pytest.mark.parametrize("dims", [(12, 12, 1), (6, 5, 4)])
-def test_pivoting_nonsymmetric(dims):
+def test_pivoting_nonsymmetric(dims, nrhs):
     A = _nonsym(dims, 3)
-    b = problems.rhs_uniform(A.n, 3, 2)
+    b = problems.rhs_uniform(A.n, nrhs, 2)
     s = _solver(A, dims, maxit=0)
     s.factor(A.values)
     x = s.solve(b)
