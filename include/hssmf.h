@@ -124,6 +124,26 @@ hssmf_status hssmf_analyze_grid(hssmf_ctx* ctx, int nx, int ny, int nz, int n,
 hssmf_status hssmf_analyze_grids(hssmf_ctx* ctx, int nsys, const int* dims_host, int n,
                                  const int* rowptr_host, const int* colind_host);
 
+/* Symbolic phase for a general n x n matrix with a structurally symmetric
+ * pattern (host CSR, column indices ascending per row).  perm == NULL: the
+ * library orders it by algebraic nested dissection (no geometry: each
+ * connected component is a separate elimination tree; in a connected set,
+ * the separator is the middle level of a breadth-first level structure from
+ * a pseudo-peripheral vertex, trimmed of vertices with no neighbour beyond
+ * it; sets of at most max(16, nd_leaf^2) vertices are leaf fronts); nfronts,
+ * sep_ptr and parent are then ignored.  Otherwise the caller gives the
+ * ordering and the separator tree of Sections 3.1 and 5.4: perm[new] = old
+ * (n entries), front f owns the new indices [sep_ptr[f], sep_ptr[f+1])
+ * (nfronts + 1 entries, 0 to n, every front non-empty), parent[f] > f or -1
+ * for a root (postorder), at most two children per front.  The tree must be
+ * an elimination structure of the pattern: every front's I^upd must lie in
+ * its parent's index set (HSSMF_ERR_ARG otherwise).  HSS cluster trees halve
+ * each front's index range down to hss_leaf.  Factor and solve are as after
+ * hssmf_analyze_grid. */
+hssmf_status hssmf_analyze_csr(hssmf_ctx* ctx, int n, const int* rowptr_host, const int* colind_host,
+                               int nfronts, const int* perm_host, const int* sep_ptr_host,
+                               const int* parent_host);
+
 /* Numerical factorization (Sections 3.2 and 4): values are the nnz matrix
  * entries in the CSR order given to analyze (host or device, FP64).
  * Fronts below hss_min_front are assembled by extend-add and partially

@@ -75,6 +75,7 @@ lib.hssmf_default_opts.restype = None
 lib.hssmf_create.argtypes = [C.POINTER(_P), C.POINTER(Options), _P]
 lib.hssmf_analyze_grid.argtypes = [_P, _I, _I, _I, _I, _IP, _IP]
 lib.hssmf_analyze_grids.argtypes = [_P, _I, _IP, _I, _IP, _IP]
+lib.hssmf_analyze_csr.argtypes = [_P, _I, _IP, _IP, _I, _IP, _IP, _IP]
 lib.hssmf_factor.argtypes = [_P, _P]
 lib.hssmf_solve.argtypes = [_P, _P, _P, _I, _I]
 lib.hssmf_solve_T.argtypes = [_P, _P, _P, _I, _I]
@@ -91,7 +92,7 @@ lib.hssmf_last_error.argtypes = [_P]
 lib.hssmf_last_error.restype = C.c_char_p
 lib.hssmf_destroy.argtypes = [_P]
 lib.hssmf_destroy.restype = None
-for _f in ("hssmf_create", "hssmf_analyze_grid", "hssmf_analyze_grids", "hssmf_factor", "hssmf_solve", "hssmf_solve_T",
+for _f in ("hssmf_create", "hssmf_analyze_grid", "hssmf_analyze_grids", "hssmf_analyze_csr", "hssmf_factor", "hssmf_solve", "hssmf_solve_T",
            "hssmf_get_stats", "hssmf_get_symbolic", "hssmf_get_upd", "hssmf_get_phase_times",
            "hssmf_set_profiling"):
     getattr(lib, _f).restype = C.c_int
@@ -172,6 +173,25 @@ class Solver:
         n = len(rp) - 1
         self._check(lib.hssmf_analyze_grids(self._h, len(dims_list), _int_ptr(dims), n, _int_ptr(rp),
                                             _int_ptr(ci)))
+        self.n = n
+        self.nnz = int(rp[-1])
+
+    def analyze_csr(self, rowptr, colind, perm=None, sep_ptr=None, parent=None):
+        """A general structurally symmetric pattern: algebraic nested
+        dissection when perm is None, else the caller's ordering
+        (perm[new] = old) and separator tree (sep_ptr, parent)."""
+        rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(colind, dtype=np.int32)
+        n = len(rp) - 1
+        if perm is None:
+            st = lib.hssmf_analyze_csr(self._h, n, _int_ptr(rp), _int_ptr(ci), 0, None, None, None)
+        else:
+            pm = np.ascontiguousarray(perm, dtype=np.int32)
+            sp = np.ascontiguousarray(sep_ptr, dtype=np.int32)
+            pa = np.ascontiguousarray(parent, dtype=np.int32)
+            st = lib.hssmf_analyze_csr(self._h, n, _int_ptr(rp), _int_ptr(ci), len(pa), _int_ptr(pm),
+                                       _int_ptr(sp), _int_ptr(pa))
+        self._check(st)
         self.n = n
         self.nnz = int(rp[-1])
 

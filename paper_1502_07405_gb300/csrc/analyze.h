@@ -61,5 +61,12 @@ std::string analyze_grid(int nx, int ny, int nz, int n, const int* rowptr, const
 // forest with a common level schedule.
 std::string analyze_grids(int nsys, const int* dims, int n, const int* rowptr, const int* colind,
                           int nd_leaf, int hss_leaf, Symbolic& out);
+// A general structurally symmetric pattern.  perm == nullptr: algebraic
+// nested dissection (one tree per connected component).  Otherwise the
+// caller's ordering (perm[new] = old) and separator tree: front f owns the
+// new indices [sep_ptr[f], sep_ptr[f+1]), parent[f] > f or -1, at most two
+// children per front.
+std::string analyze_csr(int n, const int* rowptr, const int* colind, int nfronts, const int* perm,
+                        const int* sep_ptr, const int* parent, int nd_leaf, int hss_leaf, Symbolic& out);
 
 }  // namespace hssmf

@@ -658,6 +658,38 @@ hssmf_status hssmf_ctx::batched_refine(int nrhs, int transpose) {
   return HSSMF_OK;
 }
 
+// Symbolic phase common to every analysis entry point: run the ordering,
+// keep the pattern, build the launch plans and the HSS structure.
+template <class F>
+static hssmf_status analyze_common(hssmf_ctx* c, int n, const int* rowptr, const int* colind, F order) {
+  if (!c) return HSSMF_ERR_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  if (c->on_device) cudaStreamSynchronize(c->stream);
+  c->free_all();
+  hss_release(*c);
+  c->reset_device_pointers();
+  c->on_device = false;
+  c->analyzed = c->factored = false;
+  std::string e = order();
+  if (!e.empty()) return c->fail(HSSMF_ERR_ARG, e);
+  hssmf_status st;
+  const Symbolic& S = c->sym;
+  c->rowptr_host.assign(rowptr, rowptr + n + 1);
+  c->colind_host.assign(colind, colind + S.nnz);
+  if ((st = c->build_plan())) return st;
+  if ((st = hss_prepare(*c))) return st;
+  c->analyzed = true;
+  c->stats = hssmf_stats();
+  c->stats.n = n;
+  c->stats.n_fronts = (int)S.fronts.size();
+  c->stats.n_levels = (int)S.levels.size();
+  c->stats.n_hss_fronts = c->n_hss;
+  for (auto& f : S.fronts) c->stats.max_front = std::max(c->stats.max_front, f.nf());
+  c->stats.t_analyze_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return HSSMF_OK;
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -707,31 +739,19 @@ hssmf_status hssmf_analyze_grid(hssmf_ctx* c, int nx, int ny, int nz, int n, con
 hssmf_status hssmf_analyze_grids(hssmf_ctx* c, int nsys, const int* dims, int n, const int* rowptr,
                                  const int* colind) {
   if (!c) return HSSMF_ERR_ARG;
-  auto t0 = std::chrono::steady_clock::now();
-  if (c->on_device) cudaStreamSynchronize(c->stream);
-  c->free_all();
-  hss_release(*c);
-  c->reset_device_pointers();
-  c->on_device = false;
-  c->analyzed = c->factored = false;
-  std::string e = analyze_grids(nsys, dims, n, rowptr, colind, c->opts.nd_leaf, c->opts.hss_leaf, c->sym);
-  if (!e.empty()) return c->fail(HSSMF_ERR_ARG, e);
-  hssmf_status st;
-  const Symbolic& S = c->sym;
-  c->rowptr_host.assign(rowptr, rowptr + n + 1);
-  c->colind_host.assign(colind, colind + S.nnz);
-  if ((st = c->build_plan())) return st;
-  if ((st = hss_prepare(*c))) return st;
-  c->analyzed = true;
-  c->stats = hssmf_stats();
-  c->stats.n = n;
-  c->stats.n_fronts = (int)S.fronts.size();
-  c->stats.n_levels = (int)S.levels.size();
-  c->stats.n_hss_fronts = c->n_hss;
-  for (auto& f : S.fronts) c->stats.max_front = std::max(c->stats.max_front, f.nf());
-  c->stats.t_analyze_ms =
-      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  return HSSMF_OK;
+  return analyze_common(c, n, rowptr, colind, [&] {
+    return analyze_grids(nsys, dims, n, rowptr, colind, c->opts.nd_leaf, c->opts.hss_leaf, c->sym);
+  });
+}
+
+hssmf_status hssmf_analyze_csr(hssmf_ctx* c, int n, const int* rowptr, const int* colind, int nfronts,
+                               const int* perm, const int* sep_ptr, const int* parent) {
+  if (!c) return HSSMF_ERR_ARG;
+  if (n < 1 || !rowptr || !colind) return c->fail(HSSMF_ERR_ARG, "empty or null pattern");
+  return analyze_common(c, n, rowptr, colind, [&] {
+    return analyze_csr(n, rowptr, colind, nfronts, perm, sep_ptr, parent, c->opts.nd_leaf, c->opts.hss_leaf,
+                       c->sym);
+  });
 }
 
 hssmf_status hssmf_factor(hssmf_ctx* c, const double* values) {

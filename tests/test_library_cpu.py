@@ -124,3 +124,138 @@ def test_batched_grids_reject_coupled_grids():
         s.analyze_grids([(8, 4, 1), (8, 4, 1)], A.rowptr, A.colind)
     with pytest.raises(P.HssmfError):  # sizes do not add up
         s.analyze_grids([(8, 8, 1), (2, 2, 1)], A.rowptr, A.colind)
+
+
+def _sym_pattern(n, edges):
+    """CSR pattern (with diagonal) of an undirected edge list."""
+    import scipy.sparse as sp
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    rows = np.concatenate([e[:, 0], e[:, 1], np.arange(n)])
+    cols = np.concatenate([e[:, 1], e[:, 0], np.arange(n)])
+    M = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+    M.sum_duplicates()
+    M.sort_indices()
+    return M.indptr.astype(np.int32), M.indices.astype(np.int32)
+
+
+def _brute_force_upd(rowptr, colind, perm, sb, se):
+    """I^upd of every front by the elimination game on the permuted pattern."""
+    n = len(perm)
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[perm] = np.arange(n)
+    adj = [set() for _ in range(n)]
+    for i in range(n):
+        for j in colind[rowptr[i]:rowptr[i + 1]]:
+            if i != j:
+                adj[iperm[i]].add(int(iperm[j]))
+    for v in range(n):  # eliminate in order: later neighbours become a clique
+        later = [w for w in adj[v] if w > v]
+        for a in later:
+            adj[a].update(w for w in later if w != a)
+    out = []
+    for b, e in zip(sb, se):
+        s = set()
+        for v in range(b, e):
+            s.update(w for w in adj[v] if w >= e)
+        out.append(sorted(s))
+    return out
+
+
+def _random_geometric(n, radius, seed):
+    rng = np.random.default_rng(seed)
+    p = rng.random((n, 3))
+    from scipy.spatial import cKDTree
+    pairs = cKDTree(p).query_pairs(radius, output_type="ndarray")
+    return pairs
+
+
+@pytest.mark.parametrize("case", ["grid2d", "grid3d", "geometric", "disconnected", "star", "path"])
+def test_algebraic_nested_dissection_structure(case):
+    """analyze_csr with no ordering: a permutation; every front's I^upd
+    contains the brute-force elimination's, lies after the front's separator
+    and equals it exactly where no set was split into groups of components
+    (a one-vertex separator between components passes one group's I^upd
+    through, which costs storage, not correctness); subtrees of sibling
+    fronts joined by no edge; leaves of at most 64 vertices."""
+    P = _lib()
+    if case == "grid2d":
+        A = problems.grid_poisson((23, 17, 1)); rp, ci = A.rowptr, A.colind
+    elif case == "grid3d":
+        A = problems.grid_poisson((9, 8, 7)); rp, ci = A.rowptr, A.colind
+    elif case == "geometric":
+        rp, ci = _sym_pattern(700, _random_geometric(700, 0.12, 1))
+    elif case == "disconnected":
+        g1 = problems.grid_poisson((12, 12, 1))
+        g2 = problems.grid_poisson((5, 9, 1))
+        iso = problems.CSR(7, np.arange(8), np.arange(7), np.ones(7))
+        A = problems.block_diag([g1, iso, g2]); rp, ci = A.rowptr, A.colind
+    elif case == "star":
+        rp, ci = _sym_pattern(300, [(0, k) for k in range(1, 300)])
+    else:
+        rp, ci = _sym_pattern(500, [(k, k + 1) for k in range(499)])
+    n = len(rp) - 1
+    s = P.Solver(P.Options.defaults())
+    s.analyze_csr(rp, ci)
+    nf = s.get_stats()["n_fronts"]
+    perm, sb, se, par, nu = s.get_symbolic(nf)
+    assert sorted(perm.tolist()) == list(range(n))
+    assert sb[0] == 0 and se[-1] == n and np.all(se > sb) and np.all(sb[1:] == se[:-1])
+    upd = _brute_force_upd(rp, ci, perm, sb, se)
+    for f in range(nf):  # the library's I^upd sets themselves
+        lib_u = s.get_upd(f, int(nu[f])).tolist()
+        assert set(upd[f]) <= set(lib_u) and all(g >= se[f] for g in lib_u)
+        if case != "geometric":
+            assert lib_u == upd[f]
+    # leaves are small; siblings' subtrees are not adjacent
+    children = [[] for _ in range(nf)]
+    for f in range(nf):
+        if par[f] >= 0:
+            children[par[f]].append(f)
+    lo = np.array(sb)
+    for f in range(nf):  # subtree ranges: a front's subtree ends at its separator
+        for c in children[f]:
+            lo[f] = min(lo[f], lo[c])
+    for f in range(nf):
+        if not children[f]:
+            assert se[f] - sb[f] <= 64
+        if len(children[f]) == 2:
+            a, b = children[f]
+            va = set(perm[lo[a]:se[a]].tolist())
+            vb = set(perm[lo[b]:se[b]].tolist())
+            for v in va:
+                assert not (set(ci[rp[v]:rp[v + 1]].tolist()) & vb)
+
+
+def test_caller_ordering_reproduces_the_grid_analysis():
+    P = _lib()
+    dims = (20, 20, 20)
+    A = problems.grid_poisson(dims)
+    g = P.Solver(P.Options.defaults())
+    g.analyze_grid(dims, A.rowptr, A.colind)
+    nf = g.get_stats()["n_fronts"]
+    perm, sb, se, par, nu = g.get_symbolic(nf)
+    c = P.Solver(P.Options.defaults())
+    c.analyze_csr(A.rowptr, A.colind, perm, np.append(sb, se[-1]), par)
+    p2, sb2, se2, par2, nu2 = c.get_symbolic(nf)
+    assert c.get_stats()["n_fronts"] == nf
+    for u, v in ((perm, p2), (sb, sb2), (se, se2), (par, par2), (nu, nu2)):
+        assert np.array_equal(u, v)
+
+
+def test_caller_ordering_rejects_invalid_trees():
+    P = _lib()
+    A = problems.grid_poisson((8, 8, 1))
+    n = A.n
+    ident = np.arange(n)
+    s = P.Solver(P.Options.defaults())
+    cases = [
+        (np.zeros(n), [0, n], [-1]),                        # not a permutation
+        (ident, [0, 32, 32, n], [2, 2, -1]),                # empty separator
+        (ident, [0, 32, n], [-1, 0]),                       # parent below child
+        (ident, [0, 16, 32, 48, n], [3, 3, 3, -1]),         # three children
+        (ident, [0, 32, n], [-1, -1]),                      # first half has later neighbours but is a root
+    ]
+    for perm, sp, pa in cases:
+        with pytest.raises(P.HssmfError):
+            s.analyze_csr(A.rowptr, A.colind, perm, sp, pa)
+    s.analyze_csr(A.rowptr, A.colind, ident, [0, n], [-1])  # one dense front is valid
