@@ -124,8 +124,12 @@ struct NodeRt {
   void *Xr = nullptr, *Xc = nullptr;
   int *Ir = nullptr, *Ic = nullptr;
   int slot = -1;
-  // per round
+  // compression: Y (this round's rows of the samples before the ID); S^r, S^c
+  // after the ID and R^r, R^c (rows 0..dk-1 computed, leading dimension dk,
+  // carried from round to round so that a later round adds only the rows of
+  // the new sample columns)
   void *Yr = nullptr, *Yc = nullptr, *Srp = nullptr, *Scp = nullptr, *Rrp = nullptr, *Rcp = nullptr;
+  int dk = 0;
   // factor
   void *Uexp = nullptr, *Vexp = nullptr, *Dt = nullptr, *Vt = nullptr, *tau = nullptr, *Tq = nullptr;
   int* lupiv = nullptr;
@@ -206,6 +210,9 @@ struct ViewGuard {  // transposed view of the listed fronts for a scope
 
 struct HssState {
   Pool fac, lvl, rnd, sol;
+  // node samples kept across compression rounds, alternating by round: round
+  // i writes keep[i & 1] and reads round i-1's arrays in the other pool
+  Pool keep[2];
   Pool gws;  // split-K partial tiles of one GEMM launch (reused by the next)
   bool transposed_ready = false;  // ULV of the transposed F11 trees built
   Ring ring;
@@ -303,6 +310,8 @@ void hss_release(hssmf_ctx& c) {
   HssState& H = *c.hss;
   H.fac.release();
   H.lvl.release();
+  H.keep[0].release();
+  H.keep[1].release();
   H.rnd.release();
   H.sol.release();
   H.gws.release();
@@ -555,8 +564,14 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     FrontRt* F;
     int t;
   };
-  while (!todo.empty()) {
+  H.keep[0].reset();
+  H.keep[1].reset();
+  for (int iter = 0; !todo.empty(); ++iter) {
     if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during HSS compression");
+    // every compressed node of an unfinished front gets new arrays in every
+    // round, so round iter-2's arrays are dead
+    Pool& keep = H.keep[iter & 1];
+    if (iter >= 2) keep.reset();
     int maxh = 0;
     for (FrontRt* F : todo) maxh = std::max(maxh, F->tree_h);
     for (int lv = 0; lv < maxh; ++lv) {
@@ -606,23 +621,28 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         HssKern<T>::extract(c.ds, c.d_values, X.arena(), d, n, X.s);
       });
       c.prof.mark(PH_PREID, X.s);
-      // (b) samples of the node before the ID, stored transposed (d x rows)
+      // (b) samples of the node before the ID, stored transposed (sample rows
+      // x node rows): all d rows for a node still to compress, only the rows
+      // dk..d-1 of the new sample columns for a node compressed in an earlier
+      // round (its children's arrays hold all d rows, leading dimension d)
       for (auto& it : batch) {
         const ClusterTree& tr = S.fronts[it.F->f].tree;
         FrontRt& F = *it.F;
         NodeRt& N = F.nd[it.t];
         const int d = F.d, lo = tr.lo[it.t];
-        N.Yr = X.A(H.rnd, (long long)d * N.m);
-        N.Yc = X.A(H.rnd, (long long)d * N.mc);
+        const int r0 = N.done ? N.dk : 0, rows = d - r0;
+        if (rows <= 0) continue;
+        N.Yr = X.A(H.rnd, (long long)rows * N.m);
+        N.Yc = X.A(H.rnd, (long long)rows * N.mc);
         if (tr.leaf(it.t)) {
-          X.copy((T*)F.Sr + lo, F.nf, 1, N.Yr, d, d, N.m);
-          X.copy((T*)F.Sc + lo, F.nf, 1, N.Yc, d, d, N.mc);
+          X.copy((T*)F.Sr + lo + (long long)r0 * F.nf, F.nf, 1, N.Yr, rows, rows, N.m);
+          X.copy((T*)F.Sc + lo + (long long)r0 * F.nf, F.nf, 1, N.Yc, rows, rows, N.mc);
         } else {
           const NodeRt &a = F.nd[tr.c1[it.t]], &b = F.nd[tr.c2[it.t]];
-          X.copy(a.Srp, d, 0, N.Yr, d, d, a.kr);
-          X.copy(b.Srp, d, 0, (T*)N.Yr + (long long)a.kr * d, d, d, b.kr);
-          X.copy(a.Scp, d, 0, N.Yc, d, d, a.kc);
-          X.copy(b.Scp, d, 0, (T*)N.Yc + (long long)a.kc * d, d, d, b.kc);
+          X.copy((T*)a.Srp + r0, d, 0, N.Yr, rows, rows, a.kr);
+          X.copy((T*)b.Srp + r0, d, 0, (T*)N.Yr + (long long)a.kr * rows, rows, rows, b.kr);
+          X.copy((T*)a.Scp + r0, d, 0, N.Yc, rows, rows, a.kc);
+          X.copy((T*)b.Scp + r0, d, 0, (T*)N.Yc + (long long)a.kc * rows, rows, rows, b.kc);
         }
       }
       X.flush_copy();
@@ -631,17 +651,20 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         FrontRt& F = *it.F;
         NodeRt& N = F.nd[it.t];
         const int d = F.d, lo = tr.lo[it.t];
+        const int r0 = N.done ? N.dk : 0, rows = d - r0;
+        if (rows <= 0) continue;
         if (tr.leaf(it.t)) {  // S^r - D R, S^c - D^* R (transposed)
-          X.gemm((T*)F.R + lo, F.nf, 1, N.D, N.n, 1, N.Yr, d, d, N.m, N.n, -1.0, 1.0);
-          X.gemm((T*)F.R + lo, F.nf, 1, N.D, N.n, 0, N.Yc, d, d, N.mc, N.n, -1.0, 1.0);
+          const T* Rt = (const T*)F.R + lo + (long long)r0 * F.nf;
+          X.gemm(Rt, F.nf, 1, N.D, N.n, 1, N.Yr, rows, rows, N.m, N.n, -1.0, 1.0);
+          X.gemm(Rt, F.nf, 1, N.D, N.n, 0, N.Yc, rows, rows, N.mc, N.n, -1.0, 1.0);
         } else {  // [S^r_1 - B12 R^r_2; S^r_2 - B21 R^r_1], [S^c_1 - B21^* R^c_2; S^c_2 - B12^* R^c_1]
           const NodeRt &a = F.nd[tr.c1[it.t]], &b = F.nd[tr.c2[it.t]];
-          X.gemm(b.Rrp, d, 0, N.B12, std::max(a.kr, 1), 1, N.Yr, d, d, a.kr, b.kc, -1.0, 1.0);
-          X.gemm(a.Rrp, d, 0, N.B21, std::max(b.kr, 1), 1, (T*)N.Yr + (long long)a.kr * d, d, d, b.kr,
-                 a.kc, -1.0, 1.0);
-          X.gemm(b.Rcp, d, 0, N.B21, std::max(b.kr, 1), 0, N.Yc, d, d, a.kc, b.kr, -1.0, 1.0);
-          X.gemm(a.Rcp, d, 0, N.B12, std::max(a.kr, 1), 0, (T*)N.Yc + (long long)a.kc * d, d, d, b.kc,
-                 a.kr, -1.0, 1.0);
+          X.gemm((T*)b.Rrp + r0, d, 0, N.B12, std::max(a.kr, 1), 1, N.Yr, rows, rows, a.kr, b.kc, -1.0, 1.0);
+          X.gemm((T*)a.Rrp + r0, d, 0, N.B21, std::max(b.kr, 1), 1, (T*)N.Yr + (long long)a.kr * rows, rows,
+                 rows, b.kr, a.kc, -1.0, 1.0);
+          X.gemm((T*)b.Rcp + r0, d, 0, N.B21, std::max(b.kr, 1), 0, N.Yc, rows, rows, a.kc, b.kr, -1.0, 1.0);
+          X.gemm((T*)a.Rcp + r0, d, 0, N.B12, std::max(a.kr, 1), 0, (T*)N.Yc + (long long)a.kc * rows, rows,
+                 rows, b.kc, a.kr, -1.0, 1.0);
         }
       }
       X.flush_gemm();
@@ -799,26 +822,40 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       c.prof.mark(PH_POSTID, X.s);
       // (d) after the ID: S <- S(J, :), R^r = V^* R, R^c = U^* R, skeleton sets
       std::vector<IntGatherJob> ig;
-      for (auto& it : batch) {
+      std::vector<int> r0s(batch.size(), 0);
+      for (size_t bi = 0; bi < batch.size(); ++bi) {
+        const Item& it = batch[bi];
         const ClusterTree& tr = S.fronts[it.F->f].tree;
         FrontRt& F = *it.F;
         NodeRt& N = F.nd[it.t];
         if (!N.done) continue;
         const int d = F.d, lo = tr.lo[it.t];
-        N.Srp = X.A(H.rnd, (long long)d * N.kr);
-        N.Scp = X.A(H.rnd, (long long)d * N.kc);
-        X.copy(N.Yr, d, 0, N.Srp, d, d, N.kr, nullptr, N.piv_r);
-        X.copy(N.Yc, d, 0, N.Scp, d, d, N.kc, nullptr, N.piv_c);
-        T* Rpc = X.A(H.rnd, (long long)d * N.mc);
-        T* Rpr = X.A(H.rnd, (long long)d * N.m);
+        const int r0 = N.dk, rows = d - r0;  // rows 0..r0-1 were computed in earlier rounds
+        r0s[bi] = r0;
+        if (rows <= 0) continue;
+        T* Srp = X.A(keep, (long long)d * N.kr);
+        T* Scp = X.A(keep, (long long)d * N.kc);
+        T* Rpc = X.A(keep, (long long)d * N.mc);
+        T* Rpr = X.A(keep, (long long)d * N.m);
+        if (r0 > 0) {  // the finished rows move to the arrays of leading dimension d
+          X.copy(N.Srp, r0, 0, Srp, d, r0, N.kr);
+          X.copy(N.Scp, r0, 0, Scp, d, r0, N.kc);
+          X.copy(N.Rrp, r0, 0, Rpc, d, r0, N.kc);
+          X.copy(N.Rcp, r0, 0, Rpr, d, r0, N.kr);
+        }
+        X.copy(N.Yr, rows, 0, Srp + r0, d, rows, N.kr, nullptr, N.piv_r);
+        X.copy(N.Yc, rows, 0, Scp + r0, d, rows, N.kc, nullptr, N.piv_c);
         if (tr.leaf(it.t)) {
-          X.copy((T*)F.R + lo, F.nf, 1, Rpc, d, d, N.mc, nullptr, N.piv_c);
-          X.copy((T*)F.R + lo, F.nf, 1, Rpr, d, d, N.m, nullptr, N.piv_r);
+          const T* Rt = (const T*)F.R + lo + (long long)r0 * F.nf;
+          X.copy(Rt, F.nf, 1, Rpc + r0, d, rows, N.mc, nullptr, N.piv_c);
+          X.copy(Rt, F.nf, 1, Rpr + r0, d, rows, N.m, nullptr, N.piv_r);
         } else {
           const NodeRt &a = F.nd[tr.c1[it.t]], &b = F.nd[tr.c2[it.t]];
-          X.copy(a.Rrp, d, 0, Rpc, d, d, N.mc, nullptr, N.piv_c, b.Rrp, d, a.kc);
-          X.copy(a.Rcp, d, 0, Rpr, d, d, N.m, nullptr, N.piv_r, b.Rcp, d, a.kr);
+          X.copy((T*)a.Rrp + r0, d, 0, Rpc + r0, d, rows, N.mc, nullptr, N.piv_c, (T*)b.Rrp + r0, d, a.kc);
+          X.copy((T*)a.Rcp + r0, d, 0, Rpr + r0, d, rows, N.m, nullptr, N.piv_r, (T*)b.Rcp + r0, d, a.kr);
         }
+        N.Srp = Srp;
+        N.Scp = Scp;
         N.Rrp = Rpc;
         N.Rcp = Rpr;
         if (N.slot == 1) {
@@ -836,15 +873,17 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         }
       }
       X.flush_copy();
-      for (auto& it : batch) {
-        FrontRt& F = *it.F;
-        NodeRt& N = F.nd[it.t];
+      for (size_t bi = 0; bi < batch.size(); ++bi) {
+        FrontRt& F = *batch[bi].F;
+        NodeRt& N = F.nd[batch[bi].t];
         if (!N.done) continue;
-        const int d = F.d;
-        X.gemm((T*)N.Rrp + (long long)N.kc * d, d, 0, N.Xc, std::max(N.kc, 1), 1, N.Rrp, d, d, N.kc,
-               N.mc - N.kc, 1.0, 1.0);
-        X.gemm((T*)N.Rcp + (long long)N.kr * d, d, 0, N.Xr, std::max(N.kr, 1), 1, N.Rcp, d, d, N.kr,
-               N.m - N.kr, 1.0, 1.0);
+        const int d = F.d, r0 = r0s[bi], rows = d - r0;
+        if (rows <= 0) continue;
+        X.gemm((T*)N.Rrp + (long long)N.kc * d + r0, d, 0, N.Xc, std::max(N.kc, 1), 1, (T*)N.Rrp + r0, d, rows,
+               N.kc, N.mc - N.kc, 1.0, 1.0);
+        X.gemm((T*)N.Rcp + (long long)N.kr * d + r0, d, 0, N.Xr, std::max(N.kr, 1), 1, (T*)N.Rcp + r0, d, rows,
+               N.kr, N.m - N.kr, 1.0, 1.0);
+        N.dk = d;
       }
       X.flush_gemm();
       X.launch(ig, [&](const IntGatherJob* d, int n) { HssKern<T>::int_gather(d, n, X.s); });
