@@ -453,3 +453,26 @@ def test_anisotropic_grf_operator():
     assert np.abs(rs[interior]).max() < 1e-12
     g = problems.gaussian_random_field(16, 4.0, 2.0, seed=9)
     assert abs(g.mean()) < 1e-12 and abs(g.std() - 2.0) < 1e-12
+
+
+def test_batch_convdiff_generator():
+    """The batch input: seeded sides in [lo, hi] and velocities in [-v, v],
+    blocks equal to the single-system upwind operator, nothing between blocks,
+    each block an M-matrix row pattern (positive diagonal dominating)."""
+    sides, vel, A = problems.batch_convdiff2d(12, side_lo=5, side_hi=11, vmax=50.0, seed=3)
+    sides2, vel2, A2 = problems.batch_convdiff2d(12, side_lo=5, side_hi=11, vmax=50.0, seed=3)
+    assert sides == sides2 and np.array_equal(vel, vel2) and np.array_equal(A.values, A2.values)
+    assert all(5 <= k <= 11 for k in sides) and np.all(np.abs(vel) <= 50.0)
+    S = A.to_scipy().tocsr()
+    off = 0
+    for k, (vx, vy) in zip(sides, vel):
+        n = k * k
+        blk = S[off:off + n, off:off + n].toarray()
+        ref = problems.grid_convdiff2d(k, vx, vy).to_scipy().toarray()
+        assert np.array_equal(blk, ref)
+        rest = S[off:off + n, :].toarray()
+        rest[:, off:off + n] = 0.0
+        assert not rest.any()
+        assert np.all(np.diag(blk) >= np.abs(blk).sum(axis=1) - np.diag(blk) - 1e-9)
+        off += n
+    assert off == A.n
