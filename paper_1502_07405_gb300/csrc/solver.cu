@@ -67,6 +67,14 @@ void* hssmf_ctx::dalloc(size_t bytes) {
   return p;
 }
 
+void hssmf_ctx::dfree(void* p) {
+  if (!p) return;
+  auto it = std::find(owned.begin(), owned.end(), p);
+  if (it == owned.end()) return;
+  cudaFree(p);
+  owned.erase(it);
+}
+
 void hssmf_ctx::free_all() {
   for (void* p : owned) cudaFree(p);
   owned.clear();
@@ -412,16 +420,33 @@ hssmf_status hssmf_ctx::ensure_krylov(int nrhs) {
   for (size_t s : sizes) total += s;
   const size_t need = sizeof(double) * total;
   if (need <= kry_bytes && nrhs == kry_nrhs) return HSSMF_OK;
-  kry_bytes = need;
-  kry_nrhs = nrhs;
-  double* p = (double*)dalloc(need);
-  int* a = (int*)dalloc(sizeof(int) * nrhs);
-  if (!p || !a) return fail(HSSMF_ERR_OOM, "Krylov workspace allocation failed");
+  // a smaller or equal workspace is laid out again inside the current one;
+  // a larger one replaces it (queued work may still read the old one)
+  if (need > kry_cap || nrhs > act_cap) {
+    cudaStreamSynchronize(stream);
+    dfree(kry_base);
+    dfree(k_active);
+    kry_base = nullptr;
+    k_active = nullptr;
+    kry_cap = 0;
+    act_cap = 0;
+    kry_bytes = 0;
+    kry_nrhs = -1;
+    double* p = (double*)dalloc(need);
+    int* a = (int*)dalloc(sizeof(int) * (size_t)nrhs);
+    if (!p || !a) return fail(HSSMF_ERR_OOM, "Krylov workspace allocation failed");
+    kry_base = p;
+    kry_cap = need;
+    k_active = a;
+    act_cap = nrhs;
+  }
+  double* p = kry_base;
   for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
     *ptrs[i] = p;
     p += sizes[i];
   }
-  k_active = a;
+  kry_bytes = need;
+  kry_nrhs = nrhs;
   if (!h_pin) {
     if (cudaMallocHost(&h_pin, 1 << 20) != cudaSuccess) {
       cudaGetLastError();

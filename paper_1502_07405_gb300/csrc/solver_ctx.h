@@ -122,9 +122,11 @@ struct hssmf_ctx {
   int w_nrhs = -1;
   double* d_io = nullptr;
   size_t io_bytes = 0;
-  // Krylov workspace
-  size_t kry_bytes = 0;
-  int kry_nrhs = -1;
+  // Krylov workspace: kry_bytes / kry_nrhs describe the current layout inside
+  // kry_base (kry_cap bytes); k_active holds act_cap ints
+  size_t kry_bytes = 0, kry_cap = 0;
+  int kry_nrhs = -1, act_cap = 0;
+  double* kry_base = nullptr;
   double *k_V = nullptr, *k_Z = nullptr, *k_x = nullptr, *k_r = nullptr, *k_w = nullptr,
          *k_b = nullptr, *k_t = nullptr, *k_H = nullptr, *k_cs = nullptr, *k_sn = nullptr,
          *k_g = nullptr, *k_y = nullptr, *k_part = nullptr, *k_s = nullptr;
@@ -154,6 +156,7 @@ struct hssmf_ctx {
   hssmf_status fail(hssmf_status st, const std::string& msg);
   hssmf_status cuda_check(cudaError_t e, const char* what);
   void* dalloc(size_t bytes);
+  void dfree(void* p);  // frees one allocation of dalloc (no-op for others)
   void free_all();
   void reset_device_pointers() {
     d_status = nullptr;
@@ -171,6 +174,10 @@ struct hssmf_ctx {
     io_bytes = 0;
     kry_bytes = 0;
     kry_nrhs = -1;
+    kry_cap = 0;
+    act_cap = 0;
+    kry_base = nullptr;
+    k_active = nullptr;
     h_pin = nullptr;
     d_sysoff = nullptr;
     k_seg = nullptr;
