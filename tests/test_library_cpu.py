@@ -259,3 +259,45 @@ def test_caller_ordering_rejects_invalid_trees():
         with pytest.raises(P.HssmfError):
             s.analyze_csr(A.rowptr, A.colind, perm, sp, pa)
     s.analyze_csr(A.rowptr, A.colind, ident, [0, n], [-1])  # one dense front is valid
+
+
+@pytest.mark.parametrize("bad", [dict(precision=2), dict(d0=0), dict(dd=0), dict(hss_tol=-1.0),
+                                 dict(hss_tol=float("nan")), dict(gmres_restart=0), dict(maxit=-1),
+                                 dict(hss_leaf=0), dict(nd_leaf=0), dict(oversample_p=-1)])
+def test_create_rejects_bad_options(bad):
+    P = _lib()
+    with pytest.raises(P.HssmfError) as e:
+        P.Solver(P.Options.defaults(**bad))
+    assert e.value.status == P.ERR_ARG
+
+
+def test_solve_and_gradient_before_factor_are_errors():
+    P = _lib()
+    A = problems.grid_poisson((8, 8, 1))
+    s = P.Solver()
+    s.analyze_grid((8, 8, 1), A.rowptr, A.colind)
+    b = np.ones(A.n)
+    for fn in (s.solve, s.solve_T):
+        with pytest.raises(P.HssmfError) as e:
+            fn(b)
+        assert e.value.status == P.ERR_ARG
+
+
+def test_analyze_grids_and_csr_argument_errors():
+    P = _lib()
+    A = problems.grid_poisson((6, 6, 1))
+    s = P.Solver()
+    with pytest.raises(P.HssmfError):
+        s.analyze_grids([], A.rowptr, A.colind)  # no grid
+    with pytest.raises(P.HssmfError):
+        s.analyze_grids([(6, 0, 1)], A.rowptr, A.colind)  # empty grid
+    ci = A.colind.copy()
+    ci[0], ci[1] = ci[1], ci[0]  # row 0 not ascending
+    with pytest.raises(P.HssmfError):
+        s.analyze_csr(A.rowptr, ci)
+    asym = problems.CSR(2, [0, 2, 3], [0, 1, 1], [1.0, 1.0, 1.0])  # (0, 1) without (1, 0)
+    with pytest.raises(P.HssmfError):
+        s.analyze_csr(asym.rowptr, asym.colind)
+    one = problems.CSR(1, [0, 1], [0], [2.0])  # a 1 x 1 matrix is one leaf front
+    s.analyze_csr(one.rowptr, one.colind)
+    assert s.get_stats()["n_fronts"] == 1
