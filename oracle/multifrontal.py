@@ -105,9 +105,22 @@ def extend_add(parent_n, parts):
 
 
 def factor(A_natural, dims, opts: Options):
+    """Multifrontal factorization of a matrix on a grid (geometric ND)."""
     t0 = time.perf_counter()
-    fz = Factorization()
     perm, fronts, Anew = ordering.analyze(dims, A_natural, opts.nd_leaf, opts.hss_leaf)
+    return _factor_ordered(perm, fronts, Anew, opts, t0)
+
+
+def factor_csr(A_natural, opts: Options, perm=None, sep_ptr=None, parent=None):
+    """Multifrontal factorization of a general pattern: algebraic nested
+    dissection, or the caller's ordering and separator tree."""
+    t0 = time.perf_counter()
+    perm, fronts, Anew = ordering.analyze_csr(A_natural, opts.nd_leaf, opts.hss_leaf, perm, sep_ptr, parent)
+    return _factor_ordered(perm, fronts, Anew, opts, t0)
+
+
+def _factor_ordered(perm, fronts, Anew, opts, t0):
+    fz = Factorization()
     fz.perm, fz.fronts, fz.A = perm, fronts, Anew
     fz.data = [None] * len(fronts)
     pos = {}

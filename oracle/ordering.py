@@ -26,6 +26,13 @@ that ordering and tree agree bit for bit):
     the separator bisection tree, the F22 tree halves the sorted I^upd list
     at floor(n/2) until a node has <= b indices; a front without I^upd has
     the F11 tree as its HSS tree.
+
+General sparse patterns (no geometry; the paper orders its application
+matrices with METIS/SCOTCH, which are not used): ``algebraic_nested_dissection``
+(level-structure separators, rule in its docstring) or a caller-given ordering
+and separator tree (``fronts_from_tree``); F11 trees halve the separator's
+index range.  Pinned by validity against brute-force elimination and by exact
+solves (tests), and matched bit for bit by the library.
 """
 from __future__ import annotations
 
@@ -294,5 +301,173 @@ def analyze(dims, A_natural, nd_leaf=8, hss_leaf=128):
     perm, fronts = nested_dissection(dims, nd_leaf, hss_leaf)
     Anew = permute_csr(A_natural, perm)
     symbolic(fronts, Anew)
+    build_hss_trees(fronts, hss_leaf)
+    return perm, fronts, Anew
+
+
+# ----------------------------------------------------------------------------
+# General sparse patterns (no geometry)
+# ----------------------------------------------------------------------------
+def _halving_pieces(n, b):
+    """F11 cluster tree of a separator without geometry: halve the index
+    range (left part floor(n/2)) until a piece has at most b indices."""
+    if n <= b:
+        return ("leaf", n)
+    return ("split", _halving_pieces(n // 2, b), _halving_pieces(n - n // 2, b))
+
+
+def algebraic_nested_dissection(A_natural, nd_leaf=8, hss_leaf=128):
+    """Nested dissection of a structurally symmetric pattern by level
+    structures (a reading: the paper orders its application matrices with
+    METIS/SCOTCH, which are not used here).
+
+    - Connected components are separate elimination trees, in the order of
+      their smallest vertex.
+    - A set of at most max(16, nd_leaf^2) vertices is a leaf front.
+    - A connected set: breadth-first search (neighbours in CSR order) from
+      its first vertex; a second search from the last vertex reached gives
+      the level structure.  Depth < 2: one leaf front.  Otherwise the
+      separator level l is the first level >= 1 where the count of levels
+      0..l passes half the set (l <= depth - 1); a level-l vertex with no
+      neighbour beyond l joins the near side.  Near side, far side and
+      separator keep the search order.
+    - A disconnected set: its components (searched from each vertex in set
+      order) sorted by decreasing size (ties in discovery order), each given
+      to the group with fewer vertices so far (the first group on a tie);
+      the last vertex of the second group is the separator.
+    Fronts in postorder (near side, far side, separator); returns (perm,
+    fronts) with perm[new] = old."""
+    A = A_natural.tocsr()
+    n = A.shape[0]
+    rp, ci = A.indptr, A.indices
+    leaf_max = max(16, nd_leaf * nd_leaf)
+    perm, fronts = [], []
+
+    def bfs(start, inset):
+        order, lev = [start], {start: 0}
+        h = 0
+        while h < len(order):
+            u = order[h]
+            h += 1
+            for w in ci[rp[u]:rp[u + 1]]:
+                w = int(w)
+                if w in inset and w not in lev:
+                    lev[w] = lev[u] + 1
+                    order.append(w)
+        return order, lev
+
+    def components(V):
+        inset, seen, comps = set(V), set(), []
+        for v in V:
+            if v not in seen:
+                order, _ = bfs(v, inset)
+                seen.update(order)
+                comps.append(order)
+        return comps
+
+    def add_front(sep, kids):
+        f = Front(sep_begin=len(perm), sep_end=len(perm) + len(sep), children=list(kids))
+        perm.extend(sep)
+        f.sep_pieces = _halving_pieces(f.ns, hss_leaf)
+        f.first = min([fronts[k].first for k in kids] + [f.sep_begin])
+        fronts.append(f)
+        me = len(fronts) - 1
+        for k in kids:
+            fronts[k].parent = me
+        return me
+
+    def rec(V):
+        if len(V) <= leaf_max:
+            return add_front(V, [])
+        inset = set(V)
+        order, lev = bfs(V[0], inset)
+        if len(order) < len(V):
+            comps = sorted(components(V), key=len, reverse=True)  # stable
+            ga, gb, na, nb = [], [], 0, 0
+            for c in comps:
+                if na <= nb:
+                    ga += c
+                    na += len(c)
+                else:
+                    gb += c
+                    nb += len(c)
+            S = [gb.pop()]
+            near, far = ga, gb
+        else:
+            order, lev = bfs(order[-1], inset)
+            depth = lev[order[-1]]
+            if depth < 2:
+                return add_front(V, [])
+            cnt = np.bincount([lev[v] for v in order], minlength=depth + 1)
+            l, cum = 1, int(cnt[0])
+            while l < depth - 1 and 2 * (cum + int(cnt[l])) <= len(V):
+                cum += int(cnt[l])
+                l += 1
+            near, S, far = [], [], []
+            for v in order:
+                if lev[v] < l:
+                    near.append(v)
+                elif lev[v] > l:
+                    far.append(v)
+                elif any(int(w) in lev and lev[int(w)] > l for w in ci[rp[v]:rp[v + 1]]):
+                    S.append(v)
+                else:
+                    near.append(v)
+        kids = []
+        if near:
+            kids.append(rec(near))
+        if far:
+            kids.append(rec(far))
+        return add_front(S, kids)
+
+    for comp in components(list(range(n))):
+        rec(comp)
+    return np.asarray(perm, dtype=np.int64), fronts
+
+
+def fronts_from_tree(n, sep_ptr, parent, hss_leaf=128):
+    """Fronts of a caller-given separator tree: front f owns the new indices
+    [sep_ptr[f], sep_ptr[f+1]), parent[f] > f or -1 (postorder)."""
+    nf = len(parent)
+    if sep_ptr[0] != 0 or sep_ptr[nf] != n:
+        raise ValueError("sep_ptr must run from 0 to n")
+    fronts = [Front(sep_begin=int(sep_ptr[f]), sep_end=int(sep_ptr[f + 1]), children=[]) for f in range(nf)]
+    for f in range(nf):
+        if fronts[f].ns < 1:
+            raise ValueError("empty separator")
+        p = int(parent[f])
+        if p != -1 and not f < p < nf:
+            raise ValueError("fronts must be in postorder")
+        fronts[f].parent = p
+        if p >= 0:
+            fronts[p].children.append(f)
+        fronts[f].sep_pieces = _halving_pieces(fronts[f].ns, hss_leaf)
+    for f in range(nf):
+        if len(fronts[f].children) > 2:
+            raise ValueError("at most two children per front")
+        fronts[f].first = min([fronts[k].first for k in fronts[f].children] + [fronts[f].sep_begin])
+    return fronts
+
+
+def analyze_csr(A_natural, nd_leaf=8, hss_leaf=128, perm=None, sep_ptr=None, parent=None):
+    """Symbolic phase of a general pattern: the algebraic nested dissection
+    (perm None) or the caller's ordering and separator tree; then I^upd, the
+    HSS trees (F11 by halving) and the permuted matrix."""
+    if perm is None:
+        perm, fronts = algebraic_nested_dissection(A_natural, nd_leaf, hss_leaf)
+    else:
+        perm = np.asarray(perm, dtype=np.int64)
+        if sorted(perm.tolist()) != list(range(A_natural.shape[0])):
+            raise ValueError("perm is not a permutation")
+        fronts = fronts_from_tree(A_natural.shape[0], sep_ptr, parent, hss_leaf)
+    Anew = permute_csr(A_natural, perm)
+    symbolic(fronts, Anew)
+    for f in fronts:
+        if f.parent >= 0:
+            p = fronts[f.parent]
+            if not set(f.upd.tolist()) <= set(p.indices.tolist()):
+                raise ValueError("a front's I^upd is not inside its parent's index set")
+        elif f.nu:
+            raise ValueError("a root front has a non-empty I^upd")
     build_hss_trees(fronts, hss_leaf)
     return perm, fronts, Anew

@@ -198,8 +198,8 @@ struct AlgebraicND {
       restamp(V, st);
       std::vector<std::vector<int>> comps;
       components(V, st, comps);
-      std::sort(comps.begin(), comps.end(),
-                [](const std::vector<int>& a, const std::vector<int>& b) { return a.size() > b.size(); });
+      std::stable_sort(comps.begin(), comps.end(),  // equal sizes keep their discovery order
+                       [](const std::vector<int>& a, const std::vector<int>& b) { return a.size() > b.size(); });
       size_t na = 0, nb = 0;
       std::vector<int> ga, gb;
       for (auto& c : comps) {  // largest first, each to the smaller group

@@ -301,3 +301,42 @@ def test_analyze_grids_and_csr_argument_errors():
     one = problems.CSR(1, [0, 1], [0], [2.0])  # a 1 x 1 matrix is one leaf front
     s.analyze_csr(one.rowptr, one.colind)
     assert s.get_stats()["n_fronts"] == 1
+
+
+@pytest.mark.parametrize("case", ["grid2d", "grid3d", "geometric", "disconnected", "star", "path"])
+def test_algebraic_ordering_bit_exact_vs_oracle(case):
+    """The library's algebraic nested dissection and symbolic phase agree
+    with the oracle's bit for bit: ordering, separator ranges, parents and
+    every I^upd."""
+    import scipy.sparse as sp
+    from oracle import ordering as ordo
+    P = _lib()
+    if case == "grid2d":
+        A = problems.grid_poisson((23, 17, 1)); rp, ci = A.rowptr, A.colind
+    elif case == "grid3d":
+        A = problems.grid_poisson((9, 8, 7)); rp, ci = A.rowptr, A.colind
+    elif case == "geometric":
+        rp, ci = _sym_pattern(3000, _random_geometric(3000, 0.08, 2))
+    elif case == "disconnected":
+        g1 = problems.grid_poisson((12, 12, 1))
+        g2 = problems.grid_poisson((5, 9, 1))
+        iso = problems.CSR(7, np.arange(8), np.arange(7), np.ones(7))
+        A = problems.block_diag([g1, iso, g2]); rp, ci = A.rowptr, A.colind
+    elif case == "star":
+        rp, ci = _sym_pattern(300, [(0, k) for k in range(1, 300)])
+    else:
+        rp, ci = _sym_pattern(500, [(k, k + 1) for k in range(499)])
+    n = len(rp) - 1
+    M = sp.csr_matrix((np.ones(len(ci)), ci, rp), shape=(n, n))
+    perm_o, fr_o, _ = ordo.analyze_csr(M)
+    s = P.Solver(P.Options.defaults())
+    s.analyze_csr(rp, ci)
+    nf = s.get_stats()["n_fronts"]
+    assert nf == len(fr_o)
+    perm, sb, se, par, nu = s.get_symbolic(nf)
+    assert np.array_equal(perm, perm_o)
+    assert np.array_equal(sb, [f.sep_begin for f in fr_o])
+    assert np.array_equal(se, [f.sep_end for f in fr_o])
+    assert np.array_equal(par, [f.parent for f in fr_o])
+    for i, f in enumerate(fr_o):
+        assert np.array_equal(s.get_upd(i, f.nu), f.upd)

@@ -476,3 +476,78 @@ def test_batch_convdiff_generator():
         assert np.all(np.diag(blk) >= np.abs(blk).sum(axis=1) - np.diag(blk) - 1e-9)
         off += n
     assert off == A.n
+
+
+def _geometric_pattern_operator(n, radius, seed):
+    from scipy.spatial import cKDTree
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 3))
+    pairs = cKDTree(pts).query_pairs(radius, output_type="ndarray")
+    w = rng.uniform(0.5, 2.0, len(pairs))
+    L = sp.csr_matrix((-np.concatenate([w, w]), (np.concatenate([pairs[:, 0], pairs[:, 1]]),
+                                                  np.concatenate([pairs[:, 1], pairs[:, 0]]))), shape=(n, n))
+    M = (L + sp.diags(-np.asarray(L.sum(axis=1)).ravel() + 0.05)).tocsr()
+    M.sort_indices()
+    return M
+
+
+def test_algebraic_ordering_is_a_valid_elimination_structure():
+    """Oracle algebraic nested dissection: a permutation; the subtrees of two
+    sibling fronts share no edge; every I^upd contains the brute-force
+    elimination's and lies after the separator; leaves of at most 64
+    vertices; one root per connected component."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    M = _geometric_pattern_operator(600, 0.13, 4)
+    M = sp.block_diag([M, problems.grid_poisson((7, 5, 1)).to_scipy()]).tocsr()  # two components
+    n = M.shape[0]
+    perm, fronts, Anew = ordering.analyze_csr(M)
+    assert sorted(perm.tolist()) == list(range(n))
+    ncomp = connected_components(M, directed=False)[0]
+    assert sum(f.parent < 0 for f in fronts) == ncomp
+    # brute-force elimination of the permuted pattern
+    adj = [set(Anew.indices[Anew.indptr[i]:Anew.indptr[i + 1]].tolist()) - {i} for i in range(n)]
+    for v in range(n):
+        later = [w for w in adj[v] if w > v]
+        for a in later:
+            adj[a].update(w for w in later if w != a)
+    for i, f in enumerate(fronts):
+        bf = set()
+        for v in range(f.sep_begin, f.sep_end):
+            bf.update(w for w in adj[v] if w >= f.sep_end)
+        assert bf <= set(f.upd.tolist()) and all(g >= f.sep_end for g in f.upd)
+        if not f.children:
+            assert f.ns <= 64
+        if len(f.children) == 2:
+            a, b = (fronts[c] for c in f.children)
+            va = set(range(a.first, a.sep_end))
+            vb = set(range(b.first, b.sep_end))
+            for v in va:
+                assert not (set(Anew.indices[Anew.indptr[v]:Anew.indptr[v + 1]].tolist()) & vb)
+
+
+def test_factor_csr_is_exact_without_compression_and_as_eps_goes_to_zero():
+    import scipy.sparse.linalg as spla
+    M = _geometric_pattern_operator(900, 0.11, 6)
+    b = problems.rhs_uniform(M.shape[0], 1, 2)[:, 0]
+    xd = spla.spsolve(M.tocsc(), b)
+    fz = mf.factor_csr(M, mf.Options())  # dense fronts only
+    assert np.linalg.norm(mf.apply_inverse(fz, b) - xd) <= 1e-10 * np.linalg.norm(xd)
+    fh = mf.factor_csr(M, mf.Options(hss_tol=1e-13, hss_min_front=64, d0=16, dd=16, hss_leaf=16))
+    assert any(d is not None and hasattr(d, "H") for d in fh.data)
+    assert np.linalg.norm(mf.apply_inverse(fh, b) - xd) <= 1e-9 * np.linalg.norm(xd)
+    assert np.linalg.norm(mf.apply_inverse(fh, b, transpose=True) - spla.spsolve(M.T.tocsc(), b)) \
+        <= 1e-9 * np.linalg.norm(xd)
+
+
+def test_caller_tree_is_validated_by_the_oracle():
+    M = problems.grid_poisson((8, 8, 1)).to_scipy()
+    n = M.shape[0]
+    ident = np.arange(n)
+    with pytest.raises(ValueError):
+        ordering.analyze_csr(M, perm=ident, sep_ptr=[0, 32, n], parent=[-1, -1])  # not an elimination tree
+    with pytest.raises(ValueError):
+        ordering.analyze_csr(M, perm=ident, sep_ptr=[0, 16, 32, 48, n], parent=[3, 3, 3, -1])
+    perm, fronts, _ = ordering.analyze_csr(M, perm=ident, sep_ptr=[0, n], parent=[-1])
+    assert len(fronts) == 1 and fronts[0].nu == 0
