@@ -55,3 +55,26 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     bench.run_reference(Args())  # returns at once: no oracle run, no output
     assert capsys.readouterr().out == ""
+
+
+def test_relres_takes_the_worst_system_and_column(monkeypatch):
+    """bench._relres: the largest relative residual over the right-hand sides,
+    and over the systems of a batch (each system's own norms)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import problems
+    mats = [problems.grid_poisson((4, 4, 1)), problems.grid_poisson((3, 5, 1), scale=10.0)]
+    A = problems.block_diag(mats)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((A.n, 2))
+    b = A.to_scipy() @ x
+    xe = x.copy()
+    xe[16:, 1] += 1e-3  # error in the second system, second column only
+    monkeypatch.setattr(bench, "WORKLOAD", dict(batch=True, sys_off=[0, 16, 31]))
+    r2 = np.linalg.norm(b[16:, 1] - mats[1].to_scipy() @ xe[16:, 1]) / np.linalg.norm(b[16:, 1])
+    assert bench._relres(A, xe, b) == pytest.approx(r2, rel=1e-12)
+    monkeypatch.setattr(bench, "WORKLOAD", dict())
+    rg = np.linalg.norm(b[:, 1] - A.to_scipy() @ xe[:, 1]) / np.linalg.norm(b[:, 1])
+    assert bench._relres(A, xe, b) == pytest.approx(rg, rel=1e-12)
+    assert rg < r2  # the whole-vector residual hides the per-system one
