@@ -212,9 +212,12 @@ hssmf_status hssmf_pattern_grad(hssmf_ctx* ctx, const double* lambda, const doub
 
 /* Records of every interpolative decomposition of the last factorization
  * run with profiling on (Algorithm 1 with the adaptive scheme of Section
- * 2.2.1): 9 ints per node attempt -- front, HSS node, adaptive round of the
- * front, sample columns d, rows m of the row ID, rows of the column ID,
- * row rank, column rank, 1 if both IDs were accepted.  Copies at most
+ * 2.2.1): 11 ints per node attempt -- front, HSS node, adaptive round of
+ * the front, sample columns d, rows m of the row ID, rows of the column ID,
+ * row rank, column rank, 1 if both IDs were accepted, and the kernel that
+ * ran the row ID and the column ID, coded 100 * family + CTAs per ID
+ * (family 0: one CTA, matrix in L2; 1: matrix in shared memory; 2: matrix
+ * in registers; 3: L2-resident cluster).  Copies at most
  * max_records records into rec (host, may be NULL) and returns the number
  * available, or -1 for a NULL context. */
 int hssmf_get_id_trace(const hssmf_ctx* ctx, int* rec, int max_records);
@@ -224,9 +227,13 @@ int hssmf_get_id_trace(const hssmf_ctx* ctx, int* rec, int max_records);
  * columns of Y_j (d_j x m_j, column-major, leading dimension d_j, device
  * memory at Y + y_off[j] elements, arithmetic T = double for prec 0, float
  * for prec 1) by column-pivoted Householder QR with column norms recomputed
- * from the trailing rows at every step (FP64) and the first largest norm
- * winning; the rank k_j is the first i with |R_{i+1,i+1}| <= eps |R_11|
- * (0 if R_11 = 0), else min(d_j, m_j).  Outputs: rank_host[j];
+ * from the trailing rows at every step and the first largest norm winning;
+ * the rank k_j is the first i with |R_{i+1,i+1}| <= eps |R_11| (0 if
+ * R_11 = 0), else min(d_j, m_j).  Norms are sums in T: FP64 for prec 0; for
+ * prec 1 the squared norms and the pivot choice are FP32, and the rank rule
+ * is the FP64 comparison (its threshold eps^2 |R_11|^2 is formed in FP64 and
+ * rounded down to FP32, which decides every FP32 norm exactly as FP64
+ * would).  Outputs: rank_host[j];
  * piv + p_off[j] (m_j ints, device): the k_j skeleton columns first, in
  * pivot order; X + x_off[j] (device, k_j x (m_j - k_j), leading dimension
  * k_j, room for m_j * m_j / 4 + 1 elements): X = R1^-1 R2 for the
@@ -289,7 +296,8 @@ hssmf_status hssmf_gemm_f32(int transa, int transb, int m, int n, int k, float a
  *     T), or if a node is too large for the kernel's shared memory.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before
- *     any stream capture.
+ *     any stream capture.  The address is kept for the life of the process:
+ *     do not use this entry point after cudaDeviceReset on that device.
  *   - Every call shares the array: calls that overlap on the GPU (other
  *     streams, other host threads) race and must be serialized by the
  *     caller.  Nothing in the array needs clearing between calls.

@@ -111,6 +111,29 @@ def factor(A_natural, dims, opts: Options):
     return _factor_ordered(perm, fronts, Anew, opts, t0)
 
 
+def factor_subtree(A_natural, dims, opts: Options, depth):
+    """Factor only the fronts of one subtree of a grid's elimination tree:
+    the subtree of the front reached from the root by taking the first child
+    ``depth`` times.  Every front of it is factored exactly as in the whole
+    factorization (same ordering, update sets and random sketch); the other
+    fronts are left out (data None).  A bounded piece of the whole workload,
+    for timing the oracle.  Returns the partial factorization and the
+    subtree's front indices."""
+    t0 = time.perf_counter()
+    perm, fronts, Anew = ordering.analyze(dims, A_natural, opts.nd_leaf, opts.hss_leaf)
+    r = len(fronts) - 1
+    for _ in range(depth):
+        if not fronts[r].children:
+            break
+        r = fronts[r].children[0]
+    sub, stack = {r}, [r]
+    while stack:
+        for c in fronts[stack.pop()].children:
+            sub.add(c)
+            stack.append(c)
+    return _factor_ordered(perm, fronts, Anew, opts, t0, only=sub), sorted(sub)
+
+
 def factor_csr(A_natural, opts: Options, perm=None, sep_ptr=None, parent=None):
     """Multifrontal factorization of a general pattern: algebraic nested
     dissection, or the caller's ordering and separator tree."""
@@ -119,7 +142,7 @@ def factor_csr(A_natural, opts: Options, perm=None, sep_ptr=None, parent=None):
     return _factor_ordered(perm, fronts, Anew, opts, t0)
 
 
-def _factor_ordered(perm, fronts, Anew, opts, t0):
+def _factor_ordered(perm, fronts, Anew, opts, t0, only=None):
     fz = Factorization()
     fz.perm, fz.fronts, fz.A = perm, fronts, Anew
     fz.data = [None] * len(fronts)
@@ -128,6 +151,8 @@ def _factor_ordered(perm, fronts, Anew, opts, t0):
         for c in f.children:
             pos[c] = ordering.child_positions(fronts, c)
     for i, f in enumerate(fronts):
+        if only is not None and i not in only:
+            continue
         if f.nf >= opts.hss_min_front:
             fz.data[i] = _factor_hss_front(fz, i, pos, opts)
         else:
@@ -238,6 +263,8 @@ def apply_inverse(fz, b, transpose=False):
     fronts = fz.fronts
     for i, f in enumerate(fronts):  # forward, bottom-up
         fx = fz.data[i]
+        if fx is None:  # a front left out of a partial factorization (factor_subtree)
+            continue
         s = slice(f.sep_begin, f.sep_end)
         if isinstance(fx, DenseFront):
             ys = y[s]
@@ -270,6 +297,8 @@ def apply_inverse(fz, b, transpose=False):
     x = y
     for i in reversed(range(len(fronts))):  # backward, top-down
         f, fx = fronts[i], fz.data[i]
+        if fx is None:
+            continue
         s = slice(f.sep_begin, f.sep_end)
         if isinstance(fx, DenseFront):
             ys = x[s]

@@ -138,6 +138,7 @@ class Solver:
         self._check(lib.hssmf_create(C.byref(self._h), C.byref(self.opts), s), ctx=False)
         self.n = 0
         self.nnz = 0
+        self.factorizations = 0  # factor() calls made (the autograd wrapper checks it)
 
     def _check(self, st, ctx=True):
         if st != OK:
@@ -197,6 +198,7 @@ class Solver:
 
     def factor(self, values):
         p, keep = _buf(values)
+        self.factorizations += 1  # counted even if it fails: the old factors are gone
         self._check(lib.hssmf_factor(self._h, p))
 
     def _solve(self, fn, B, X, nrhs, ldb):
@@ -255,13 +257,16 @@ class Solver:
                                            int(nrhs), int(self.n), C.c_void_p(out.data_ptr())))
         return out
 
-    ID_TRACE_FIELDS = ("front", "node", "round", "d", "m", "mc", "kr", "kc", "accepted")
+    ID_TRACE_FIELDS = ("front", "node", "round", "d", "m", "mc", "kr", "kc", "accepted", "kernel_r",
+                       "kernel_c")
 
     def get_id_trace(self):
         """Per-node ID records of the last profiled factorization, an
-        (records x 9) int array with columns ID_TRACE_FIELDS."""
+        (records x 11) int array with columns ID_TRACE_FIELDS (kernel codes:
+        100 * family + CTAs per ID; family 0 one CTA in L2, 1 shared memory,
+        2 registers, 3 L2 cluster)."""
         n = lib.hssmf_get_id_trace(self._h, None, 0)
-        buf = np.zeros((max(n, 0), 9), dtype=np.int32)
+        buf = np.zeros((max(n, 0), len(self.ID_TRACE_FIELDS)), dtype=np.int32)
         if n > 0:
             lib.hssmf_get_id_trace(self._h, _int_ptr(buf), n)
         return buf

@@ -42,12 +42,17 @@ class SparseSolve(torch.autograd.Function):
         solver.factor(vals)
         x = solver.solve(bc)
         ctx.solver = solver
+        ctx.factorization = solver.factorizations
         ctx.save_for_backward(x)
         return x
 
     @staticmethod
     def backward(ctx, gx):
         solver = ctx.solver
+        if solver.factorizations != ctx.factorization:
+            # the adjoint needs the factorization of the forward pass's A
+            raise RuntimeError("sparse_solve: the solver was factored again between forward and backward; "
+                               "use one solver per differentiated solve or call backward first")
         (x,) = ctx.saved_tensors
         lam = solver.solve_T(_colmajor(gx.detach()))
         gvals = None

@@ -703,16 +703,22 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         // (more CTAs per SM).  The L2-resident cluster kernels remain the
         // fallback where a cluster cannot be scheduled.
         std::vector<IdJob> tier[3], smem_tier[5];
+        std::vector<int> tier_ix[3], smem_ix[5];  // positions in ij, for the ID trace
         int tm[3] = {0, 0, 0}, td[3] = {0, 0, 0}, sm_m[5] = {0, 0, 0, 0, 0}, sm_d[5] = {0, 0, 0, 0, 0};
         std::map<int, std::vector<IdJob>> rr_tier;  // register-resident (FP32), by configuration
         std::map<int, std::pair<int, int>> rr_md;
-        for (const IdJob& j : ij) {
+        // kernel that ran each ID (ID trace): 100 * family + CTAs per job, family
+        // 0 = one CTA in L2, 1 = shared memory, 2 = registers, 3 = L2 cluster
+        std::vector<int> route(ij.size(), 0);
+        for (size_t ji = 0; ji < ij.size(); ++ji) {
+          const IdJob& j = ij[ji];
           // registers hold less than shared memory: the register-resident
           // kernel only where it needs no larger cluster
           const int rr = HssKern<T>::id_rr_config(j.d, j.m);
           const int cl_sm = HssKern<T>::id_smem_cluster_size(j.d, j.m);
           if (rr > 0 && (cl_sm == 0 || (rr & 31) <= cl_sm)) {
             rr_tier[rr].push_back(j);
+            route[ji] = 200 + (rr & 31);
             auto& md = rr_md[rr];
             md.first = std::max(md.first, j.m);
             md.second = std::max(md.second, j.d);
@@ -725,12 +731,16 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           if (w * (long long)sizeof(T) > kTinyIdBytes) {
             const int ti = cl == 1 ? 0 : cl == 2 ? 1 : cl == 4 ? 2 : cl == 8 ? 3 : 4;
             smem_tier[ti].push_back(j);
+            smem_ix[ti].push_back((int)ji);
+            route[ji] = 100 + cl;
             sm_m[ti] = std::max(sm_m[ti], j.m);
             sm_d[ti] = std::max(sm_d[ti], j.d);
             continue;
           }
           const int t = (w >= kClusterIdWork16 && j.m > 256) ? 2 : (w >= kClusterIdWork && j.m > 256) ? 1 : 0;
           tier[t].push_back(j);
+          tier_ix[t].push_back((int)ji);
+          route[ji] = t == 0 ? 1 : t == 1 ? 308 : 316;
           tm[t] = std::max(tm[t], j.m);
           td[t] = std::max(td[t], j.d);
         }
@@ -755,9 +765,12 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
           if (HssKern<T>::batched_id_smem(dj, (int)smem_tier[ti].size(), sm_m[ti], sm_d[ti], eps, rdiag, order,
                                           cl, X.s) < 0) {
-            for (const IdJob& j : smem_tier[ti]) {  // not schedulable: the L2-resident kernels
+            for (size_t q = 0; q < smem_tier[ti].size(); ++q) {  // not schedulable: the L2-resident kernels
+              const IdJob& j = smem_tier[ti][q];
               const int t = j.m > 256 ? 1 : 0;
               tier[t].push_back(j);
+              tier_ix[t].push_back(smem_ix[ti][q]);
+              route[smem_ix[ti][q]] = t == 0 ? 1 : 308;
               tm[t] = std::max(tm[t], j.m);
               td[t] = std::max(td[t], j.d);
             }
@@ -775,6 +788,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           if (HssKern<T>::batched_id_cluster(dj, (int)tier[t].size(), tm[t], td[t], eps, rdiag, order, X.s,
                                              t == 2 ? 16 : 8) < 0) {
             tier[0].insert(tier[0].end(), tier[t].begin(), tier[t].end());  // one CTA per job
+            for (int q : tier_ix[t]) route[q] = 1;
             tm[0] = std::max(tm[0], tm[t]);
             td[0] = std::max(td[0], td[t]);
           }
@@ -807,8 +821,9 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           const bool ok_r = kr <= d - p || kr == N.m || cap;
           const bool ok_c = kc <= d - p || kc == N.mc || cap;
           if (c.prof.on) {
-            const int rec[9] = {F.f, idn[i].t, F.rounds, d, N.m, N.mc, kr, kc, (int)(ok_r && ok_c)};
-            c.id_trace.insert(c.id_trace.end(), rec, rec + 9);
+            const int rec[kIdTraceFields] = {F.f, idn[i].t, F.rounds, d, N.m, N.mc, kr, kc, (int)(ok_r && ok_c),
+                                             route[2 * i], route[2 * i + 1]};
+            c.id_trace.insert(c.id_trace.end(), rec, rec + kIdTraceFields);
           }
           if (ok_r && ok_c) {
             N.done = true;

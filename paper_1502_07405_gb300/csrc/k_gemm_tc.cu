@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
 
   const int nk = (kend - kbeg + TC_K - 1) / TC_K;
   bool ok = true;
+  int issued = 0;  // K steps whose MMAs were issued and committed
   // the global loads of stage t + 1 are issued before stage t is split and
   // stored, so that they are in flight during its MMAs
   float xa[TC_CH][8], xb[TC_CH][8];
@@ -260,9 +261,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
       tile_fetch(A, a_sr, a_sk, jb.ta == 0, m0, M, kbeg + (t + 1) * TC_K, kend, ya);
       tile_fetch(B, b_sr, b_sk, jb.tb != 0, n0, N, kbeg + (t + 1) * TC_K, kend, yb);
     }
-    if (t >= TC_STAGES) ok = ok && mbar_wait(smem_u32(&s_bar[st]), ((t - TC_STAGES) >> 1) & 1);
-    tile_store(xa, jb.ta == 0, m0, M, na, sa);
-    tile_store(xb, jb.tb != 0, n0, N, nb, sb);
+    // stage st is free once the MMAs of step t - 2 completed; after a wait
+    // that ran out nothing more is stored or issued (drain rule below)
+    const bool free_ok = t < TC_STAGES || mbar_wait(smem_u32(&s_bar[st]), ((t - TC_STAGES) >> 1) & 1);
+    if (free_ok) {
+      tile_store(xa, jb.ta == 0, m0, M, na, sa);
+      tile_store(xb, jb.tb != 0, n0, N, nb, sb);
+    }
 #pragma unroll
     for (int q4 = 0; q4 < TC_CH; ++q4)
 #pragma unroll
@@ -271,7 +276,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
         xb[q4][j] = yb[q4][j];
       }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    if (!__syncthreads_and(free_ok)) {  // the same decision in every thread
+      ok = false;
+      break;
+    }
+    issued = t + 1;
     if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
@@ -287,9 +296,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
       mma_commit(smem_u32(&s_bar[st]));
     }
   }
-  // the last commit covers every MMA issued before it
-  if (nk > 0) ok = ok && mbar_wait(smem_u32(&s_bar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1);
+  // Drain rule: the last commit covers every MMA issued before it, so one
+  // wait on it (bounded) covers exactly the work that was issued; after a
+  // wait that ran out the loop stopped before storing or issuing more, the
+  // accumulator is not read, and ST_TIMEOUT is reported.
+  if (issued > 0 && !mbar_wait(smem_u32(&s_bar[(issued - 1) & 1]), ((issued - 1) >> 1) & 1)) ok = false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  ok = __syncthreads_and(ok);
   if (!ok && threadIdx.x == 0) set_status(status, ST_TIMEOUT);
 
   // epilogue: warp w reads lanes 32 (w % 4) .. +31 (rows), columns 64 (w / 4) .. +63
@@ -337,11 +350,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
 
 void gemm_tc(const GemmJob* jobs, const Tile* tiles, int ntiles, unsigned* status, cudaStream_t s) {
   if (ntiles <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    attr = true;
-  }
+  set_func_attr((const void*)k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   k_gemm_tc<<<ntiles, TC_THREADS, TC_SMEM, s>>>(jobs, tiles, status);
   count_launch();
 }

@@ -200,22 +200,39 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_gemm_tma(const TmaJob* __rest
   const uint32_t tmem = s_tmem;
   bool ok = true;
 
+  // Drain rule for bounded waits: the producer and the MMA issuer stop at
+  // their first wait that runs out and issue nothing more; the producer then
+  // waits (bounded) until its last load into every stage has landed, so no
+  // bulk copy is in flight when the CTA exits; the final commit covers only
+  // the MMAs that were issued.  A timeout is reported as ST_TIMEOUT and the
+  // accumulator is not read.
   if (threadIdx.x == 0) {  // producer
+    int loaded = 0;
     for (int t = 0; t < nk; ++t) {
       const int s = t % stages, round = t / stages;
-      if (round > 0) ok = ok && bar_wait(su32(&s_empty[s]), (round - 1) & 1);
+      if (round > 0 && !bar_wait(su32(&s_empty[s]), (round - 1) & 1)) {
+        ok = false;
+        break;
+      }
       const uint32_t fb = su32(&s_full[s]);
       bar_expect(fb, (unsigned)stage_bytes);
       const uint32_t base = su32(smem + (size_t)s * stage_bytes);
       const int k0 = (kt0 + t) * TT_K;
       for (int a = 0; a < na; ++a) tma_load3(base + a * TT_TERM_A, &jp->ta, k0, m0, a, fb);
       for (int b = 0; b < nb; ++b) tma_load3(base + na * TT_TERM_A + b * tb_bytes, &jp->tb, k0, n0, b, fb);
+      loaded = t + 1;
     }
+    if (!ok)  // the most recent load into each stage (consumed or not) has landed
+      for (int t = max(0, loaded - stages); t < loaded; ++t)
+        if (!bar_wait(su32(&s_full[t % stages]), (t / stages) & 1)) break;
   } else if (threadIdx.x == 32) {  // MMA issuer
     const uint32_t idesc = idesc_bf16(bn);
     for (int t = 0; t < nk; ++t) {
       const int s = t % stages, round = t / stages;
-      ok = ok && bar_wait(su32(&s_full[s]), round & 1);
+      if (!bar_wait(su32(&s_full[s]), round & 1)) {
+        ok = false;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t base = su32(smem + (size_t)s * stage_bytes);
 #pragma unroll
@@ -228,12 +245,13 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_gemm_tma(const TmaJob* __rest
           }
       commit(su32(&s_empty[s]));
     }
-    commit(su32(&s_done));  // covers every MMA issued before it
+    commit(su32(&s_done));  // covers every MMA issued before it (possibly none)
   }
   __syncwarp();
   if (nk > 0) ok = bar_wait(su32(&s_done), 0) && ok;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!ok) atomicOr(status, ST_TIMEOUT);
+  ok = __syncthreads_and(ok);
+  if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
 
   // epilogue: warp w holds rows 32 w .. 32 w + 31 of the tile
   const int i = 32 * warp + lane, gi = m0 + i;
@@ -423,11 +441,8 @@ int gemm_tma_batch(const std::vector<GemmJob>& gj, TmaScratch& mem, unsigned* st
   const Tile* dt = (const Tile*)mem.put(tiles.data(), sizeof(Tile) * tiles.size());
   const Tile* dr = rtiles.empty() ? nullptr : (const Tile*)mem.put(rtiles.data(), sizeof(Tile) * rtiles.size());
   if (!dsj || !dst || !dtj || !dt || (!rtiles.empty() && !dr)) return -1;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM_BUDGET + 1024);
-    attr = true;
-  }
+  if (!set_func_attr((const void*)k_gemm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM_BUDGET + 1024))
+    return -1;
   k_split3<<<(int)st.size(), 256, 0, s>>>(dsj, dst);
   count_launch();
   k_gemm_tma<<<(int)tiles.size(), TT_THREADS, smem, s>>>(dtj, dt, stages, status);

@@ -445,9 +445,11 @@ void HssKern<T>::extract(const DevSym& ds, const double* values, const T* arena,
 // ---------------------------------------------------------------------------
 // Interpolative decomposition by column-pivoted Householder QR (Section 2.2;
 // rank rule of Section 5.3).  One CTA per job.  Y (d x m) is copied to W;
-// column norms (FP64) are recomputed from the trailing rows after every
-// step; the pivot is the first column of largest norm; the rank is the first
-// i with |R_{i+1,i+1}| <= eps |R_11|.  Then X = R1^-1 R2 by back
+// column norms (sums in T: FP64 for the FP64 form, FP32 for the FP32 form)
+// are recomputed from the trailing rows after every step; the pivot is the
+// first column of largest norm; the rank is the first i with
+// |R_{i+1,i+1}| <= eps |R_11| (in the FP32 form compared against a
+// threshold formed in FP64, id_threshold).  Then X = R1^-1 R2 by back
 // substitution, one warp per column.
 // ---------------------------------------------------------------------------
 // Threads per CTA (measured on GB300): 512 with two CTAs per SM for the
@@ -579,11 +581,7 @@ int HssKern<T>::batched_id(const IdJob* jobs, int njobs, int max_m, int max_d, d
   // m norms (double), d vector entries (double), m pivots (int)
   const size_t smem = 12 * (size_t)std::max(max_m, 1) + 8 * (size_t)std::max(max_d, 1);
   if (smem > 200 * 1024) return -1;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_cpqr_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  if (!set_func_attr((const void*)k_cpqr_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) return -1;
   k_cpqr_id<T><<<njobs, ID_THREADS, smem, s>>>(jobs, eps);
   count_launch();
   return 0;
@@ -774,13 +772,11 @@ static int launch_id_cluster(const IdJob* jobs, int njobs, int max_m, int max_d,
                              double* rdiag, int* order, cudaStream_t s) {
   const size_t smem = sizeof(double) * ((size_t)max_m / CL + 1 + (size_t)max_d) + (size_t)max_m + 16;
   if (smem > 200 * 1024) return -1;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_cpqr_id_cluster<T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (CL > 8) cudaFuncSetAttribute(k_cpqr_id_cluster<T, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaGetLastError();
-    attr = true;
-  }
+  if (!set_func_attr((const void*)k_cpqr_id_cluster<T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))
+    return -1;
+  if (CL > 8 && !set_func_attr((const void*)k_cpqr_id_cluster<T, CL>,
+                               cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
+    return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * CL, 1, 1);
   cfg.blockDim = dim3(IDC_THREADS, 1, 1);
@@ -1320,13 +1316,8 @@ static int launch_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, do
     kern = ovf ? k_cpqr_id_push<T, CL, true> : k_cpqr_id_push<T, CL, false>;
   else
     kern = ovf ? k_cpqr_id_smem<T, CL, true> : k_cpqr_id_smem<T, CL, false>;
-  static bool attr[2] = {false, false};
-  if (!attr[ovf]) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIdSmemBudget);
-    if (CL > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaGetLastError();
-    attr[ovf] = true;
-  }
+  if (!set_func_attr((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIdSmemBudget)) return -1;
+  if (CL > 8 && !set_func_attr((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * CL, 1, 1);
   cfg.blockDim = dim3(IDS_THREADS, 1, 1);
@@ -1665,12 +1656,9 @@ template <int RPL, int CPW, int CL>
 static int launch_id_rr(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
                         int* order, cudaStream_t s) {
   if (max_d > 32 * RPL || max_m > RR_NW * CPW * CL) return -1;
-  static bool attr = false;
-  if (!attr) {
-    if (CL > 8) cudaFuncSetAttribute(k_cpqr_id_rr<RPL, CPW, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaGetLastError();
-    attr = true;
-  }
+  if (CL > 8 && !set_func_attr((const void*)k_cpqr_id_rr<RPL, CPW, CL>,
+                               cudaFuncAttributeNonPortableClusterSizeAllowed, 1))
+    return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * CL, 1, 1);
   cfg.blockDim = dim3(RR_THREADS, 1, 1);
@@ -2140,11 +2128,8 @@ int HssKern<T>::ulv_fwd(const UlvFwdJob* jobs, int njobs, int max_nrhs, int max_
   if (njobs <= 0) return 0;
   const size_t smem = 2 * sizeof(T) * (size_t)std::max(max_m, 1);
   if (smem > kUlvSmemMax) return -1;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_ulv_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUlvSmemMax);
-    attr = true;
-  }
+  if (!set_func_attr((const void*)k_ulv_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUlvSmemMax))
+    return -1;
   k_ulv_fwd<T><<<dim3(njobs, std::min(std::max(max_nrhs, 1), 256)), ULV_THREADS, smem, s>>>(jobs);
   count_launch();
   return 0;
@@ -2225,11 +2210,8 @@ int HssKern<T>::ulv_bwd(const UlvBwdJob* jobs, int njobs, int max_nrhs, int max_
   if (njobs <= 0) return 0;
   const size_t smem = sizeof(T) * (size_t)std::max(max_m, 1);
   if (smem > kUlvSmemMax) return -1;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_ulv_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUlvSmemMax);
-    attr = true;
-  }
+  if (!set_func_attr((const void*)k_ulv_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUlvSmemMax))
+    return -1;
   k_ulv_bwd<T><<<dim3(njobs, std::min(std::max(max_nrhs, 1), 256)), ULV_THREADS, smem, s>>>(jobs);
   count_launch();
   return 0;

@@ -234,11 +234,7 @@ void Kern<T>::solve_fwd_dense(const DevSym& ds, const T* arena, const int* piv, 
                               const int* flist, int nfr, int max_nf, int nrhs, int transpose, cudaStream_t s) {
   if (nfr <= 0) return;
   if (warp_cols_fit<T>(max_nf, nrhs)) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_solve_fwd_dense_wc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpColSmem);
-      attr = true;
-    }
+    set_func_attr((const void*)k_solve_fwd_dense_wc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpColSmem);
     const size_t smem = (size_t)WC_WARPS * max_nf * sizeof(T);
     k_solve_fwd_dense_wc<T><<<dim3(nfr, (nrhs + WC_WARPS - 1) / WC_WARPS), 256, smem, s>>>(
         ds.fronts, arena, piv, W, flist, nrhs, max_nf, transpose);
@@ -400,11 +396,7 @@ void Kern<T>::solve_bwd_dense(const DevSym& ds, const T* arena, const int* piv, 
                               const int* flist, int nfr, int max_nf, int nrhs, int transpose, cudaStream_t s) {
   if (nfr <= 0) return;
   if (warp_cols_fit<T>(max_nf, nrhs)) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_solve_bwd_dense_wc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpColSmem);
-      attr = true;
-    }
+    set_func_attr((const void*)k_solve_bwd_dense_wc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpColSmem);
     const size_t smem = (size_t)WC_WARPS * max_nf * sizeof(T);
     k_solve_bwd_dense_wc<T><<<dim3(nfr, (nrhs + WC_WARPS - 1) / WC_WARPS), 256, smem, s>>>(
         ds.fronts, arena, piv, W, xp, flist, ds.n, nrhs, max_nf, transpose);

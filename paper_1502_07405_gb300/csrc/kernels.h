@@ -19,6 +19,14 @@ inline void count_launch(int k = 1) {
   if (cudaPeekAtLastError() != cudaSuccess) g_launch_error.store(1, std::memory_order_relaxed);
 }
 
+// Kernel attributes (the dynamic shared-memory limit, non-portable cluster
+// sizes) belong to a device, not to the process: each (device, kernel,
+// attribute, value) is set once on the current device, under a lock so that
+// host threads do not race.  Returns false if the runtime refuses it (the
+// error state is cleared: a launch that needed the attribute is then rejected
+// and caught by count_launch, or the caller falls back).
+bool set_func_attr(const void* func, cudaFuncAttribute attr, int value);
+
 // Per-front table uploaded once after analyze (all offsets in elements).
 struct DFront {
   long long off;       // front storage F (nf x nf, T) in the factor arena (dense fronts)

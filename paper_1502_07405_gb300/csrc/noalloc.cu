@@ -30,7 +30,10 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of g_id_scratch on the current device (looked up once per
-// device; the host-side symbol itself is not a device address).
+// device; the host-side symbol itself is not a device address).  The cached
+// address assumes the device is not reset while the library is loaded: after
+// cudaDeviceReset the module is loaded again, possibly elsewhere, and this
+// entry point must not be used in that process any more.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -86,9 +89,12 @@ hssmf_status run(int njobs, const void* Y, const long long* y_off, const int* m,
     return HSSMF_ERR_CUDA;
   }
   if (HssKern<T>::batched_id(djobs, njobs, max_m, max_d, eps, s) < 0) return HSSMF_ERR_ARG;
-  if (cudaMemcpyAsync(rank_host, ranks, sizeof(int) * njobs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-    return HSSMF_ERR_CUDA;
+  // every step runs, and the error state is always read (and cleared), so a
+  // failure here is not left behind for the caller's next CUDA call
+  const cudaError_t e1 = cudaMemcpyAsync(rank_host, ranks, sizeof(int) * njobs, cudaMemcpyDeviceToHost, s);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  const cudaError_t e3 = cudaGetLastError();
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return HSSMF_ERR_CUDA;
   return HSSMF_OK;
 }
 

@@ -11,7 +11,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -25,6 +28,25 @@
 namespace hssmf {
 std::atomic<long long> g_launches{0};
 std::atomic<int> g_launch_error{0};
+
+bool set_func_attr(const void* func, cudaFuncAttribute attr, int value) {
+  static std::mutex mu;
+  static std::set<std::tuple<int, const void*, int, int>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const auto key = std::make_tuple(dev, func, (int)attr, value);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(key)) return true;
+  if (cudaFuncSetAttribute(func, attr, value) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  done.insert(key);
+  return true;
+}
 }
 
 using namespace hssmf;
@@ -1004,9 +1026,9 @@ hssmf_status hssmf_pattern_grad(hssmf_ctx* c, const double* lambda, const double
 
 int hssmf_get_id_trace(const hssmf_ctx* c, int* rec, int max_records) {
   if (!c) return -1;
-  const int n = (int)(c->id_trace.size() / 9);
+  const int n = (int)(c->id_trace.size() / kIdTraceFields);
   if (rec)
-    for (int i = 0; i < std::min(n, max_records) * 9; ++i) rec[i] = c->id_trace[i];
+    for (int i = 0; i < std::min(n, max_records) * kIdTraceFields; ++i) rec[i] = c->id_trace[i];
   return n;
 }
 

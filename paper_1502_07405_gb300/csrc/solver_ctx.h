@@ -26,6 +26,8 @@ struct LevelPlan {
 
 struct HssState;  // HSS-front factor data (hss.cu)
 
+constexpr int kIdTraceFields = 11;  // ints per record of hssmf_get_id_trace
+
 enum Phase {
   PH_DENSE = 0, PH_SAMPLE, PH_EXTRACT, PH_PREID, PH_ID, PH_POSTID, PH_ULV, PH_SCHUR, PH_SOLVE,
   PH_OUTER, PH_IDK, PH_COUNT  // PH_IDK: the ID kernels alone (PH_ID keeps the rest of that step)
@@ -150,7 +152,7 @@ struct hssmf_ctx {
   hssmf::HssState* hss = nullptr;
   hssmf::PhaseProf prof;
   // per-node ID records of the last factor (profiling on): front, node, round,
-  // d, m, mc, kr, kc, accepted
+  // d, m, mc, kr, kc, accepted, kernel of the row ID, kernel of the column ID
   std::vector<int> id_trace;
 
   hssmf_status fail(hssmf_status st, const std::string& msg);

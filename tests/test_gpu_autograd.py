@@ -94,3 +94,23 @@ def test_adjoint_identity_hss_24cubed():
     # dL/dA on the pattern is -lambda_i x_j
     rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
     np.testing.assert_allclose(gv, -gb[rows] * x[A.colind], rtol=1e-12, atol=1e-14)
+
+
+def test_backward_after_refactor_raises():
+    """The adjoint solve needs the factorization of the forward pass: if the
+    same solver is factored again before backward, backward refuses instead
+    of returning gradients of another matrix."""
+    from paper_1502_07405_gb300.autograd import sparse_solve
+    side = 8
+    A, b, xt = _problem(side, 41)
+    s = _solver(A, side, hss_min_front=1 << 30)
+    vals = torch.tensor(A.values, device="cuda", requires_grad=True)
+    bt = torch.tensor(b, device="cuda", requires_grad=True)
+    loss = (sparse_solve(s, vals, bt) ** 2).sum()
+    s.factor(torch.tensor(2.0 * A.values, device="cuda"))
+    with pytest.raises(RuntimeError, match="factored again"):
+        loss.backward()
+    # a fresh forward pass on the current factorization differentiates normally
+    vals2 = torch.tensor(A.values, device="cuda", requires_grad=True)
+    (sparse_solve(s, vals2, bt) ** 2).sum().backward()
+    assert torch.isfinite(vals2.grad).all()

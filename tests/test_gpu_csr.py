@@ -99,3 +99,47 @@ def test_caller_ordering_equals_the_grid_analysis():
     c.factor(A.values)
     xc = c.solve(b)
     assert np.array_equal(xg, xc)
+
+
+def test_algebraic_order_fp64_takes_the_oracles_decisions_at_inexact_eps():
+    """eps = 1e-4 (inexact: one application leaves a residual ~5e-4) on a
+    nonsymmetric geometric operator ordered by the algebraic nested
+    dissection: the FP64 form takes the oracle's decisions (factor_csr, same
+    ordering and seed) front by front and node by node, so one application
+    equals the oracle's to rounding; the FP32 form stays within 10x of the
+    oracle's residual."""
+    from oracle import multifrontal as mf
+    import paper_1502_07405_gb300 as P
+    A, M = _geometric_operator(4000, 0.085, 3, nonsym=True)
+    b = problems.rhs_uniform(A.n, 1, 1)
+    fo = mf.factor_csr(A.to_scipy(), mf.Options(hss_tol=1e-4, **KW))
+    xo = mf.apply_inverse(fo, b)
+    ro = np.linalg.norm(b[:, 0] - M @ xo[:, 0]) / np.linalg.norm(b)
+    assert ro > 1e-6
+    stats_o = mf.hss_stats(fo)
+    s = _solver(hss_tol=1e-4, maxit=0, precision=0, **KW)
+    s.set_profiling(True)
+    s.analyze_csr(A.rowptr, A.colind)
+    s.factor(A.values)
+    st = s.get_stats()
+    assert st["n_hss_fronts"] == len(stats_o)
+    assert st["max_rank"] == max(r for _, _, r, _, _ in stats_o)
+    assert st["adaptive_rounds"] == sum(rr - 1 for _, _, _, _, rr in stats_o)
+    F = P.Solver.ID_TRACE_FIELDS
+    acc = {}
+    for r in s.get_id_trace():
+        rec = dict(zip(F, r))
+        if rec["accepted"]:
+            acc.setdefault(rec["front"], []).append((rec["kr"], rec["kc"]))
+    for i, *_ in stats_o:
+        H = fo.data[i].H
+        want = sorted((H.kr[t], H.kc[t]) for t in range(H.tree.n_nodes) if t != H.tree.root)
+        assert sorted(acc[i]) == want, i
+    x = s.solve(b)
+    assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
+    s32 = _solver(hss_tol=1e-4, maxit=0, precision=1, **KW)
+    s32.analyze_csr(A.rowptr, A.colind)
+    s32.factor(A.values)
+    x32 = s32.solve(b)
+    r32 = np.linalg.norm(b[:, 0] - M @ x32[:, 0]) / np.linalg.norm(b)
+    assert r32 <= 10.0 * ro, (r32, ro)

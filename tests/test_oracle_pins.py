@@ -551,3 +551,71 @@ def test_caller_tree_is_validated_by_the_oracle():
         ordering.analyze_csr(M, perm=ident, sep_ptr=[0, 16, 32, 48, n], parent=[3, 3, 3, -1])
     perm, fronts, _ = ordering.analyze_csr(M, perm=ident, sep_ptr=[0, n], parent=[-1])
     assert len(fronts) == 1 and fronts[0].nu == 0
+
+
+def _path_pattern(n):
+    rows = np.concatenate([np.arange(n - 1), np.arange(1, n), np.arange(n)])
+    cols = np.concatenate([np.arange(1, n), np.arange(n - 1), np.arange(n)])
+    return sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+
+
+def _fronts_as_lists(perm, fronts):
+    """(separator vertices in natural numbering, children) per front."""
+    return [(perm[f.sep_begin:f.sep_end].tolist(), list(f.children)) for f in fronts]
+
+
+def test_algebraic_nd_path_of_40_worked_by_hand():
+    """Path 0-1-...-39, leaves of at most 16 vertices (nd_leaf 4).  Worked by
+    hand from the level-structure rule: the first search from vertex 0 ends
+    at 39; the second search from 39 gives level(v) = 39 - v; levels 0..19
+    hold 20 vertices and adding level 20 would pass half of 40, so level 20
+    (vertex 19) is the separator, the near side is 39..20 (search order) and
+    the far side 18..0.  The near side (20 vertices): searches from 39 then
+    from 20, level(v) = v - 20, cumulative count passes 10 at level 10:
+    separator 30, near 20..29, far 31..39 (leaves).  The far side (19
+    vertices): level(v) = v from 0, passes 9.5 at level 9: separator 9, near
+    0..8, far 10..18.  Postorder: near subtree, far subtree, separator."""
+    perm, fronts, _ = ordering.analyze_csr(_path_pattern(40), nd_leaf=4, hss_leaf=8)
+    want = [
+        (list(range(20, 30)), []),
+        (list(range(31, 40)), []),
+        ([30], [0, 1]),
+        (list(range(0, 9)), []),
+        (list(range(10, 19)), []),
+        ([9], [3, 4]),
+        ([19], [2, 5]),
+    ]
+    assert _fronts_as_lists(perm, fronts) == want
+    assert [f.parent for f in fronts] == [2, 2, 6, 5, 5, 6, -1]
+    # I^upd in the new numbering: vertex 30 is new index 19, 9 is 38, 19 is 39
+    assert [f.upd.tolist() for f in fronts] == [[19, 39], [19], [39], [38], [38, 39], [39], []]
+
+
+def test_algebraic_nd_star_worked_by_hand():
+    """Star: centre 0 joined to 1..40 (leaves of at most 16).  The second
+    search starts at 40: level 0 = {40}, level 1 = {0}, level 2 = 1..39; the
+    depth is 2, so the separator is level 1 (the centre), the near side {40}
+    and the far side 1..39, which is disconnected.  A disconnected set splits
+    its components (all single vertices, taken in order) between two groups,
+    each to the group with fewer vertices so far (the first on a tie): odd
+    vertices 1..39 and even vertices 2..38; the last vertex of the second
+    group (38) is the separator.  The odd group (20 > 16) splits again into
+    1, 5, ..., 37 and 3, 7, ..., 39 with separator 39; the even group without
+    38 (18 > 16) into 2, 6, ..., 34 and 4, 8, ..., 36 with separator 36."""
+    n = 41
+    rows = np.concatenate([np.zeros(40, dtype=int), np.arange(1, 41), np.arange(n)])
+    cols = np.concatenate([np.arange(1, 41), np.zeros(40, dtype=int), np.arange(n)])
+    M = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+    perm, fronts, _ = ordering.analyze_csr(M, nd_leaf=4, hss_leaf=8)
+    want = [
+        ([40], []),
+        (list(range(1, 38, 4)), []),
+        (list(range(3, 36, 4)), []),
+        ([39], [1, 2]),
+        (list(range(2, 35, 4)), []),
+        (list(range(4, 33, 4)), []),
+        ([36], [4, 5]),
+        ([38], [3, 6]),
+        ([0], [0, 7]),
+    ]
+    assert _fronts_as_lists(perm, fronts) == want

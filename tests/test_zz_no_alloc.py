@@ -77,3 +77,28 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
                                         lp(ranks), C.c_void_p(piv.data_ptr()), lp(z),
                                         C.c_void_p(X.data_ptr()), lp(z), None)
     assert st == P.ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_allocates_no_device_memory(prec):
+    """Free device memory is the same before and after each call: the entry
+    point uses only its fixed array (the first call on the device, which may
+    load the library's device image, is made before measuring)."""
+    import paper_1502_07405_gb300 as P
+    dt = torch.float64 if prec == 0 else torch.float32
+    Yd, m, d, y_off, p_off, x_off = _inputs(3, [(256, 200), (128, 96), (320, 64)], dt)
+    piv = torch.full((int(m.sum()),), -1, dtype=torch.int32, device="cuda")
+    X = torch.zeros(int(sum(mm * mm // 4 + 1 for mm in m)), dtype=dt, device="cuda")
+    ranks = np.zeros(len(m), dtype=np.int32)
+    lp = lambda a: a.ctypes.data_as(C.c_void_p)
+    fn = P.lib.hssmf_batched_id_noalloc
+    fn.restype = C.c_int
+    call = lambda: fn(prec, len(m), C.c_void_p(Yd.data_ptr()), lp(y_off), lp(m), lp(d), C.c_double(1e-4),
+                      lp(ranks), C.c_void_p(piv.data_ptr()), lp(p_off), C.c_void_p(X.data_ptr()), lp(x_off), None)
+    assert call() == 0  # set-up call
+    torch.cuda.synchronize()
+    for _ in range(3):
+        free0 = torch.cuda.mem_get_info()[0]
+        assert call() == 0
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
