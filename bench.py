@@ -38,7 +38,6 @@ WORKLOAD = dict(dims=(64, 64, 64), hss_min_front=1024, hss_tol=1e-4, d0=128, dd=
                 rhs_seed=1, nrhs=1)
 WORKLOAD_NAME = ("3D 7-point Poisson 64^3 (n=262144), geometric ND (8^3 leaves), HSS on fronts >= 1024, "
                  "eps=1e-4, d0=128, dd=64, 1 RHS U[-1,1] seed 1, GMRES(30) to rel. residual 1e-10")
-CPU_SAMPLE_SIDE = 32  # oracle sample: the same problem family on a 32^3 grid
 # --config grf100: the 100^3 anisotropic variable-coefficient diffusion (kappa =
 # exp(Gaussian random field, correlation length 8 cells, sigma 1), anisotropy
 # 1:1:10, harmonic-mean faces), HSS on fronts >= 2048; 1 and 64 RHS.  At eps
@@ -396,39 +395,11 @@ def run_ours(args):
         line["systems_per_s"] = round(ws / (ms * 1e-3), 4)
     if rank == 0:
         if ws == 1 and not args.no_cpu and not WORKLOAD.get("grf") and not WORKLOAD.get("batch"):
-            line["cpu_baseline"] = cpu_baseline(st["factor_flops"])
+            line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-
-
-def _oracle_step(side):
-    """Oracle factor + GMRES on a side^3 grid with the workload's settings."""
-    import problems
-    from oracle import krylov, multifrontal as mf
-    dims = (side,) * 3
-    A = problems.grid_poisson(dims).to_scipy()
-    b = problems.rhs_uniform(A.shape[0], 1, WORKLOAD["rhs_seed"])[:, 0]
-    t0 = time.perf_counter()
-    fz = mf.factor(A, dims, mf.Options(hss_tol=WORKLOAD["hss_tol"], d0=WORKLOAD["d0"], dd=WORKLOAD["dd"],
-                                        hss_min_front=WORKLOAD["hss_min_front"], seed=WORKLOAD["seed"]))
-    x, its, rel = krylov.gmres(A, lambda v: mf.apply_inverse(fz, v), b, rtol=1e-10)
-    return time.perf_counter() - t0, rel
-
-
-def _flops_at(side):
-    """Library factor flops on a side^3 grid (same settings), for scaling."""
-    import paper_1502_07405_gb300 as P
-    import problems
-    A = problems.grid_poisson((side,) * 3)
-    s = P.Solver(P.Options.defaults(hss_min_front=WORKLOAD["hss_min_front"], hss_tol=WORKLOAD["hss_tol"],
-                                    d0=WORKLOAD["d0"], dd=WORKLOAD["dd"], maxit=0))
-    s.analyze_grid((side,) * 3, A.rowptr, A.colind)
-    s.factor(A.values)
-    f = s.get_stats()["factor_flops"]
-    s.close()
-    return f
 
 
 def _cores():
@@ -438,46 +409,97 @@ def _cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(full_flops):
-    t, rel = _oracle_step(CPU_SAMPLE_SIDE)
-    f_sample = _flops_at(CPU_SAMPLE_SIDE)
-    scale = full_flops / f_sample if f_sample > 0 else float("nan")
-    return {"value": round(t * 1e3 * scale, 1), "unit": "ms", "cores": _cores(), "kind": "oracle",
-            "sample": (f"oracle (numpy FP64) factor + GMRES on the 32^3 grid with the same settings "
-                       f"({t:.1f} s, rel. residual {rel:.1e}), scaled to 64^3 by the library's factor-flop "
-                       f"ratio {scale:.1f}"),
-            "sample_seconds": round(t, 2)}
+def _blas_threads():
+    """Threads the oracle's BLAS uses in this process (the environment's
+    limit, else every core)."""
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        v = os.environ.get(k)
+        if v and v.isdigit():
+            return int(v)
+    return _cores()
+
+
+def _calibration():
+    path = os.path.join(ROOT, "oracle", "poisson64_calibration.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return None
+
+
+def _sample_subprocess(threads, depth=None):
+    """One oracle sample step in a child process whose BLAS uses ``threads``
+    threads (the limit must be set before numpy loads); returns seconds."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads))
+    code = ("import json, sys; sys.path.insert(0, %r); from oracle import bench_sample as S; "
+            "print(json.dumps(S.sample_step(%s)))" % (ROOT, "" if depth is None else int(depth)))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])[0]
+
+
+def _sample_text(cal, t_ms, extra=""):
+    from oracle import bench_sample as S
+    if cal is None:
+        return (f"oracle (numpy FP64) on the depth-{S.SAMPLE_DEPTH} subtree of the 64^3 elimination tree "
+                f"({t_ms:.0f} ms); no calibration record, so value is the unscaled sample time")
+    return (f"oracle (numpy FP64) factorization of the depth-{cal['sample_depth']} subtree of the 64^3 "
+            f"elimination tree ({cal['sample_fronts']} fronts, {cal['sample_hss_fronts']} HSS) plus one "
+            f"solve sweep over it: {t_ms:.0f} ms{extra}; scaled by {cal['ratio']:.1f} = whole oracle run "
+            f"({cal['full_s']:.0f} s: factor + {cal['iterations']} GMRES iterations, rel. residual "
+            f"{cal['relres']:.1e}) / the same sample ({cal['sample_s']:.1f} s), both measured back to back on "
+            f"{cal['machine']['machine']} x{cal['machine']['cpus']} "
+            f"(oracle/poisson64_calibration.json, written by oracle/bench_sample.py)")
+
+
+def cpu_baseline():
+    """The oracle on a bounded sample of the same workload (all cores, then
+    one thread), scaled to the whole factor + GMRES by the calibration."""
+    cal = _calibration()
+    n = _cores()
+    t_all = sorted(_sample_subprocess(n) for _ in range(2))[0]
+    t_one = _sample_subprocess(1)
+    scale = cal["ratio"] if cal else 1.0
+    return {"value": round(t_all * 1e3 * scale, 1), "unit": "ms", "cores": n, "kind": "oracle",
+            "sample": _sample_text(cal, t_all * 1e3, f" on {n} BLAS threads ({t_one * 1e3:.0f} ms on 1)"),
+            "sample_ms": round(t_all * 1e3, 1), "sample_ms_1thread": round(t_one * 1e3, 1),
+            "value_1thread": round(t_one * 1e3 * scale, 1), "scale": round(scale, 2) if cal else None}
 
 
 def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, each step one bounded
+    sample of the 64^3 workload (no GPU library is loaded)."""
     ws, rank, local = _dist()
     if rank != 0:
         return
-    # warm-up steps on a tiny grid (the oracle has no state to warm)
-    for _ in range(args.warmup):
-        _oracle_step(8)
-    full = None
-    try:
-        full = _flops_at(WORKLOAD["dims"][0])
-        f_sample = _flops_at(CPU_SAMPLE_SIDE)
-        scale = full / f_sample
-    except Exception as e:  # no GPU: report the unscaled sample time
-        scale, f_sample = 1.0, None
-    times = []
-    for _ in range(args.steps):
-        t, rel = _oracle_step(CPU_SAMPLE_SIDE)
-        times.append(t * 1e3 * scale)
-    times.sort()
-    ms = times[len(times) // 2]
-    line = {"impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": "ms", "n_gpus": ws,
+    import numpy as np
+    from oracle import bench_sample as S
+    cal = _calibration()
+    A, b = S._problem()
+    for _ in range(args.warmup):  # untimed: a leaf front of the same tree
+        S.sample_step(9, A, b)
+    times = [S.sample_step(S.SAMPLE_DEPTH, A, b)[0] * 1e3 for _ in range(args.steps)]
+    t_one = _sample_subprocess(1)
+    ms = float(np.median(times)) if times else float("nan")
+    scale = cal["ratio"] if cal else 1.0
+    value = ms * scale
+    threads = _blas_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "form": "CPU oracle (numpy FP64)"},
-            "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": _cores(), "kind": "oracle",
-                             "sample": (f"oracle factor + GMRES on the 32^3 grid, same settings, scaled to "
-                                        f"64^3 by the library's factor-flop ratio {scale:.1f}")},
-            "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOAD_NAME,
+                       "form": "CPU oracle (numpy FP64), one bounded sample of the workload per step",
+                       "l2": "no flush: CPU run", "parallelism": "1 process, BLAS threads"},
+            "value_note": ("value = projected time of the whole factor + solve (the metric); ms_per_step = the "
+                           "measured time of one sample step"),
+            "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": threads, "kind": "oracle",
+                             "sample": _sample_text(cal, ms, f" on {threads} BLAS threads (median of "
+                                                              f"{len(times)}; {t_one * 1e3:.0f} ms on 1)"),
+                             "sample_ms": round(ms, 1), "sample_ms_1thread": round(t_one * 1e3, 1),
+                             "value_1thread": round(t_one * 1e3 * scale, 1),
+                             "scale": round(scale, 2) if cal else None},
+            "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 

@@ -217,10 +217,19 @@ hssmf_status hssmf_pattern_grad(hssmf_ctx* ctx, const double* lambda, const doub
  * row rank, column rank, 1 if both IDs were accepted, and the kernel that
  * ran the row ID and the column ID, coded 100 * family + CTAs per ID
  * (family 0: one CTA, matrix in L2; 1: matrix in shared memory; 2: matrix
- * in registers; 3: L2-resident cluster).  Copies at most
+ * in registers; 3: L2-resident cluster; 4: matrix in registers, one
+ * exchange of proposals per pivot step).  Copies at most
  * max_records records into rec (host, may be NULL) and returns the number
  * available, or -1 for a NULL context. */
 int hssmf_get_id_trace(const hssmf_ctx* ctx, int* rec, int max_records);
+
+/* One record per ID kernel launch of the last factorization run with
+ * profiling on (the paper has no counterpart; a profiling aid): 6 doubles --
+ * kernel code (as in hssmf_get_id_trace), CTAs per ID, IDs in the launch,
+ * largest d, largest m, device time in ms (CUDA events around the launch).
+ * Copies at most max_records records into rec (host, may be NULL) and
+ * returns the number available, or -1 for a NULL context. */
+int hssmf_get_id_launch_trace(const hssmf_ctx* ctx, double* rec, int max_records);
 
 /* Kernel-level entry point: a batch of interpolative decompositions
  * (Section 2.2, ID definitions; rank rule of Section 5.3).  Job j selects
@@ -246,7 +255,11 @@ int hssmf_get_id_trace(const hssmf_ctx* ctx, int* rec, int max_records);
  * 1..16 CTAs sized for the largest job (past 16 CTAs the columns that do not
  * fit stay in global memory);
  * use_cluster = -100 - c (c = 2, 4, 8, 16) runs the shared-memory kernel on
- * clusters of c CTAs whatever the size; use_cluster = -2 (prec 1 only) keeps
+ * clusters of c CTAs whatever the size; use_cluster = -3 (prec 1 only) keeps
+ * every matrix in the registers of a cluster of 1..16 CTAs of 256 threads
+ * with one exchange of proposals per pivot step (d <= 832; m up to 2048,
+ * 1280 or 896 for d <= 256, 512, 832), else HSSMF_ERR_ARG;
+ * use_cluster = -2 (prec 1 only) keeps
  * every matrix in the registers of a
  * cluster of 1..16 CTAs, for d <= 512 and m <= 2048 (d <= 256) or m <= 1024
  * (d <= 512), else HSSMF_ERR_ARG.
@@ -255,6 +268,16 @@ hssmf_status hssmf_batched_id(int prec, int njobs, const void* Y, const long lon
                               const int* m, const int* d, double eps, int* rank_host, int* piv,
                               const long long* p_off, void* X, const long long* x_off,
                               int use_cluster, void* cuda_stream);
+
+/* Test of the failure path of the bounded waits (the paper has no
+ * counterpart): one FP32 ID on the register-resident cluster kernel with
+ * cl CTAs (2, 4, 8 or 16) in which CTA 0 withholds its first proposal, so
+ * that every wait of the cluster runs out after spin polls.  The kernel
+ * then stops, meets its cluster barriers and reports rank -1; the call
+ * returns HSSMF_ERR_TIMEOUT (HSSMF_OK would mean the wait did not run out),
+ * HSSMF_ERR_ARG for invalid arguments.  Allocates and frees its own small
+ * device buffers; synchronizes the device. */
+hssmf_status hssmf_id_timeout_test(int cl, int spin);
 
 /* Kernel-level entry point: the FP32 GEMM of the FP32 factorization,
  * C = alpha op(A) op(B) + beta C with op(A) m x k and op(B) k x n

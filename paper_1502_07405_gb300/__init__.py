@@ -88,6 +88,8 @@ lib.hssmf_get_id_trace.argtypes = [_P, _IP, _I]
 lib.hssmf_pattern_grad.argtypes = [_P, _P, _P, _I, _I, _P]
 lib.hssmf_pattern_grad.restype = C.c_int
 lib.hssmf_get_id_trace.restype = C.c_int
+lib.hssmf_get_id_launch_trace.argtypes = [_P, C.POINTER(C.c_double), _I]
+lib.hssmf_get_id_launch_trace.restype = C.c_int
 lib.hssmf_last_error.argtypes = [_P]
 lib.hssmf_last_error.restype = C.c_char_p
 lib.hssmf_destroy.argtypes = [_P]
@@ -264,11 +266,23 @@ class Solver:
         """Per-node ID records of the last profiled factorization, an
         (records x 11) int array with columns ID_TRACE_FIELDS (kernel codes:
         100 * family + CTAs per ID; family 0 one CTA in L2, 1 shared memory,
-        2 registers, 3 L2 cluster)."""
+        2 registers, 3 L2 cluster, 4 registers with one exchange per step)."""
         n = lib.hssmf_get_id_trace(self._h, None, 0)
         buf = np.zeros((max(n, 0), len(self.ID_TRACE_FIELDS)), dtype=np.int32)
         if n > 0:
             lib.hssmf_get_id_trace(self._h, _int_ptr(buf), n)
+        return buf
+
+    ID_LAUNCH_FIELDS = ("kernel", "ctas", "jobs", "max_d", "max_m", "ms")
+
+    def get_id_launch_trace(self):
+        """Per-launch records of the ID kernels of the last profiled
+        factorization, a (launches x 6) float array with columns
+        ID_LAUNCH_FIELDS."""
+        n = lib.hssmf_get_id_launch_trace(self._h, None, 0)
+        buf = np.zeros((max(n, 0), 6), dtype=np.float64)
+        if n > 0:
+            lib.hssmf_get_id_launch_trace(self._h, buf.ctypes.data_as(C.POINTER(C.c_double)), n)
         return buf
 
     def get_symbolic(self, n_fronts):

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhssmf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["analyze.cpp", "k_dense.cu", "k_solve.cu", "k_hss.cu", "k_gemm_tc.cu", "k_gemm_tma.cu", "hss.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["analyze.cpp", "k_dense.cu", "k_solve.cu", "k_hss.cu", "k_id_rx.cu", "k_gemm_tc.cu", "k_gemm_tma.cu", "hss.cu", "solver.cu", "noalloc.cu"]
 
 
 def _nvcc():

@@ -708,9 +708,10 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         std::map<int, std::vector<IdJob>> rr_tier;  // register-resident (FP32), by configuration
         std::map<int, std::pair<int, int>> rr_md;
         // kernel that ran each ID (ID trace): 100 * family + CTAs per job, family
-        // 0 = one CTA in L2, 1 = shared memory, 2 = registers, 3 = L2 cluster
+        // 0 = one CTA in L2, 1 = shared memory, 2 = registers, 3 = L2 cluster,
+        // 4 = registers with one exchange per pivot step
         std::vector<int> route(ij.size(), 0);
-        for (size_t ji = 0; ji < ij.size(); ++ji) {
+        auto route_old = [&](size_t ji) {
           const IdJob& j = ij[ji];
           // registers hold less than shared memory: the register-resident
           // kernel only where it needs no larger cluster
@@ -722,7 +723,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
             auto& md = rr_md[rr];
             md.first = std::max(md.first, j.m);
             md.second = std::max(md.second, j.d);
-            continue;
+            return;
           }
           // shared-memory kernel on the smallest cluster that holds the
           // matrix; past 16 CTAs the overflow columns stay in global memory
@@ -735,7 +736,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
             route[ji] = 100 + cl;
             sm_m[ti] = std::max(sm_m[ti], j.m);
             sm_d[ti] = std::max(sm_d[ti], j.d);
-            continue;
+            return;
           }
           const int t = (w >= kClusterIdWork16 && j.m > 256) ? 2 : (w >= kClusterIdWork && j.m > 256) ? 1 : 0;
           tier[t].push_back(j);
@@ -743,15 +744,73 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           route[ji] = t == 0 ? 1 : t == 1 ? 308 : 316;
           tm[t] = std::max(tm[t], j.m);
           td[t] = std::max(td[t], j.d);
+        };
+        // FP32 nodes that need a cluster go to the register-resident kernel
+        // with one exchange per pivot step where they fit (family 4 in the
+        // trace); the others, and any batch that cannot be scheduled, to the
+        // kernels above
+        std::map<int, std::vector<IdJob>> rx_tier;
+        std::map<int, std::vector<int>> rx_ix;
+        std::map<int, std::pair<int, int>> rx_md;
+        for (size_t ji = 0; ji < ij.size(); ++ji) {
+          const IdJob& j = ij[ji];
+          const int rx = std::is_same<T, float>::value ? id_rx_config(j.d, j.m) : 0;
+          if (rx > 0) {
+            const int rr = HssKern<T>::id_rr_config(j.d, j.m);
+            const int cl_sm = HssKern<T>::id_smem_cluster_size(j.d, j.m);
+            const bool old_single = (rr > 0 && (cl_sm == 0 || (rr & 31) <= cl_sm)) ? (rr & 31) == 1
+                                    : (long long)j.d * j.m * (long long)sizeof(T) > kTinyIdBytes ? cl_sm == 1
+                                                                                                 : true;
+            if (!old_single || (rx & 31) > 1) {
+              rx_tier[rx].push_back(j);
+              rx_ix[rx].push_back((int)ji);
+              route[ji] = 400 + (rx & 31);
+              auto& md = rx_md[rx];
+              md.first = std::max(md.first, j.m);
+              md.second = std::max(md.second, j.d);
+              continue;
+            }
+          }
+          route_old(ji);
         }
         c.prof.mark(PH_IDK, X.s);
+        // with profiling on, every ID launch is timed by its own events
+        auto timed = [&](int code, int cl, int nj, int dmax, int mmax, auto&& launch) -> int {
+          cudaEvent_t e0 = nullptr, e1 = nullptr;
+          const bool rec = c.prof.on && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+          if (rec) cudaEventRecord(e0, X.s);
+          const int r = launch();
+          if (rec) {
+            cudaEventRecord(e1, X.s);
+            c.id_ev.push_back({e0, e1});
+            const double desc[5] = {(double)code, (double)cl, (double)nj, (double)dmax, (double)mmax};
+            c.id_ev_desc.insert(c.id_ev_desc.end(), desc, desc + 5);
+          }
+          return r;
+        };
+        for (auto& kv : rx_tier) {
+          const int mm = rx_md[kv.first].first, dd = rx_md[kv.first].second;
+          double* rdiag = (double*)H.rnd.alloc(sizeof(double) * kv.second.size() * std::max(std::min(mm, dd), 1));
+          int* order = (int*)H.rnd.alloc(sizeof(int) * kv.second.size() * std::max(mm, 1));
+          const IdJob* dj = H.ring.put(kv.second, X.s);
+          if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
+          if (timed(400 + (kv.first & 31), kv.first & 31, (int)kv.second.size(), dd, mm, [&] {
+                return batched_id_rx(dj, (int)kv.second.size(), mm, dd, eps, rdiag, order, kv.first, X.s);
+              }) < 0) {
+            for (int q : rx_ix[kv.first]) route_old((size_t)q);  // not schedulable: the other kernels
+          } else {
+            ++c.id_launches;
+          }
+        }
         for (auto& kv : rr_tier) {
           const int mm = rr_md[kv.first].first, dd = rr_md[kv.first].second;
           double* rdiag = (double*)H.rnd.alloc(sizeof(double) * kv.second.size() * std::max(std::min(mm, dd), 1));
           int* order = (int*)H.rnd.alloc(sizeof(int) * kv.second.size() * std::max(mm, 1));
           const IdJob* dj = H.ring.put(kv.second, X.s);
           if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
-          if (HssKern<T>::batched_id_rr(dj, (int)kv.second.size(), mm, dd, eps, rdiag, order, kv.first, X.s) < 0)
+          if (timed(200 + (kv.first & 31), kv.first & 31, (int)kv.second.size(), dd, mm, [&] {
+                return HssKern<T>::batched_id_rr(dj, (int)kv.second.size(), mm, dd, eps, rdiag, order, kv.first, X.s);
+              }) < 0)
             return c.fail(HSSMF_ERR_CUDA, "register-resident ID launch failed");
           ++c.id_launches;
         }
@@ -763,8 +822,10 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           int* order = (int*)H.rnd.alloc(sizeof(int) * smem_tier[ti].size() * std::max(sm_m[ti], 1));
           const IdJob* dj = H.ring.put(smem_tier[ti], X.s);
           if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
-          if (HssKern<T>::batched_id_smem(dj, (int)smem_tier[ti].size(), sm_m[ti], sm_d[ti], eps, rdiag, order,
-                                          cl, X.s) < 0) {
+          if (timed(100 + cl, cl, (int)smem_tier[ti].size(), sm_d[ti], sm_m[ti], [&] {
+                return HssKern<T>::batched_id_smem(dj, (int)smem_tier[ti].size(), sm_m[ti], sm_d[ti], eps, rdiag,
+                                                   order, cl, X.s);
+              }) < 0) {
             for (size_t q = 0; q < smem_tier[ti].size(); ++q) {  // not schedulable: the L2-resident kernels
               const IdJob& j = smem_tier[ti][q];
               const int t = j.m > 256 ? 1 : 0;
@@ -785,8 +846,10 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           int* order = (int*)H.rnd.alloc(sizeof(int) * tier[t].size() * std::max(tm[t], 1));
           const IdJob* dj = H.ring.put(tier[t], X.s);
           if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
-          if (HssKern<T>::batched_id_cluster(dj, (int)tier[t].size(), tm[t], td[t], eps, rdiag, order, X.s,
-                                             t == 2 ? 16 : 8) < 0) {
+          if (timed(t == 2 ? 316 : 308, t == 2 ? 16 : 8, (int)tier[t].size(), td[t], tm[t], [&] {
+                return HssKern<T>::batched_id_cluster(dj, (int)tier[t].size(), tm[t], td[t], eps, rdiag, order, X.s,
+                                                      t == 2 ? 16 : 8);
+              }) < 0) {
             tier[0].insert(tier[0].end(), tier[t].begin(), tier[t].end());  // one CTA per job
             for (int q : tier_ix[t]) route[q] = 1;
             tm[0] = std::max(tm[0], tm[t]);
@@ -796,7 +859,9 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         if (!tier[0].empty()) {
           const IdJob* dj = H.ring.put(tier[0], X.s);
           if (!dj) return c.fail(HSSMF_ERR_OOM, "job ring");
-          if (HssKern<T>::batched_id(dj, (int)tier[0].size(), tm[0], td[0], eps, X.s) < 0)
+          if (timed(1, 1, (int)tier[0].size(), td[0], tm[0], [&] {
+                return HssKern<T>::batched_id(dj, (int)tier[0].size(), tm[0], td[0], eps, X.s);
+              }) < 0)
             return c.fail(HSSMF_ERR_ARG, "an HSS node is too large for the ID kernel");
         }
         c.prof.mark(PH_ID, X.s);
@@ -806,6 +871,17 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         if ((st = c.cuda_check(cudaStreamSynchronize(X.s), "ID"))) return st;
         H.ring.off = 0;
         c.prof.resolve();
+        for (size_t q = 0; q < c.id_ev.size(); ++q) {  // the stream is synchronized: launch times are final
+          float ms = -1.f;
+          if (cudaEventElapsedTime(&ms, c.id_ev[q].first, c.id_ev[q].second) != cudaSuccess) cudaGetLastError();
+          c.id_launch_trace.insert(c.id_launch_trace.end(), c.id_ev_desc.begin() + 5 * q,
+                                   c.id_ev_desc.begin() + 5 * q + 5);
+          c.id_launch_trace.push_back(ms);
+          cudaEventDestroy(c.id_ev[q].first);
+          cudaEventDestroy(c.id_ev[q].second);
+        }
+        c.id_ev.clear();
+        c.id_ev_desc.clear();
         for (int t = 0; t < 3; ++t) c.id_launches += tier[t].empty() ? 0 : 1;
         for (size_t i = 0; i < idn.size(); ++i) {
           FrontRt& F = *idn[i].F;
@@ -1417,6 +1493,7 @@ void hss_begin_factor(hssmf_ctx& c) {
   c.id_launches = 0;
   c.id_bytes = c.id_flops = 0.0;
   c.id_trace.clear();
+  c.id_launch_trace.clear();
   c.hss_flops = c.hss_bytes = 0.0;
   if (!c.hss) return;
   c.hss->transposed_ready = false;

@@ -1,0 +1,522 @@
+// Interpolative decomposition of FP32 nodes (Section 2.2; rank rule of
+// Section 5.3) with the node's matrix held in registers across a
+// thread-block cluster and one exchange round per pivot step.
+//
+// Y (d x m) is factored by column-pivoted Householder QR: the pivot is the
+// first column of largest trailing norm, the norms are recomputed from the
+// trailing rows after every step, the rank k is the first i with
+// |R_{i+1,i+1}| <= eps |R_11| (FP64 threshold, rounded down to FP32, which
+// decides every FP32 norm exactly as FP64 would), and X = R1^-1 R2.
+//
+// Layout: CTA r of a cluster of CL owns the columns j = r (mod CL); its warp
+// w owns the local columns l = w + NW c (c < CPW) and lane t holds rows
+// t + 32 s (s < RPL) of each, so the Householder updates touch no memory.
+// One pivot step:
+//   1. every warp stages its best candidate column (largest trailing norm)
+//      in shared memory and posts its proposal;        -- CTA barrier
+//   2. every warp reduces the CTA's proposals; on a cluster, one thread
+//      writes the proposal (norm, column) behind the CTA's candidate and
+//      sends both to every CTA of the cluster with bulk asynchronous copies
+//      (shared::cta -> shared::cluster) that complete on the receiver's
+//      mbarrier through its transaction count;
+//   3. every thread waits (bounded) on its own mbarrier, reduces the CL
+//      proposals to the same decision and finds the pivot column already
+//      in its own shared memory;                         -- CTA barrier
+//   4. every warp applies the reflector to its columns in registers and
+//      recomputes their trailing norms.
+// One CTA runs the same steps without the copies (one barrier per step).
+// Staging and landing areas alternate with the step's parity: a CTA
+// rewrites its staging area two steps later, after its next wait, which
+// completes only when every peer has sent the next step's copy, which a
+// peer does only after this step's copy has landed in it.
+// A wait that runs out makes the whole CTA stop (the barrier after the wait
+// reduces the outcome); the kernel still meets every cluster barrier (no
+// CTA leaves while a peer may read its shared memory) and reports rank -1.
+// Then X = R1^-1 R2 by a blocked back substitution (32-row blocks of R1
+// read from W, 16 right-hand sides at a time in shared memory).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "hss_kernels.h"
+#include "id_common.cuh"
+
+namespace hssmf {
+namespace {
+
+constexpr int RX_THREADS = 256;
+constexpr int RX_NW = RX_THREADS / 32;
+constexpr int RX_SPIN = 1 << 22;  // polls of a bounded wait
+
+__device__ __forceinline__ uint32_t rx_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t rx_mapa(uint32_t a, int cta) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(cta));
+  return r;
+}
+__device__ __forceinline__ bool rx_wait(uint32_t bar, uint32_t parity, int spin) {
+  for (int it = 0; it < spin; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+template <int N>
+struct Pow2Ceil {
+  static constexpr int value = N <= 1 ? 1 : 2 * Pow2Ceil<(N + 1) / 2>::value;
+};
+template <>
+struct Pow2Ceil<1> {
+  static constexpr int value = 1;
+};
+template <int P>
+struct Log2 {
+  static constexpr int value = 1 + Log2<P / 2>::value;
+};
+template <>
+struct Log2<1> {
+  static constexpr int value = 0;
+};
+
+// Warp sums of P per-lane values (P a power of two <= 32) by a butterfly
+// that hands half of the values to the partner at each of the first log2 P
+// levels (P - 1 + log2(32 / P) shuffles).  Lane t returns the total of value
+// t >> (5 - log2 P).
+template <int P>
+__device__ __forceinline__ float rx_reduce(float (&y)[P], int lane) {
+#pragma unroll
+  for (int h = P / 2, off = 16; h >= 1; h >>= 1, off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int q = 0; q < h; ++q) {
+      const float send = up ? y[q] : y[q + h];
+      const float keep = up ? y[q + h] : y[q];
+      y[q] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  float t = y[0];
+#pragma unroll
+  for (int off = 16 / P; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  return t;
+}
+
+constexpr int RX_SEG = 8;  // row blocks per segment of the Householder passes
+
+template <int RPL, int CPW, int CL>
+__global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __restrict__ jobs, double eps,
+                                                            double* __restrict__ rdiag_all,
+                                                            int* __restrict__ order_all, int max_m, int max_k,
+                                                            int spin, int hang_rank) {
+  constexpr int P = Pow2Ceil<CPW>::value;
+  constexpr int LP = Log2<P>::value;
+  constexpr int LDV = 32 * RPL;  // rows of a staged column
+  constexpr int LDS = LDV + 4;   // + a 16-byte header: proposal norm and column
+  namespace cg = cooperative_groups;
+  const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int jid = blockIdx.x / CL;
+  const IdJob jb = jobs[jid];
+  const int d = jb.d, m = jb.m;
+  const float* Y = (const float*)jb.Y;
+  float* W = (float*)jb.W;
+  double* rdiag = rdiag_all + (long long)jid * max_k;
+  int* order = order_all + (long long)jid * max_m;
+  extern __shared__ __align__(16) float rx_smem[];
+  float* stage = rx_smem;                       // [2][RX_NW][LDS]: each warp's candidate, by step parity
+  float* land = stage + 2 * RX_NW * LDS;        // [2][CL][LDS]: the CL CTAs' candidates (CL > 1)
+  float* rdb = land + (CL > 1 ? 2 * CL * LDS : 0);  // [32][33]: diagonal block (epilogue)
+  unsigned char* skel = (unsigned char*)(rdb + 32 * 33);  // [m]: skeleton flags (epilogue)
+  __shared__ float s_wv[RX_NW];
+  __shared__ int s_wj[RX_NW];
+  __shared__ __align__(8) unsigned long long bar_c[2];
+  __shared__ int s_fail, s_nl;
+  __shared__ int s_list[RX_NW * CPW];  // epilogue: this CTA's non-skeleton columns
+  __shared__ float s_rd[32];           // epilogue: R1 diagonal of a block
+  __shared__ int s_ord[32];            // epilogue: pivot columns of a block
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int mycol = lane >> (5 - LP);  // column whose norm this lane holds after rx_reduce
+  const int myj = mycol < CPW ? rank + CL * (wid + RX_NW * mycol) : m;
+
+  float a[CPW][RPL];
+  unsigned act = 0;  // bit c: column c of this warp exists and is not pivoted
+  float y[P];
+#pragma unroll
+  for (int c = 0; c < P; ++c) y[c] = 0.f;
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) {
+    const int j = rank + CL * (wid + RX_NW * c);
+    if (j < m) act |= 1u << c;
+#pragma unroll
+    for (int s = 0; s < RPL; ++s) {
+      const int r = lane + 32 * s;
+      a[c][s] = (j < m && r < d) ? Y[r + (long long)j * d] : 0.f;
+      y[c] = fmaf(a[c][s], a[c][s], y[c]);
+    }
+  }
+  float cn = rx_reduce<P>(y, lane);  // trailing norm^2 of column mycol
+  if (!(mycol < CPW && ((act >> mycol) & 1))) cn = -1.f;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    if (CL > 1) {
+      for (int q = 0; q < 2; ++q)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(rx_saddr(&bar_c[q])) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  if (CL > 1)
+    cg::this_cluster().sync();  // every CTA's barriers exist before the first copy
+  else
+    __syncthreads();
+
+  const int kmax = min(d, m);
+  int k = kmax;
+  bool failed = false;
+  float thr = 0.f;
+  for (int i = 0; i < kmax; ++i) {
+    const int par = i & 1;
+    const int i0 = i & ~3;  // copies start at the 16-byte boundary at or below row i
+    // 1. each warp stages its best candidate column
+    {
+      float bv = cn;
+      int bj = cn >= 0.f ? myj : m;
+      id_argmax(bv, bj, 32 >> LP);
+      if (bj < m) {
+        const int cs = ((bj - rank) / CL - wid) / RX_NW;  // the candidate's slot in this warp
+        float* st = stage + ((size_t)par * RX_NW + wid) * LDS;
+#pragma unroll
+        for (int c = 0; c < CPW; ++c)
+          if (c == cs) {
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) st[lane + 32 * s] = a[c][s];
+          }
+      }
+      if (lane == 0) {
+        s_wv[wid] = bv;
+        s_wj[wid] = bj;
+      }
+      if (CL > 1) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // read next by bulk copies
+    }
+    __syncthreads();
+    // 2. the CTA's proposal; in a cluster, its candidate goes to every CTA
+    float b = lane < RX_NW ? s_wv[lane] : -1.f;
+    int p = lane < RX_NW ? s_wj[lane] : m;
+    id_argmax(b, p);
+    bool ok = true;
+    const float* vsrc;
+    if (CL == 1) {
+      vsrc = stage + ((size_t)par * RX_NW + (p < m ? (p / CL) % RX_NW : 0)) * LDS;
+    } else {
+      const unsigned bytes = (unsigned)(LDS - i0) * 4u;
+      if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(rx_saddr(&bar_c[par])),
+                     "r"(bytes * CL)
+                     : "memory");
+        if (p < m && !(i == 0 && rank == hang_rank)) {
+          float* st = stage + ((size_t)par * RX_NW + (p / CL) % RX_NW) * LDS;
+          st[LDV] = b;
+          st[LDV + 1] = __int_as_float(p);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          const uint32_t src = rx_saddr(st + i0);
+          const uint32_t dst = rx_saddr(land + ((size_t)par * CL + rank) * LDS + i0);
+          const uint32_t bar = rx_saddr(&bar_c[par]);
+          for (int q = 0; q < CL; ++q)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    rx_mapa(dst, q)),
+                "r"(src), "r"(bytes), "r"(rx_mapa(bar, q))
+                : "memory");
+        } else if (!(i == 0 && rank == hang_rank)) {  // no candidate left: an empty proposal
+          float* st = stage + (size_t)par * RX_NW * LDS;
+          st[LDV] = -1.f;
+          st[LDV + 1] = __int_as_float(m);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          const uint32_t src = rx_saddr(st + i0);
+          const uint32_t dst = rx_saddr(land + ((size_t)par * CL + rank) * LDS + i0);
+          const uint32_t bar = rx_saddr(&bar_c[par]);
+          for (int q = 0; q < CL; ++q)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    rx_mapa(dst, q)),
+                "r"(src), "r"(bytes), "r"(rx_mapa(bar, q))
+                : "memory");
+        }
+        // (the stage these copies read is rewritten two steps later, after
+        // this CTA's next wait: every peer sends its next copy only after
+        // its own copy of this step has landed)
+      }
+      ok = rx_wait(rx_saddr(&bar_c[par]), (i >> 1) & 1, spin);
+      b = -1.f;
+      p = m;
+      if (ok && lane < CL) {
+        const float* h = land + ((size_t)par * CL + lane) * LDS + LDV;
+        b = h[0];
+        p = __float_as_int(h[1]);
+      }
+      id_argmax(b, p);
+      if (p < 0 || p > m) p = m;
+      vsrc = land + ((size_t)par * CL + (p < m ? p % CL : 0)) * LDS;
+      if (__syncthreads_or(!ok)) {  // a wait ran out somewhere in the CTA
+        failed = true;
+        k = i;
+        break;
+      }
+    }
+    if (i == 0) thr = __double2float_rd(eps * eps * (double)fmaxf(b, 0.f));
+    if ((i == 0 ? !(b > 0.f) : !(b > thr)) || p >= m) {
+      k = i;
+      break;
+    }
+    // 3. the reflector H = I - tau w w^T with w = x - beta e_i (x the pivot
+    // column's trailing part): w is kept unscaled, row i replaced by vi
+    const float nrm = sqrtf(b);
+    const float alpha = vsrc[i];
+    const float beta = alpha >= 0.f ? -nrm : nrm;
+    const float vi = alpha - beta;
+    const float tau = -1.f / (beta * vi);
+    if (rank == 0 && threadIdx.x == 0) {
+      rdiag[i] = (double)beta;
+      order[i] = p;
+    }
+    if (rank == p % CL && wid == (p / CL) % RX_NW) act &= ~(1u << ((p / CL) / RX_NW));
+#pragma unroll
+    for (int c = 0; c < P; ++c) y[c] = 0.f;
+    // segments of RX_SEG row blocks: skipped when they lie wholly above row i
+    // or below row d, computed without branches otherwise
+#pragma unroll
+    for (int g = 0; g < RPL; g += RX_SEG) {
+      if (32 * (g + RX_SEG) <= i || 32 * g >= d) continue;
+#pragma unroll
+      for (int s = g; s < g + RX_SEG && s < RPL; ++s) {
+        const int r = lane + 32 * s;
+        const float x = vsrc[r];
+        const float vr = r > i ? x : (r == i ? vi : 0.f);
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) y[c] = fmaf(vr, a[c][s], y[c]);
+      }
+    }
+    const float dt = rx_reduce<P>(y, lane);
+    float f[CPW];
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      const float dc = __shfl_sync(0xffffffffu, dt, c << (5 - LP));
+      f[c] = ((act >> c) & 1) ? tau * dc : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < P; ++c) y[c] = 0.f;
+#pragma unroll
+    for (int g = 0; g < RPL; g += RX_SEG) {
+      if (32 * (g + RX_SEG) <= i || 32 * g >= d) continue;
+#pragma unroll
+      for (int s = g; s < g + RX_SEG && s < RPL; ++s) {
+        const int r = lane + 32 * s;
+        const float x = vsrc[r];
+        const float vr = r > i ? x : (r == i ? vi : 0.f);
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+          a[c][s] = fmaf(-f[c], vr, a[c][s]);
+          const float t = r > i ? a[c][s] : 0.f;
+          y[c] = fmaf(t, t, y[c]);
+        }
+      }
+    }
+    cn = rx_reduce<P>(y, lane);
+    if (!(mycol < CPW && ((act >> mycol) & 1))) cn = -1.f;
+  }
+  // the owned columns (R in place) go to W for the back substitution
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) {
+    const int j = rank + CL * (wid + RX_NW * c);
+    if (j < m) {
+#pragma unroll
+      for (int s = 0; s < RPL; ++s) {
+        const int r = lane + 32 * s;
+        if (r < d) W[r + (long long)j * d] = a[c][s];
+      }
+    }
+  }
+  if (failed && threadIdx.x == 0) s_fail = 1;
+  // every CTA has left the step loop (its copies have landed: each CTA
+  // waited for all of them), and W, rdiag and order are visible
+  if (CL > 1)
+    cg::this_cluster().sync();
+  else
+    __syncthreads();
+  bool any_fail = s_fail != 0;
+  if (CL > 1)
+    for (int q = 0; q < CL; ++q) any_fail = any_fail || *cg::this_cluster().map_shared_rank(&s_fail, q) != 0;
+  if (!any_fail) {
+    // X = R1^-1 R2 for this CTA's non-skeleton columns: a blocked back
+    // substitution over 32-row blocks from the bottom, 16 columns at a time
+    // in shared memory (the staging area), R1 read from W
+    for (int j = threadIdx.x; j < m; j += RX_THREADS) skel[j] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < k; t += RX_THREADS) skel[order[t]] = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int n = 0;
+      for (int j = rank; j < m; j += CL)
+        if (!skel[j]) s_list[n++] = j;
+      s_nl = n;
+    }
+    __syncthreads();
+    float* X = (float*)jb.X;
+    float* Bs = stage;  // k x 16, ld k
+    const int nl = s_nl;
+    for (int cb = 0; cb < nl && k > 0; cb += 16) {
+      const int nc = min(16, nl - cb);
+      for (int e = threadIdx.x; e < 16 * k; e += RX_THREADS) {
+        const int q = e / k, r = e - q * k;
+        Bs[e] = q < nc ? W[r + (long long)s_list[cb + q] * d] : 0.f;
+      }
+      for (int r1 = k; r1 > 0; r1 -= 32) {
+        const int r0 = max(r1 - 32, 0), nb = r1 - r0;
+        if (threadIdx.x < 32) {
+          s_ord[threadIdx.x] = threadIdx.x < nb ? order[r0 + threadIdx.x] : 0;
+          s_rd[threadIdx.x] = threadIdx.x < nb ? (float)rdiag[r0 + threadIdx.x] : 1.f;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 32; e += RX_THREADS) {  // R1(r0:r1, r0:r1), upper part
+          const int t = e & 31, c = e >> 5;
+          rdb[t * 33 + c] = (t < nb && c < nb && t < c) ? W[(r0 + t) + (long long)s_ord[c] * d] : 0.f;
+        }
+        __syncthreads();
+        for (int q = wid; q < nc; q += RX_NW) {  // the diagonal block, one warp per column
+          float x = lane < nb ? Bs[r0 + lane + q * k] : 0.f;
+          for (int c = nb - 1; c >= 0; --c) {
+            const float xc = __shfl_sync(0xffffffffu, x, c) / s_rd[c];
+            if (lane == c) x = xc;
+            if (lane < c) x = fmaf(-rdb[lane * 33 + c], xc, x);
+          }
+          if (lane < nb) Bs[r0 + lane + q * k] = x;
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < r0; r += RX_THREADS) {  // rows above the block
+          float acc[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+          for (int c = 0; c < nb; ++c) {
+            const float rc = W[r + (long long)s_ord[c] * d];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = fmaf(rc, Bs[r0 + c + q * k], acc[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < 16; ++q) Bs[r + q * k] -= acc[q];
+        }
+        __syncthreads();
+      }
+      for (int q = wid; q < nc; q += RX_NW) {  // X column and its place among the non-skeleton columns
+        const int j = s_list[cb + q];
+        int pos = 0;
+        for (int c = lane; c < j; c += 32) pos += skel[c] ? 0 : 1;
+        for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+        for (int r = lane; r < k; r += 32) X[r + (long long)pos * k] = Bs[r + q * k];
+        if (lane == 0) jb.piv[k + pos] = j;
+      }
+      __syncthreads();
+    }
+    if (k == 0)  // nothing to solve: every column keeps its place
+      for (int q = threadIdx.x; q < nl; q += RX_THREADS) {
+        const int j = s_list[q];
+        jb.piv[j] = j;
+      }
+  }
+  if (rank == 0) {
+    if (!any_fail)
+      for (int t = threadIdx.x; t < k; t += RX_THREADS) jb.piv[t] = order[t];
+    if (threadIdx.x == 0) *jb.rank = any_fail ? -1 : k;
+  }
+  if (CL > 1) cg::this_cluster().sync();  // peers may still read this CTA's failure flag
+}
+
+// shared memory of a configuration (bytes)
+inline size_t rx_smem_bytes(int rpl, int cl, int max_m) {
+  const size_t lds = 32 * (size_t)rpl + 4;
+  return sizeof(float) * ((2 * RX_NW + (cl > 1 ? 2 * cl : 0)) * lds + 32 * 33) + (size_t)std::max(max_m, 1);
+}
+
+template <int RPL, int CPW, int CL>
+int launch_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag, int* order,
+              cudaStream_t s, int spin, int hang_rank) {
+  if (max_d > 32 * RPL || max_m > CL * RX_NW * CPW) return -1;
+  auto kern = k_cpqr_id_rx<RPL, CPW, CL>;
+  const size_t smem = rx_smem_bytes(RPL, CL, max_m);
+  // one limit per kernel (the largest m it takes), so that the attribute set
+  // on a device never needs lowering or raising
+  if (!set_func_attr((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                     (int)rx_smem_bytes(RPL, CL, CL * RX_NW * CPW)))
+    return -1;
+  if (CL > 8 && !set_func_attr((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) return -1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * CL, 1, 1);
+  cfg.blockDim = dim3(RX_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = CL > 1 ? 1 : 0;
+  const int max_k = std::max(std::min(max_m, max_d), 1);
+  if (cudaLaunchKernelEx(&cfg, kern, jobs, eps, rdiag, order, std::max(max_m, 1), max_k,
+                         spin > 0 ? spin : RX_SPIN, hang_rank) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;  // not schedulable: the caller falls back
+  }
+  count_launch();
+  return 0;
+}
+
+// Configurations: rows per lane RPL (d <= 32 RPL) and columns per warp CPW,
+// chosen so that CPW * RPL data registers fit the 255 of a thread of a
+// 256-thread CTA.
+constexpr int RX_RPL[3] = {8, 16, 26};
+constexpr int RX_CPW[3] = {16, 10, 7};
+
+template <int RPL, int CPW>
+int launch_rx_cl(int cl, const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
+                 int* order, cudaStream_t s, int spin, int hang_rank) {
+  switch (cl) {
+    case 1: return launch_rx<RPL, CPW, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 2: return launch_rx<RPL, CPW, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 4: return launch_rx<RPL, CPW, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 8: return launch_rx<RPL, CPW, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 16: return launch_rx<RPL, CPW, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    default: return -1;
+  }
+}
+
+}  // namespace
+
+int id_rx_config(int d, int m) {
+  for (int t = 0; t < 3; ++t) {
+    if (d > 32 * RX_RPL[t]) continue;
+    for (int cl = 1; cl <= 16; cl *= 2)
+      if (m <= cl * RX_NW * RX_CPW[t]) return 32 * t + cl;
+    return 0;
+  }
+  return 0;
+}
+
+int batched_id_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag, int* order,
+                  int cfg, cudaStream_t s, int spin, int hang_rank) {
+  if (njobs <= 0) return 0;
+  const int t = cfg / 32, cl = cfg % 32;
+  switch (t) {
+    case 0: return launch_rx_cl<8, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 1: return launch_rx_cl<16, 10>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 2: return launch_rx_cl<26, 7>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    default: return -1;
+  }
+}
+
+}  // namespace hssmf

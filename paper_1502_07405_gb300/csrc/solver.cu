@@ -965,7 +965,10 @@ static hssmf_status batched_id_impl(int njobs, const void* Y, const long long* y
   }
   cudaMemcpyAsync(dj, jobs.data(), sizeof(IdJob) * njobs, cudaMemcpyHostToDevice, s);
   int r;
-  if (use_cluster == -2) {  // register-resident matrices (FP32) on a cluster sized for the largest job
+  if (use_cluster == -3) {  // register-resident matrices with pushed proposals (FP32)
+    const int cfg = std::is_same<T, float>::value ? id_rx_config(max_d, max_m) : 0;
+    r = cfg > 0 ? batched_id_rx(dj, njobs, max_m, max_d, eps, rdiag, order, cfg, s) : -1;
+  } else if (use_cluster == -2) {  // register-resident matrices (FP32) on a cluster sized for the largest job
     const int cfg = HssKern<T>::id_rr_config(max_d, max_m);
     r = cfg > 0 ? HssKern<T>::batched_id_rr(dj, njobs, max_m, max_d, eps, rdiag, order, cfg, s) : -1;
   } else if (use_cluster <= -102 && use_cluster >= -116) {  // shared-memory kernel on a given cluster size
@@ -989,6 +992,37 @@ static hssmf_status batched_id_impl(int njobs, const void* Y, const long long* y
 }
 
 extern "C" {
+
+hssmf_status hssmf_id_timeout_test(int cl, int spin) {
+  if (cl < 2 || cl > 16 || (cl & (cl - 1)) || spin < 1) return HSSMF_ERR_ARG;
+  const int d = 64, m = 8 * cl;
+  char* buf = nullptr;
+  const size_t bytes = 2 * sizeof(float) * d * m + sizeof(float) * m * m + sizeof(int) * (2 * m + 1) +
+                       sizeof(double) * m + sizeof(IdJob) + 1024;
+  if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return HSSMF_ERR_OOM;
+  }
+  hssmf_status st = HSSMF_OK;
+  if (cudaMemset(buf, 0, bytes) != cudaSuccess) st = HSSMF_ERR_CUDA;
+  float* Y = (float*)buf;
+  float* W = Y + d * m;
+  float* X = W + d * m;
+  int* piv = (int*)(X + m * m);
+  int* order = piv + m;
+  int* rank = order + m;
+  double* rdiag = (double*)(((uintptr_t)(rank + 1) + 255) & ~(uintptr_t)255);
+  IdJob* dj = (IdJob*)(((uintptr_t)(rdiag + m) + 255) & ~(uintptr_t)255);
+  const IdJob job{Y, W, piv, X, rank, d, m};
+  if (!st && cudaMemcpy(dj, &job, sizeof(IdJob), cudaMemcpyHostToDevice) != cudaSuccess) st = HSSMF_ERR_CUDA;
+  if (!st && batched_id_rx(dj, 1, m, d, 1e-4, rdiag, order, cl, 0, spin, 0) < 0) st = HSSMF_ERR_CUDA;
+  int rk = 0;
+  if (!st && (cudaMemcpy(&rk, rank, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)) st = HSSMF_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess && !st) st = HSSMF_ERR_CUDA;
+  cudaFree(buf);
+  if (st) return st;
+  return rk < 0 ? HSSMF_ERR_TIMEOUT : HSSMF_OK;
+}
 
 hssmf_status hssmf_batched_id(int prec, int njobs, const void* Y, const long long* y_off, const int* m,
                               const int* d, double eps, int* rank_host, int* piv, const long long* p_off,
@@ -1032,6 +1066,14 @@ int hssmf_get_id_trace(const hssmf_ctx* c, int* rec, int max_records) {
   return n;
 }
 
+int hssmf_get_id_launch_trace(const hssmf_ctx* c, double* rec, int max_records) {
+  if (!c) return -1;
+  const int n = (int)(c->id_launch_trace.size() / 6);
+  if (rec)
+    for (int i = 0; i < std::min(n, max_records) * 6; ++i) rec[i] = c->id_launch_trace[i];
+  return n;
+}
+
 hssmf_status hssmf_set_profiling(hssmf_ctx* c, int on) {
   if (!c) return HSSMF_ERR_ARG;
   c->prof.on = on != 0;
@@ -1046,6 +1088,10 @@ void hssmf_destroy(hssmf_ctx* c) {
   c->free_all();
   hss_release(*c);
   c->prof.release();
+  for (auto& e : c->id_ev) {  // launch timers left by a failed factorization
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;

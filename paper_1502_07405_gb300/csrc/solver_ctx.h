@@ -154,6 +154,11 @@ struct hssmf_ctx {
   // per-node ID records of the last factor (profiling on): front, node, round,
   // d, m, mc, kr, kc, accepted, kernel of the row ID, kernel of the column ID
   std::vector<int> id_trace;
+  // per-launch records of the ID kernels of the last profiled factor: kernel
+  // code, CTAs per job, jobs, largest d, largest m, device ms
+  std::vector<double> id_launch_trace;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> id_ev;  // pending, with their descriptors
+  std::vector<double> id_ev_desc;
 
   hssmf_status fail(hssmf_status st, const std::string& msg);
   hssmf_status cuda_check(cudaError_t e, const char* what);

@@ -78,3 +78,33 @@ def test_relres_takes_the_worst_system_and_column(monkeypatch):
     rg = np.linalg.norm(b[:, 1] - A.to_scipy() @ xe[:, 1]) / np.linalg.norm(b[:, 1])
     assert bench._relres(A, xe, b) == pytest.approx(rg, rel=1e-12)
     assert rg < r2  # the whole-vector residual hides the per-system one
+
+
+def test_reference_arm_scales_the_sample_and_loads_no_gpu_library(tmp_path):
+    """The reference arm times the oracle alone: in a fresh process, with a
+    small sample (a leaf front of the 64^3 tree) and a stand-in calibration
+    record, its value is the sample time times the recorded ratio, and
+    neither the package nor libhssmf.so is loaded."""
+    import subprocess
+    code = f"""
+import json, sys
+sys.path.insert(0, {ROOT!r})
+import bench
+from oracle import bench_sample as S
+S.SAMPLE_DEPTH = 9
+bench._sample_subprocess = lambda threads, depth=None: 0.25
+bench._calibration = lambda: {{"ratio": 100.0, "sample_depth": 9, "sample_fronts": 1, "sample_hss_fronts": 0,
+    "full_s": 900.0, "iterations": 9, "relres": 1e-11, "sample_s": 9.0, "machine": {{"machine": "x", "cpus": 8}}}}
+class Args:
+    steps, warmup = 2, 1
+bench.run_reference(Args())
+maps = open("/proc/self/maps").read()
+print(json.dumps({{"lib": "libhssmf" in maps, "pkg": "paper_1502_07405_gb300" in sys.modules}}))
+"""
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, check=True, cwd=str(tmp_path))
+    lines = [json.loads(x) for x in out.stdout.strip().splitlines()]
+    ref, loaded = lines[0], lines[1]
+    assert ref["impl"] == "reference" and ref["steps"] == 2
+    assert ref["value"] == pytest.approx(ref["ms_per_step"] * 100.0, rel=1e-3)
+    assert ref["cpu_baseline"]["sample_ms_1thread"] == 250.0
+    assert loaded == {"lib": False, "pkg": False}

@@ -165,3 +165,63 @@ def test_largest_node_shape_all_kernel_families(prec):
         assert sorted(piv.tolist()) == list(range(Y.shape[1]))
         err = np.linalg.norm(Y[:, piv[k:]] - Y[:, piv[:k]] @ X) / np.linalg.norm(Y)
         assert err <= 2 * eps, (mode, err)
+
+
+@pytest.mark.parametrize("shapes", [
+    [(128, 128), (192, 100), (64, 7)],          # 8 rows per lane, one CTA
+    [(256, 256), (200, 250), (250, 33)],        # 8 rows per lane, cluster of 2
+    [(256, 2000), (130, 1500)],                 # 8 rows per lane, cluster of 16
+    [(320, 64), (512, 60), (300, 17)],          # 16 rows per lane, one CTA
+    [(512, 1200), (400, 700), (257, 300)],      # 16 rows per lane, cluster of 16
+    [(832, 800), (704, 600), (600, 130)],       # 26 rows per lane, cluster of 16
+    [(768, 300), (520, 256)],                   # 26 rows per lane, cluster of 8
+])
+def test_exchange_register_id_shapes(shapes):
+    """The register-resident kernel with one exchange of proposals per pivot
+    step (use_cluster -3): the oracle's rank (within one, FP32 rounding) and
+    skeleton columns, and the interpolation error at the tolerance."""
+    Ys = [_decaying(d_, m_, max(9.0, min(d_, m_) / 40.0), 17 + i) for i, (d_, m_) in enumerate(shapes)]
+    eps = 1e-4
+    res = _run_ids(Ys, eps, 1, -3)
+    for Y, (k, piv, Xg) in zip(Ys, res):
+        ko, pivo, Ro = hss.cpqr_rank(Y, eps)
+        assert abs(k - ko) <= 1
+        kk = min(k, ko)
+        assert np.array_equal(piv[:kk], pivo[:kk])
+        assert sorted(piv.tolist()) == list(range(Y.shape[1]))
+        U = np.zeros((Y.shape[1], k))
+        U[piv[:k], :] = np.eye(k)
+        U[piv[k:], :] = Xg.T
+        err = np.linalg.norm(Y[:, piv[:k]] @ U.T - Y) / np.linalg.norm(Y)
+        assert err <= 50 * eps
+
+
+def test_exchange_register_id_exact_low_rank_zero_and_full_rank():
+    rng = np.random.default_rng(8)
+    Y1 = rng.standard_normal((200, 9)) @ rng.standard_normal((9, 500))
+    Y2 = np.zeros((64, 80))
+    Y3 = rng.standard_normal((96, 40))  # full column rank: k = m, no X
+    res = _run_ids([Y1, Y2, Y3], 1e-5, 1, -3)
+    k, piv, Xg = res[0]
+    assert k == 9
+    U = np.zeros((500, 9))
+    U[piv[:9], :] = np.eye(9)
+    U[piv[9:], :] = Xg.T
+    assert np.linalg.norm(Y1[:, piv[:9]] @ U.T - Y1) <= 1e-5 * np.linalg.norm(Y1)
+    assert res[1][0] == 0
+    assert res[2][0] == 40 and sorted(res[2][1].tolist()) == list(range(40))
+
+
+@pytest.mark.parametrize("cl", [2, 16])
+def test_bounded_wait_runs_out_and_reports_timeout(cl):
+    """Failure path of the bounded waits: one CTA of the cluster withholds
+    its first proposal, every wait of the cluster runs out (a few thousand
+    polls), the kernel meets its barriers and reports rank -1, the call
+    returns HSSMF_ERR_TIMEOUT, and the context stays usable."""
+    import paper_1502_07405_gb300 as P
+    P.lib.hssmf_id_timeout_test.restype = C.c_int
+    assert P.lib.hssmf_id_timeout_test(cl, 4096) == P.ERR_TIMEOUT
+    torch.cuda.synchronize()
+    Y = _decaying(256, 300, 9.0, 3)
+    (k, piv, _), = _run_ids([Y], 1e-4, 1, -3)
+    assert k == hss.cpqr_rank(Y, 1e-4)[0] or abs(k - hss.cpqr_rank(Y, 1e-4)[0]) <= 1
