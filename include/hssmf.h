@@ -258,7 +258,8 @@ int hssmf_get_id_launch_trace(const hssmf_ctx* ctx, double* rec, int max_records
  * clusters of c CTAs whatever the size; use_cluster = -3 (prec 1 only) keeps
  * every matrix in the registers of a cluster of 1..16 CTAs of 256 threads
  * with one exchange of proposals per pivot step (d <= 832; m up to 2048,
- * 1280 or 896 for d <= 256, 512, 832), else HSSMF_ERR_ARG;
+ * 1280 or 896 for d <= 256, 512, 832), else HSSMF_ERR_ARG; use_cluster =
+ * -4 the same on CTAs of 512 threads (m up to 2048, 1024 or 768);
  * use_cluster = -2 (prec 1 only) keeps
  * every matrix in the registers of a
  * cluster of 1..16 CTAs, for d <= 512 and m <= 2048 (d <= 256) or m <= 1024

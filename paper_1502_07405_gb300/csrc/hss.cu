@@ -752,26 +752,34 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
         std::map<int, std::vector<IdJob>> rx_tier;
         std::map<int, std::vector<int>> rx_ix;
         std::map<int, std::pair<int, int>> rx_md;
+        // The exchange kernel takes every node that needs a cluster (it may
+        // use more CTAs per node than the shared-memory kernels, registers
+        // holding less than shared memory; measured at 64^3 it is faster
+        // whether or not the launch fits in one wave of the GPU).
+        std::vector<int> rx_cfg(ij.size(), 0), old_cl(ij.size(), 1);
         for (size_t ji = 0; ji < ij.size(); ++ji) {
           const IdJob& j = ij[ji];
           const int rx = std::is_same<T, float>::value ? id_rx_config(j.d, j.m) : 0;
-          if (rx > 0) {
-            const int rr = HssKern<T>::id_rr_config(j.d, j.m);
-            const int cl_sm = HssKern<T>::id_smem_cluster_size(j.d, j.m);
-            const bool old_single = (rr > 0 && (cl_sm == 0 || (rr & 31) <= cl_sm)) ? (rr & 31) == 1
-                                    : (long long)j.d * j.m * (long long)sizeof(T) > kTinyIdBytes ? cl_sm == 1
-                                                                                                 : true;
-            if (!old_single || (rx & 31) > 1) {
-              rx_tier[rx].push_back(j);
-              rx_ix[rx].push_back((int)ji);
-              route[ji] = 400 + (rx & 31);
-              auto& md = rx_md[rx];
-              md.first = std::max(md.first, j.m);
-              md.second = std::max(md.second, j.d);
-              continue;
-            }
+          const int rr = HssKern<T>::id_rr_config(j.d, j.m);
+          const int cl_sm = HssKern<T>::id_smem_cluster_size(j.d, j.m);
+          old_cl[ji] = (rr > 0 && (cl_sm == 0 || (rr & 31) <= cl_sm)) ? (rr & 31)
+                       : (long long)j.d * j.m * (long long)sizeof(T) > kTinyIdBytes ? (cl_sm > 0 ? cl_sm : 16)
+                                                                                    : 1;
+          if (rx > 0 && (old_cl[ji] > 1 || (rx & 31) > 1)) rx_cfg[ji] = rx;
+        }
+        for (size_t ji = 0; ji < ij.size(); ++ji) {
+          const IdJob& j = ij[ji];
+          const int rx = rx_cfg[ji];
+          if (rx == 0) {
+            route_old(ji);
+            continue;
           }
-          route_old(ji);
+          rx_tier[rx].push_back(j);
+          rx_ix[rx].push_back((int)ji);
+          route[ji] = 400 + (rx & 31);
+          auto& md = rx_md[rx];
+          md.first = std::max(md.first, j.m);
+          md.second = std::max(md.second, j.d);
         }
         c.prof.mark(PH_IDK, X.s);
         // with profiling on, every ID launch is timed by its own events

@@ -123,13 +123,14 @@ struct UlvBwdJob {
 
 // Register-resident ID of FP32 nodes on clusters of 1..16 CTAs with one
 // exchange round per pivot step (k_id_rx.cu).  id_rx_config: 0 if a d x m
-// node does not fit, else a configuration code for batched_id_rx.  rdiag
+// node does not fit, else a configuration code for batched_id_rx (family 0:
+// 256-thread CTAs, 255 registers a thread; 1: 512-thread CTAs).  rdiag
 // (njobs x min(max_m, max_d) doubles) and order (njobs x max_m ints) are
 // scratch.  spin bounds every wait (0: the default); hang_rank >= 0 makes
 // that CTA of every cluster withhold its first proposal, so that the waits
 // run out (tests of the timeout path; -1 otherwise).  Returns -1 if the
 // configuration cannot be launched (the caller falls back).
-int id_rx_config(int d, int m);
+int id_rx_config(int d, int m, int family = 0);
 int batched_id_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag, int* order,
                   int cfg, cudaStream_t s, int spin = 0, int hang_rank = -1);
 

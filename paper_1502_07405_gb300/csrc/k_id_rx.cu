@@ -45,8 +45,6 @@
 namespace hssmf {
 namespace {
 
-constexpr int RX_THREADS = 256;
-constexpr int RX_NW = RX_THREADS / 32;
 constexpr int RX_SPIN = 1 << 22;  // polls of a bounded wait
 
 __device__ __forceinline__ uint32_t rx_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -111,8 +109,8 @@ __device__ __forceinline__ float rx_reduce(float (&y)[P], int lane) {
 
 constexpr int RX_SEG = 8;  // row blocks per segment of the Householder passes
 
-template <int RPL, int CPW, int CL>
-__global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __restrict__ jobs, double eps,
+template <int RPL, int CPW, int CL, int NW>
+__global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restrict__ jobs, double eps,
                                                             double* __restrict__ rdiag_all,
                                                             int* __restrict__ order_all, int max_m, int max_k,
                                                             int spin, int hang_rank) {
@@ -130,20 +128,21 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
   double* rdiag = rdiag_all + (long long)jid * max_k;
   int* order = order_all + (long long)jid * max_m;
   extern __shared__ __align__(16) float rx_smem[];
-  float* stage = rx_smem;                       // [2][RX_NW][LDS]: each warp's candidate, by step parity
-  float* land = stage + 2 * RX_NW * LDS;        // [2][CL][LDS]: the CL CTAs' candidates (CL > 1)
-  float* rdb = land + (CL > 1 ? 2 * CL * LDS : 0);  // [32][33]: diagonal block (epilogue)
+  float* stage = rx_smem;                       // [2][NW][LDS]: each warp's candidate, by step parity
+  float* land = stage + 2 * NW * LDS;        // [2][CL][LDS]: the CL CTAs' candidates (CL > 1)
+  float* vm = land + (CL > 1 ? 2 * CL * LDS : 0);  // [LDV]: the step's reflector, masked
+  float* rdb = vm + LDV;                            // [32][33]: diagonal block (epilogue)
   unsigned char* skel = (unsigned char*)(rdb + 32 * 33);  // [m]: skeleton flags (epilogue)
-  __shared__ float s_wv[RX_NW];
-  __shared__ int s_wj[RX_NW];
+  __shared__ float s_wv[NW];
+  __shared__ int s_wj[NW];
   __shared__ __align__(8) unsigned long long bar_c[2];
   __shared__ int s_fail, s_nl;
-  __shared__ int s_list[RX_NW * CPW];  // epilogue: this CTA's non-skeleton columns
+  __shared__ int s_list[NW * CPW];  // epilogue: this CTA's non-skeleton columns
   __shared__ float s_rd[32];           // epilogue: R1 diagonal of a block
   __shared__ int s_ord[32];            // epilogue: pivot columns of a block
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int mycol = lane >> (5 - LP);  // column whose norm this lane holds after rx_reduce
-  const int myj = mycol < CPW ? rank + CL * (wid + RX_NW * mycol) : m;
+  const int myj = mycol < CPW ? rank + CL * (wid + NW * mycol) : m;
 
   float a[CPW][RPL];
   unsigned act = 0;  // bit c: column c of this warp exists and is not pivoted
@@ -152,7 +151,7 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
   for (int c = 0; c < P; ++c) y[c] = 0.f;
 #pragma unroll
   for (int c = 0; c < CPW; ++c) {
-    const int j = rank + CL * (wid + RX_NW * c);
+    const int j = rank + CL * (wid + NW * c);
     if (j < m) act |= 1u << c;
 #pragma unroll
     for (int s = 0; s < RPL; ++s) {
@@ -189,13 +188,17 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
       int bj = cn >= 0.f ? myj : m;
       id_argmax(bv, bj, 32 >> LP);
       if (bj < m) {
-        const int cs = ((bj - rank) / CL - wid) / RX_NW;  // the candidate's slot in this warp
-        float* st = stage + ((size_t)par * RX_NW + wid) * LDS;
+        const int cs = ((bj - rank) / CL - wid) / NW;  // the candidate's slot in this warp
+        float* st = stage + ((size_t)par * NW + wid) * LDS;
 #pragma unroll
         for (int c = 0; c < CPW; ++c)
           if (c == cs) {
 #pragma unroll
-            for (int s = 0; s < RPL; ++s) st[lane + 32 * s] = a[c][s];
+            for (int g = 0; g < RPL; g += RX_SEG) {  // rows from the segment holding row i
+              if (32 * (g + RX_SEG) <= i) continue;
+#pragma unroll
+              for (int s = g; s < g + RX_SEG && s < RPL; ++s) st[lane + 32 * s] = a[c][s];
+            }
           }
       }
       if (lane == 0) {
@@ -206,13 +209,13 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
     }
     __syncthreads();
     // 2. the CTA's proposal; in a cluster, its candidate goes to every CTA
-    float b = lane < RX_NW ? s_wv[lane] : -1.f;
-    int p = lane < RX_NW ? s_wj[lane] : m;
+    float b = lane < NW ? s_wv[lane] : -1.f;
+    int p = lane < NW ? s_wj[lane] : m;
     id_argmax(b, p);
     bool ok = true;
     const float* vsrc;
     if (CL == 1) {
-      vsrc = stage + ((size_t)par * RX_NW + (p < m ? (p / CL) % RX_NW : 0)) * LDS;
+      vsrc = stage + ((size_t)par * NW + (p < m ? (p / CL) % NW : 0)) * LDS;
     } else {
       const unsigned bytes = (unsigned)(LDS - i0) * 4u;
       if (threadIdx.x == 0) {
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
                      "r"(bytes * CL)
                      : "memory");
         if (p < m && !(i == 0 && rank == hang_rank)) {
-          float* st = stage + ((size_t)par * RX_NW + (p / CL) % RX_NW) * LDS;
+          float* st = stage + ((size_t)par * NW + (p / CL) % NW) * LDS;
           st[LDV] = b;
           st[LDV + 1] = __int_as_float(p);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
                 "r"(src), "r"(bytes), "r"(rx_mapa(bar, q))
                 : "memory");
         } else if (!(i == 0 && rank == hang_rank)) {  // no candidate left: an empty proposal
-          float* st = stage + (size_t)par * RX_NW * LDS;
+          float* st = stage + (size_t)par * NW * LDS;
           st[LDV] = -1.f;
           st[LDV + 1] = __int_as_float(m);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -263,29 +266,34 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
       id_argmax(b, p);
       if (p < 0 || p > m) p = m;
       vsrc = land + ((size_t)par * CL + (p < m ? p % CL : 0)) * LDS;
-      if (__syncthreads_or(!ok)) {  // a wait ran out somewhere in the CTA
-        failed = true;
-        k = i;
-        break;
-      }
     }
     if (i == 0) thr = __double2float_rd(eps * eps * (double)fmaxf(b, 0.f));
-    if ((i == 0 ? !(b > 0.f) : !(b > thr)) || p >= m) {
-      k = i;
-      break;
-    }
+    const bool stop = !ok || (i == 0 ? !(b > 0.f) : !(b > thr)) || p >= m;
     // 3. the reflector H = I - tau w w^T with w = x - beta e_i (x the pivot
-    // column's trailing part): w is kept unscaled, row i replaced by vi
+    // column's trailing part): w is kept unscaled, row i replaced by vi; the
+    // CTA writes it masked (zero above row i) from the first active segment
     const float nrm = sqrtf(b);
-    const float alpha = vsrc[i];
+    const float alpha = stop ? 1.f : vsrc[i];
     const float beta = alpha >= 0.f ? -nrm : nrm;
     const float vi = alpha - beta;
     const float tau = -1.f / (beta * vi);
+    if (!stop)
+      for (int r = (i / (32 * RX_SEG)) * (32 * RX_SEG) + threadIdx.x; r < LDV; r += 32 * NW)
+        vm[r] = r > i ? vsrc[r] : (r == i ? vi : 0.f);
+    if (__syncthreads_or(!ok)) {  // a wait ran out somewhere in the CTA
+      failed = true;
+      k = i;
+      break;
+    }
+    if (stop) {
+      k = i;
+      break;
+    }
     if (rank == 0 && threadIdx.x == 0) {
       rdiag[i] = (double)beta;
       order[i] = p;
     }
-    if (rank == p % CL && wid == (p / CL) % RX_NW) act &= ~(1u << ((p / CL) / RX_NW));
+    if (rank == p % CL && wid == (p / CL) % NW) act &= ~(1u << ((p / CL) / NW));
 #pragma unroll
     for (int c = 0; c < P; ++c) y[c] = 0.f;
     // segments of RX_SEG row blocks: skipped when they lie wholly above row i
@@ -295,9 +303,7 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
       if (32 * (g + RX_SEG) <= i || 32 * g >= d) continue;
 #pragma unroll
       for (int s = g; s < g + RX_SEG && s < RPL; ++s) {
-        const int r = lane + 32 * s;
-        const float x = vsrc[r];
-        const float vr = r > i ? x : (r == i ? vi : 0.f);
+        const float vr = vm[lane + 32 * s];
 #pragma unroll
         for (int c = 0; c < CPW; ++c) y[c] = fmaf(vr, a[c][s], y[c]);
       }
@@ -317,8 +323,7 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
 #pragma unroll
       for (int s = g; s < g + RX_SEG && s < RPL; ++s) {
         const int r = lane + 32 * s;
-        const float x = vsrc[r];
-        const float vr = r > i ? x : (r == i ? vi : 0.f);
+        const float vr = vm[r];
 #pragma unroll
         for (int c = 0; c < CPW; ++c) {
           a[c][s] = fmaf(-f[c], vr, a[c][s]);
@@ -333,7 +338,7 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
   // the owned columns (R in place) go to W for the back substitution
 #pragma unroll
   for (int c = 0; c < CPW; ++c) {
-    const int j = rank + CL * (wid + RX_NW * c);
+    const int j = rank + CL * (wid + NW * c);
     if (j < m) {
 #pragma unroll
       for (int s = 0; s < RPL; ++s) {
@@ -356,9 +361,9 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
     // X = R1^-1 R2 for this CTA's non-skeleton columns: a blocked back
     // substitution over 32-row blocks from the bottom, 16 columns at a time
     // in shared memory (the staging area), R1 read from W
-    for (int j = threadIdx.x; j < m; j += RX_THREADS) skel[j] = 0;
+    for (int j = threadIdx.x; j < m; j += (32 * NW)) skel[j] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < k; t += RX_THREADS) skel[order[t]] = 1;
+    for (int t = threadIdx.x; t < k; t += (32 * NW)) skel[order[t]] = 1;
     __syncthreads();
     if (threadIdx.x == 0) {
       int n = 0;
@@ -372,7 +377,7 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
     const int nl = s_nl;
     for (int cb = 0; cb < nl && k > 0; cb += 16) {
       const int nc = min(16, nl - cb);
-      for (int e = threadIdx.x; e < 16 * k; e += RX_THREADS) {
+      for (int e = threadIdx.x; e < 16 * k; e += (32 * NW)) {
         const int q = e / k, r = e - q * k;
         Bs[e] = q < nc ? W[r + (long long)s_list[cb + q] * d] : 0.f;
       }
@@ -383,12 +388,12 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
           s_rd[threadIdx.x] = threadIdx.x < nb ? (float)rdiag[r0 + threadIdx.x] : 1.f;
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < 32 * 32; e += RX_THREADS) {  // R1(r0:r1, r0:r1), upper part
+        for (int e = threadIdx.x; e < 32 * 32; e += (32 * NW)) {  // R1(r0:r1, r0:r1), upper part
           const int t = e & 31, c = e >> 5;
           rdb[t * 33 + c] = (t < nb && c < nb && t < c) ? W[(r0 + t) + (long long)s_ord[c] * d] : 0.f;
         }
         __syncthreads();
-        for (int q = wid; q < nc; q += RX_NW) {  // the diagonal block, one warp per column
+        for (int q = wid; q < nc; q += NW) {  // the diagonal block, one warp per column
           float x = lane < nb ? Bs[r0 + lane + q * k] : 0.f;
           for (int c = nb - 1; c >= 0; --c) {
             const float xc = __shfl_sync(0xffffffffu, x, c) / s_rd[c];
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
           if (lane < nb) Bs[r0 + lane + q * k] = x;
         }
         __syncthreads();
-        for (int r = threadIdx.x; r < r0; r += RX_THREADS) {  // rows above the block
+        for (int r = threadIdx.x; r < r0; r += (32 * NW)) {  // rows above the block
           float acc[16];
 #pragma unroll
           for (int q = 0; q < 16; ++q) acc[q] = 0.f;
@@ -412,7 +417,7 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
         }
         __syncthreads();
       }
-      for (int q = wid; q < nc; q += RX_NW) {  // X column and its place among the non-skeleton columns
+      for (int q = wid; q < nc; q += NW) {  // X column and its place among the non-skeleton columns
         const int j = s_list[cb + q];
         int pos = 0;
         for (int c = lane; c < j; c += 32) pos += skel[c] ? 0 : 1;
@@ -423,40 +428,40 @@ __global__ void __launch_bounds__(RX_THREADS, 1) k_cpqr_id_rx(const IdJob* __res
       __syncthreads();
     }
     if (k == 0)  // nothing to solve: every column keeps its place
-      for (int q = threadIdx.x; q < nl; q += RX_THREADS) {
+      for (int q = threadIdx.x; q < nl; q += (32 * NW)) {
         const int j = s_list[q];
         jb.piv[j] = j;
       }
   }
   if (rank == 0) {
     if (!any_fail)
-      for (int t = threadIdx.x; t < k; t += RX_THREADS) jb.piv[t] = order[t];
+      for (int t = threadIdx.x; t < k; t += (32 * NW)) jb.piv[t] = order[t];
     if (threadIdx.x == 0) *jb.rank = any_fail ? -1 : k;
   }
   if (CL > 1) cg::this_cluster().sync();  // peers may still read this CTA's failure flag
 }
 
 // shared memory of a configuration (bytes)
-inline size_t rx_smem_bytes(int rpl, int cl, int max_m) {
+inline size_t rx_smem_bytes(int rpl, int nw, int cl, int max_m) {
   const size_t lds = 32 * (size_t)rpl + 4;
-  return sizeof(float) * ((2 * RX_NW + (cl > 1 ? 2 * cl : 0)) * lds + 32 * 33) + (size_t)std::max(max_m, 1);
+  return sizeof(float) * ((2 * nw + (cl > 1 ? 2 * cl : 0)) * lds + 32 * rpl + 32 * 33) + (size_t)std::max(max_m, 1);
 }
 
-template <int RPL, int CPW, int CL>
+template <int RPL, int CPW, int NW, int CL>
 int launch_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag, int* order,
               cudaStream_t s, int spin, int hang_rank) {
-  if (max_d > 32 * RPL || max_m > CL * RX_NW * CPW) return -1;
-  auto kern = k_cpqr_id_rx<RPL, CPW, CL>;
-  const size_t smem = rx_smem_bytes(RPL, CL, max_m);
+  if (max_d > 32 * RPL || max_m > CL * NW * CPW) return -1;
+  auto kern = k_cpqr_id_rx<RPL, CPW, CL, NW>;
+  const size_t smem = rx_smem_bytes(RPL, NW, CL, max_m);
   // one limit per kernel (the largest m it takes), so that the attribute set
   // on a device never needs lowering or raising
   if (!set_func_attr((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                     (int)rx_smem_bytes(RPL, CL, CL * RX_NW * CPW)))
+                     (int)rx_smem_bytes(RPL, NW, CL, CL * NW * CPW)))
     return -1;
   if (CL > 8 && !set_func_attr((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * CL, 1, 1);
-  cfg.blockDim = dim3(RX_THREADS, 1, 1);
+  cfg.blockDim = dim3(32 * NW, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
@@ -476,32 +481,35 @@ int launch_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, do
   return 0;
 }
 
-// Configurations: rows per lane RPL (d <= 32 RPL) and columns per warp CPW,
-// chosen so that CPW * RPL data registers fit the 255 of a thread of a
-// 256-thread CTA.
-constexpr int RX_RPL[3] = {8, 16, 26};
-constexpr int RX_CPW[3] = {16, 10, 7};
-
-template <int RPL, int CPW>
+template <int RPL, int CPW, int NW>
 int launch_rx_cl(int cl, const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
                  int* order, cudaStream_t s, int spin, int hang_rank) {
   switch (cl) {
-    case 1: return launch_rx<RPL, CPW, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 2: return launch_rx<RPL, CPW, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 4: return launch_rx<RPL, CPW, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 8: return launch_rx<RPL, CPW, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 16: return launch_rx<RPL, CPW, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 1: return launch_rx<RPL, CPW, NW, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 2: return launch_rx<RPL, CPW, NW, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 4: return launch_rx<RPL, CPW, NW, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 8: return launch_rx<RPL, CPW, NW, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 16: return launch_rx<RPL, CPW, NW, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
     default: return -1;
   }
 }
 
+// Configurations (rows per lane RPL: d <= 32 RPL; columns per warp CPW; warps
+// per CTA NW): CPW * RPL data registers of a thread fit the 255 of a
+// 256-thread CTA (family 0) or the 128 of a 512-thread CTA (family 1).
+struct RxShape {
+  int rpl, cpw, nw;
+};
+constexpr RxShape RX_SHAPES[6] = {{8, 16, 8}, {16, 10, 8}, {26, 7, 8}, {8, 8, 16}, {16, 4, 16}, {26, 3, 16}};
+
 }  // namespace
 
-int id_rx_config(int d, int m) {
-  for (int t = 0; t < 3; ++t) {
-    if (d > 32 * RX_RPL[t]) continue;
+int id_rx_config(int d, int m, int family) {
+  for (int t = 3 * family; t < 3 * family + 3; ++t) {
+    const RxShape& c = RX_SHAPES[t];
+    if (d > 32 * c.rpl) continue;
     for (int cl = 1; cl <= 16; cl *= 2)
-      if (m <= cl * RX_NW * RX_CPW[t]) return 32 * t + cl;
+      if (m <= cl * c.nw * c.cpw) return 32 * t + cl;
     return 0;
   }
   return 0;
@@ -512,9 +520,12 @@ int batched_id_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps
   if (njobs <= 0) return 0;
   const int t = cfg / 32, cl = cfg % 32;
   switch (t) {
-    case 0: return launch_rx_cl<8, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 1: return launch_rx_cl<16, 10>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 2: return launch_rx_cl<26, 7>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 0: return launch_rx_cl<8, 16, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 1: return launch_rx_cl<16, 10, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 2: return launch_rx_cl<26, 7, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 3: return launch_rx_cl<8, 8, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 4: return launch_rx_cl<16, 4, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 5: return launch_rx_cl<26, 3, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
     default: return -1;
   }
 }

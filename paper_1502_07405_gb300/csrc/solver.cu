@@ -279,6 +279,13 @@ hssmf_status hssmf_ctx::ensure_device() {
   const int n = S.n, nfr = (int)S.fronts.size();
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);
   hssmf_status st;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) ==
+                                                   cudaSuccess && nsm > 0)
+      num_sms = nsm;
+    cudaGetLastError();
+  }
   if (!ev0 && (st = cuda_check(cudaEventCreate(&ev0), "event"))) return st;
   if (!ev1 && (st = cuda_check(cudaEventCreate(&ev1), "event"))) return st;
   d_status = (unsigned*)dalloc(sizeof(unsigned) * 4);
@@ -965,8 +972,8 @@ static hssmf_status batched_id_impl(int njobs, const void* Y, const long long* y
   }
   cudaMemcpyAsync(dj, jobs.data(), sizeof(IdJob) * njobs, cudaMemcpyHostToDevice, s);
   int r;
-  if (use_cluster == -3) {  // register-resident matrices with pushed proposals (FP32)
-    const int cfg = std::is_same<T, float>::value ? id_rx_config(max_d, max_m) : 0;
+  if (use_cluster == -3 || use_cluster == -4) {  // register-resident matrices, one exchange per step (FP32)
+    const int cfg = std::is_same<T, float>::value ? id_rx_config(max_d, max_m, -3 - use_cluster) : 0;
     r = cfg > 0 ? batched_id_rx(dj, njobs, max_m, max_d, eps, rdiag, order, cfg, s) : -1;
   } else if (use_cluster == -2) {  // register-resident matrices (FP32) on a cluster sized for the largest job
     const int cfg = HssKern<T>::id_rr_config(max_d, max_m);

@@ -91,6 +91,7 @@ struct PhaseProf {
 struct hssmf_ctx {
   hssmf_opts opts{};
   bool fp32 = false;
+  int num_sms = 148;  // streaming multiprocessors of the context's device
   cudaStream_t stream = nullptr;
   std::string err;
   bool analyzed = false, factored = false;

@@ -167,22 +167,27 @@ def test_largest_node_shape_all_kernel_families(prec):
         assert err <= 2 * eps, (mode, err)
 
 
-@pytest.mark.parametrize("shapes", [
-    [(128, 128), (192, 100), (64, 7)],          # 8 rows per lane, one CTA
-    [(256, 256), (200, 250), (250, 33)],        # 8 rows per lane, cluster of 2
-    [(256, 2000), (130, 1500)],                 # 8 rows per lane, cluster of 16
-    [(320, 64), (512, 60), (300, 17)],          # 16 rows per lane, one CTA
-    [(512, 1200), (400, 700), (257, 300)],      # 16 rows per lane, cluster of 16
-    [(832, 800), (704, 600), (600, 130)],       # 26 rows per lane, cluster of 16
-    [(768, 300), (520, 256)],                   # 26 rows per lane, cluster of 8
+@pytest.mark.parametrize("family,shapes", [
+    (-3, [(128, 128), (192, 100), (64, 7)]),          # 8 rows per lane, one CTA
+    (-3, [(256, 256), (200, 250), (250, 33)]),        # 8 rows per lane, cluster of 2
+    (-3, [(256, 2000), (130, 1500)]),                 # 8 rows per lane, cluster of 16
+    (-3, [(320, 64), (512, 60), (300, 17)]),          # 16 rows per lane, one CTA
+    (-3, [(512, 1200), (400, 700), (257, 300)]),      # 16 rows per lane, cluster of 16
+    (-3, [(832, 800), (704, 600), (600, 130)]),       # 26 rows per lane, cluster of 16
+    (-3, [(768, 300), (520, 256)]),                   # 26 rows per lane, cluster of 8
+    (-4, [(128, 128), (192, 100), (64, 7)]),          # 512-thread CTAs: one CTA
+    (-4, [(256, 2000), (130, 1500)]),                 # cluster of 16
+    (-4, [(512, 1000), (400, 700), (257, 300)]),      # 16 rows per lane, cluster of 16
+    (-4, [(832, 760), (704, 600), (600, 130)]),       # 26 rows per lane, cluster of 16
 ])
-def test_exchange_register_id_shapes(shapes):
+def test_exchange_register_id_shapes(family, shapes):
     """The register-resident kernel with one exchange of proposals per pivot
-    step (use_cluster -3): the oracle's rank (within one, FP32 rounding) and
-    skeleton columns, and the interpolation error at the tolerance."""
+    step (use_cluster -3: 256-thread CTAs, -4: 512-thread CTAs): the oracle's
+    rank (within one, FP32 rounding) and skeleton columns, and the
+    interpolation error at the tolerance."""
     Ys = [_decaying(d_, m_, max(9.0, min(d_, m_) / 40.0), 17 + i) for i, (d_, m_) in enumerate(shapes)]
     eps = 1e-4
-    res = _run_ids(Ys, eps, 1, -3)
+    res = _run_ids(Ys, eps, 1, family)
     for Y, (k, piv, Xg) in zip(Ys, res):
         ko, pivo, Ro = hss.cpqr_rank(Y, eps)
         assert abs(k - ko) <= 1
@@ -196,12 +201,13 @@ def test_exchange_register_id_shapes(shapes):
         assert err <= 50 * eps
 
 
-def test_exchange_register_id_exact_low_rank_zero_and_full_rank():
+@pytest.mark.parametrize("family", [-3, -4])
+def test_exchange_register_id_exact_low_rank_zero_and_full_rank(family):
     rng = np.random.default_rng(8)
     Y1 = rng.standard_normal((200, 9)) @ rng.standard_normal((9, 500))
     Y2 = np.zeros((64, 80))
     Y3 = rng.standard_normal((96, 40))  # full column rank: k = m, no X
-    res = _run_ids([Y1, Y2, Y3], 1e-5, 1, -3)
+    res = _run_ids([Y1, Y2, Y3], 1e-5, 1, family)
     k, piv, Xg = res[0]
     assert k == 9
     U = np.zeros((500, 9))
