@@ -518,32 +518,44 @@ def _sample_subprocess(threads, depth=None):
     return json.loads(out.stdout.strip().splitlines()[-1])[0]
 
 
-def _sample_text(cal, t_ms, extra=""):
-    from oracle import bench_sample as S
-    if cal is None:
-        return (f"oracle (numpy FP64) on the depth-{S.SAMPLE_DEPTH} subtree of the 64^3 elimination tree "
-                f"({t_ms:.0f} ms); no calibration record, so value is the unscaled sample time")
-    return (f"oracle (numpy FP64) factorization of the depth-{cal['sample_depth']} subtree of the 64^3 "
-            f"elimination tree ({cal['sample_fronts']} fronts, {cal['sample_hss_fronts']} HSS) plus one "
-            f"solve sweep over it: {t_ms:.0f} ms{extra}; scaled by {cal['ratio']:.1f} = whole oracle run "
-            f"({cal['full_s']:.0f} s: factor + {cal['iterations']} GMRES iterations, rel. residual "
-            f"{cal['relres']:.1e}) / the same sample ({cal['sample_s']:.1f} s), both measured back to back on "
-            f"{cal['machine']['machine']} x{cal['machine']['cpus']} "
+def _scale(cal, depth):
+    """Whole oracle run / one sample of this depth, both timed on the
+    calibration machine (None without a record)."""
+    try:
+        return float(cal["samples"][str(depth)]["ratio"])
+    except (TypeError, KeyError, ValueError):
+        return None
+
+
+def _sample_text(cal, depth, t_ms, extra=""):
+    scale = _scale(cal, depth)
+    if scale is None:
+        return (f"oracle (numpy FP64) on the depth-{depth} subtree of the 64^3 elimination tree ({t_ms:.0f} ms); "
+                f"no calibration record, so value is the unscaled sample time")
+    smp = cal["samples"][str(depth)]
+    return (f"oracle (numpy FP64) factorization of the depth-{depth} subtree of the 64^3 elimination tree "
+            f"({smp['fronts']} fronts, {smp['hss_fronts']} HSS) plus one solve sweep over it: {t_ms:.0f} ms{extra}; "
+            f"scaled by {scale:.1f} = whole oracle run ({cal['full_s']:.0f} s: factor + {cal['iterations']} GMRES "
+            f"iterations, rel. residual {cal['relres']:.1e}) / the same sample ({smp['seconds']:.2f} s), both "
+            f"measured back to back on {cal['machine']['machine']} x{cal['machine']['cpus']} "
             f"(oracle/poisson64_calibration.json, written by oracle/bench_sample.py)")
 
 
 def cpu_baseline():
     """The oracle on a bounded sample of the same workload (all cores, then
     one thread), scaled to the whole factor + GMRES by the calibration."""
+    from oracle import bench_sample as S
     cal = _calibration()
+    depth = S.BASELINE_DEPTH
     n = _cores()
-    t_all = sorted(_sample_subprocess(n) for _ in range(2))[0]
-    t_one = _sample_subprocess(1)
-    scale = cal["ratio"] if cal else 1.0
-    return {"value": round(t_all * 1e3 * scale, 1), "unit": "ms", "cores": n, "kind": "oracle",
-            "sample": _sample_text(cal, t_all * 1e3, f" on {n} BLAS threads ({t_one * 1e3:.0f} ms on 1)"),
+    t_all = sorted(_sample_subprocess(n, depth) for _ in range(2))[0]
+    t_one = _sample_subprocess(1, depth)
+    scale = _scale(cal, depth)
+    k = scale if scale is not None else 1.0
+    return {"value": round(t_all * 1e3 * k, 1), "unit": "ms", "cores": n, "kind": "oracle",
+            "sample": _sample_text(cal, depth, t_all * 1e3, f" on {n} BLAS threads ({t_one * 1e3:.0f} ms on 1)"),
             "sample_ms": round(t_all * 1e3, 1), "sample_ms_1thread": round(t_one * 1e3, 1),
-            "value_1thread": round(t_one * 1e3 * scale, 1), "scale": round(scale, 2) if cal else None}
+            "value_1thread": round(t_one * 1e3 * k, 1), "scale": None if scale is None else round(scale, 2)}
 
 
 def run_reference(args):
@@ -559,10 +571,11 @@ def run_reference(args):
     for _ in range(args.warmup):  # untimed: a leaf front of the same tree
         S.sample_step(9, A, b)
     times = [S.sample_step(S.SAMPLE_DEPTH, A, b)[0] * 1e3 for _ in range(args.steps)]
-    t_one = _sample_subprocess(1)
+    t_one = _sample_subprocess(1, S.SAMPLE_DEPTH)
     ms = float(np.median(times)) if times else float("nan")
-    scale = cal["ratio"] if cal else 1.0
-    value = ms * scale
+    scale = _scale(cal, S.SAMPLE_DEPTH)
+    k = scale if scale is not None else 1.0
+    value = ms * k
     threads = _blas_threads()
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
@@ -574,11 +587,11 @@ def run_reference(args):
             "value_note": ("value = projected time of the whole factor + solve (the metric); ms_per_step = the "
                            "measured time of one sample step"),
             "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": threads, "kind": "oracle",
-                             "sample": _sample_text(cal, ms, f" on {threads} BLAS threads (median of "
-                                                              f"{len(times)}; {t_one * 1e3:.0f} ms on 1)"),
+                             "sample": _sample_text(cal, S.SAMPLE_DEPTH, ms, f" on {threads} BLAS threads (median "
+                                                    f"of {len(times)}; {t_one * 1e3:.0f} ms on 1)"),
                              "sample_ms": round(ms, 1), "sample_ms_1thread": round(t_one * 1e3, 1),
-                             "value_1thread": round(t_one * 1e3 * scale, 1),
-                             "scale": round(scale, 2) if cal else None},
+                             "value_1thread": round(t_one * 1e3 * k, 1),
+                             "scale": None if scale is None else round(scale, 2)},
             "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

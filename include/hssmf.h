@@ -231,6 +231,28 @@ int hssmf_get_id_trace(const hssmf_ctx* ctx, int* rec, int max_records);
  * returns the number available, or -1 for a NULL context. */
 int hssmf_get_id_launch_trace(const hssmf_ctx* ctx, double* rec, int max_records);
 
+/* Autotuner of the dense fronts (the paper has no counterpart; it replaces
+ * the task scheduling of Section 5 for batched levels).  The dense fronts of
+ * every elimination-tree level are split by size: the larger ones take the
+ * blocked panel LU (assembly tiles, 32-column panels, batched GEMMs), the
+ * others one persistent launch whose CTAs take fronts from a work queue and
+ * assemble and factor each in shared memory.  With autotuning on (the
+ * default), the first factorization after an analysis times every distinct
+ * split of each level among a fixed set of size bounds, with 128 or 256
+ * threads per CTA, and keeps the fastest; later factorizations reuse it.
+ * Off: levels not tuned yet keep the default split (every front that fits
+ * the shared memory takes the persistent kernel, 256 threads); splits
+ * already chosen are kept until the next analysis. */
+hssmf_status hssmf_set_autotune(hssmf_ctx* ctx, int on);
+
+/* The split chosen per elimination-tree level (bottom level first): 6 ints
+ * per level -- dense fronts, fronts on the panel path (the largest), size
+ * bound of the persistent kernel, its threads per CTA, 1 if tuned by timed
+ * trials, the tuned level's time in microseconds.  Copies at most
+ * max_levels records into rec (host, may be NULL) and returns the number of
+ * levels, or -1 for a NULL context. */
+int hssmf_get_tuning(const hssmf_ctx* ctx, int* rec, int max_levels);
+
 /* Kernel-level entry point: a batch of interpolative decompositions
  * (Section 2.2, ID definitions; rank rule of Section 5.3).  Job j selects
  * columns of Y_j (d_j x m_j, column-major, leading dimension d_j, device

@@ -31,7 +31,8 @@ from . import multifrontal as mf
 DIMS = (64, 64, 64)
 OPTS = dict(hss_tol=1e-4, d0=128, dd=64, hss_min_front=1024, hss_leaf=128, seed=0)
 RHS_SEED = 1
-SAMPLE_DEPTH = 6  # 15 fronts: a 16 x 16 x 8 box's subtree, one HSS front
+SAMPLE_DEPTH = 6  # a reference-arm step: 15 fronts (a 16 x 16 x 8 box's subtree), one HSS front
+BASELINE_DEPTH = 5  # the CPU baseline of a benchmark line: 31 fronts, three HSS fronts
 CALIBRATION = os.path.join(os.path.dirname(os.path.abspath(__file__)), "poisson64_calibration.json")
 
 
@@ -79,14 +80,15 @@ def machine():
 def calibrate(path=CALIBRATION, reps=3):
     A, b = _problem()
     tf, ts, its, rel, hs = full_run(A, b)
-    samples = [sample_step(SAMPLE_DEPTH, A, b) for _ in range(reps)]
-    t_sample = float(np.median([s[0] for s in samples]))
     rec = {"workload": "64^3 Poisson, HSS fronts >= 1024, eps 1e-4, d0 128, dd 64, GMRES(30) to 1e-10",
            "full_factor_s": tf, "full_solve_s": ts, "full_s": tf + ts, "iterations": int(its),
            "relres": float(rel), "hss_fronts": len(hs), "max_rank": max(r for _, _, r, _, _ in hs),
-           "sample_depth": SAMPLE_DEPTH, "sample_fronts": samples[0][1], "sample_hss_fronts": samples[0][2],
-           "sample_s": t_sample, "ratio": (tf + ts) / t_sample, "machine": machine(),
-           "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+           "samples": {}, "machine": machine(), "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    for depth in (SAMPLE_DEPTH, BASELINE_DEPTH):
+        runs = [sample_step(depth, A, b) for _ in range(reps)]
+        t = float(np.median([r[0] for r in runs]))
+        rec["samples"][str(depth)] = {"fronts": runs[0][1], "hss_fronts": runs[0][2], "seconds": t,
+                                      "ratio": (tf + ts) / t}
     with open(path, "w") as fh:
         json.dump(rec, fh, indent=1)
     return rec

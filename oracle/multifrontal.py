@@ -148,6 +148,8 @@ def _factor_ordered(perm, fronts, Anew, opts, t0, only=None):
     fz.data = [None] * len(fronts)
     pos = {}
     for i, f in enumerate(fronts):
+        if only is not None and i not in only:
+            continue  # (a partial factorization needs only its own fronts' maps)
         for c in f.children:
             pos[c] = ordering.child_positions(fronts, c)
     for i, f in enumerate(fronts):

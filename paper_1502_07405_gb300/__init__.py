@@ -90,6 +90,10 @@ lib.hssmf_pattern_grad.restype = C.c_int
 lib.hssmf_get_id_trace.restype = C.c_int
 lib.hssmf_get_id_launch_trace.argtypes = [_P, C.POINTER(C.c_double), _I]
 lib.hssmf_get_id_launch_trace.restype = C.c_int
+lib.hssmf_set_autotune.argtypes = [_P, _I]
+lib.hssmf_set_autotune.restype = C.c_int
+lib.hssmf_get_tuning.argtypes = [_P, _IP, _I]
+lib.hssmf_get_tuning.restype = C.c_int
 lib.hssmf_last_error.argtypes = [_P]
 lib.hssmf_last_error.restype = C.c_char_p
 lib.hssmf_destroy.argtypes = [_P]
@@ -271,6 +275,21 @@ class Solver:
         buf = np.zeros((max(n, 0), len(self.ID_TRACE_FIELDS)), dtype=np.int32)
         if n > 0:
             lib.hssmf_get_id_trace(self._h, _int_ptr(buf), n)
+        return buf
+
+    TUNING_FIELDS = ("dense_fronts", "panel_fronts", "bound", "threads", "tuned", "us")
+
+    def set_autotune(self, on=True):
+        self._check(lib.hssmf_set_autotune(self._h, int(bool(on))))
+
+    def get_tuning(self):
+        """Per-level split of the dense fronts between the panel path and the
+        persistent kernel, a (levels x 6) int array with columns
+        TUNING_FIELDS."""
+        n = lib.hssmf_get_tuning(self._h, None, 0)
+        buf = np.zeros((max(n, 0), 6), dtype=np.int32)
+        if n > 0:
+            lib.hssmf_get_tuning(self._h, _int_ptr(buf), n)
         return buf
 
     ID_LAUNCH_FIELDS = ("kernel", "ctas", "jobs", "max_d", "max_m", "ms")

@@ -41,6 +41,7 @@ struct Tile {  // one output tile of one job (64 x 64 SIMT, 128 x 128 tensor cor
 };
 
 constexpr int GEMM_TILE = 64;
+constexpr size_t kFrontLuSmemMax = 200 * 1024;  // shared memory of the persistent front kernel
 constexpr int GEMM_TILE_TC = 128;
 constexpr int GEMV_MAX_N = 4;  // products with N <= this use the GEMV kernel
 // rows per GEMV tile: op(A) = A / op(A) = A^T

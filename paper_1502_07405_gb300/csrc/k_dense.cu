@@ -1,6 +1,7 @@
 // Dense-front kernels: batched GEMM, front assembly by extend-add
 // (Section 3.2, eq. extend-add), blocked partial LU with row partial
 // pivoting restricted to F11 (Section 3.2).
+#include <algorithm>
 #include <cfloat>
 
 #include "kernels.h"
@@ -334,6 +335,161 @@ void Kern<T>::panel_trsm(const DevSym& ds, T* arena, const int* flist, int nfr, 
   dim3 g(nfr, max_chunks);  // fronts on x (no 65535 limit)
   k_panel_trsm<T><<<g, 128, 0, s>>>(ds.fronts, arena, flist, k0, nb);
   count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent per-level factorization of the small dense fronts (Section 3.2):
+// a work queue over the level's fronts (largest first, an atomic counter);
+// the CTA that takes a front assembles it in shared memory (extend-add of
+// the children's update matrices in child order, then the entries of A_i,
+// as k_assemble), factors F11 by the blocked partial LU with row pivoting
+// inside F11 (first maximum of |a| wins, full-row swaps; L21, U12 and the
+// update F22 - L21 U12 come out in place), and writes the front back.  One
+// launch covers every front with nf <= the level's shared-memory bound.
+// ---------------------------------------------------------------------------
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_front_lu(const DFront* __restrict__ fr, const int* __restrict__ ints,
+                                                  T* __restrict__ ar, const double* __restrict__ values,
+                                                  int* __restrict__ piv, const int* __restrict__ flist, int nfr,
+                                                  int* __restrict__ counter, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char fl_smem[];
+  T* Fs = reinterpret_cast<T*>(fl_smem);
+  __shared__ T s_val[NT / 32];
+  __shared__ int s_idx[NT / 32];
+  __shared__ int s_front, s_p;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) s_front = atomicAdd(counter, 1);
+    __syncthreads();
+    const int q = s_front;
+    if (q >= nfr) break;
+    const DFront f = fr[flist[q]];
+    const int nf = f.nf, ns = f.ns;
+    // assembly
+    for (int e = threadIdx.x; e < nf * nf; e += NT) {
+      const int r = e % nf, c = e / nf;
+      T v = T(0);
+      for (int k = 0; k < f.nchild; ++k) {
+        const DFront ch = fr[k == 0 ? f.child0 : f.child1];
+        const int* inv = ints + f.inv_off + (long long)k * nf;
+        const int ir = inv[r], ic = inv[c];
+        if (ir >= 0 && ic >= 0) v += ar[ch.u_off + ir + (long long)ic * ch.u_ld];
+      }
+      Fs[e] = v;
+    }
+    __syncthreads();
+    {
+      const int* arow = ints + f.arow_off;
+      const int nnz_f = arow[nf];
+      const int* acol = arow + nf + 1;
+      const int* aval = acol + nnz_f;
+      for (int r = threadIdx.x; r < nf; r += NT)  // one thread per row: the row's entries in CSR order
+        for (int p = arow[r]; p < arow[r + 1]; ++p) Fs[r + acol[p] * nf] += T(values[aval[p]]);
+    }
+    __syncthreads();
+    // the blocked partial LU of the panel path (32-column panels: panel LU,
+    // U12 rows by forward substitution, trailing update with the panel's
+    // products summed first), in the same operation order, so that either
+    // path gives the same factors bit for bit
+    for (int k0 = 0; k0 < ns; k0 += 32) {
+      const int k1 = min(k0 + 32, ns), w = k1 - k0;
+      for (int j = k0; j < k1; ++j) {
+        T best = T(-1);
+        int bi = ns;
+        for (int r = j + threadIdx.x; r < ns; r += NT) {
+          const T a = tabs(Fs[r + j * nf]);
+          if (a > best) { best = a; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const T ob = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          T b = s_val[0];
+          int i = s_idx[0];
+          for (int w2 = 1; w2 < NT / 32; ++w2)
+            if (s_val[w2] > b || (s_val[w2] == b && s_idx[w2] < i)) { b = s_val[w2]; i = s_idx[w2]; }
+          if (!(b > T(0)) || !isfinite((double)b)) {
+            set_status(status, b == T(0) ? ST_ZERO_PIVOT : ST_NONFINITE);
+            i = j;
+          }
+          s_p = i;
+          piv[f.piv_off + j] = i;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != j)
+          for (int c = threadIdx.x; c < nf; c += NT) {
+            const T t = Fs[j + c * nf];
+            Fs[j + c * nf] = Fs[p + c * nf];
+            Fs[p + c * nf] = t;
+          }
+        __syncthreads();
+        const T d = Fs[j + j * nf];
+        const T inv = (d != T(0)) ? T(1) / d : T(0);
+        for (int r = j + 1 + threadIdx.x; r < nf; r += NT) {
+          const T l = Fs[r + j * nf] * inv;
+          Fs[r + j * nf] = l;
+          for (int c = j + 1; c < k1; ++c) Fs[r + c * nf] -= l * Fs[j + c * nf];
+        }
+        __syncthreads();
+      }
+      // rows k0..k1-1 of the columns right of the panel: L_panel^-1 times them
+      for (int c = k1 + threadIdx.x; c < nf; c += NT) {
+        T x[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] = i < w ? Fs[(k0 + i) + c * nf] : T(0);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const T xi = x[i];
+#pragma unroll
+          for (int r = i + 1; r < 32; ++r) x[r] -= (r < w && i < w ? Fs[(k0 + r) + (k0 + i) * nf] : T(0)) * xi;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < w) Fs[(k0 + i) + c * nf] = x[i];
+      }
+      __syncthreads();
+      // trailing update: F22 block -= sum over the panel columns, summed first
+      const int m1 = nf - k1;
+      for (int e = threadIdx.x; e < m1 * m1; e += NT) {
+        const int r = k1 + e % m1, c = k1 + e / m1;
+        T acc = T(0);
+        for (int k = 0; k < w; ++k) acc += Fs[r + (k0 + k) * nf] * Fs[(k0 + k) + c * nf];
+        Fs[r + c * nf] = T(-1) * acc + T(1) * Fs[r + c * nf];
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nf * nf; e += NT) ar[f.off + e] = Fs[e];
+    __syncthreads();  // Fs and s_front are reused by the next front
+  }
+}
+
+template <typename T>
+int Kern<T>::front_lu(const DevSym& ds, T* arena, const double* values, int* piv, const int* flist, int nfr,
+                      int max_nf, int threads, int nsm, int* counter, unsigned* status, cudaStream_t s) {
+  if (nfr <= 0) return 0;
+  const size_t smem = sizeof(T) * (size_t)max_nf * max_nf;
+  if (smem > kFrontLuSmemMax || nsm <= 0) return -1;
+  const void* kern = threads == 128 ? (const void*)k_front_lu<T, 128> : (const void*)k_front_lu<T, 256>;
+  if (!set_func_attr(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFrontLuSmemMax)) return -1;
+  // a persistent grid: every CTA that can be resident at once, at most one per front
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    return -1;
+  }
+  const int grid = (int)std::min<long long>(nfr, (long long)nsm * occ);
+  if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess) return -1;
+  if (threads == 128)
+    k_front_lu<T, 128><<<grid, 128, smem, s>>>(ds.fronts, ds.ints, arena, values, piv, flist, nfr, counter, status);
+  else
+    k_front_lu<T, 256><<<grid, 256, smem, s>>>(ds.fronts, ds.ints, arena, values, piv, flist, nfr, counter, status);
+  count_launch();
+  return 0;
 }
 
 template struct Kern<double>;

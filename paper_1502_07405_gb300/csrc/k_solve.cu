@@ -1,6 +1,8 @@
 // Multifrontal solve kernels for dense fronts (Section 3.3) and the FP64
 // kernels of the outer iteration (sparse product, GMRES(30) with modified
 // Gram-Schmidt, iterative refinement; Sections 4.6 and 6.1).
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace hssmf {
@@ -229,11 +231,254 @@ static bool warp_cols_fit(int max_nf, int nrhs) {
   return nrhs >= 4 && max_nf > 0 && (size_t)WC_WARPS * max_nf * sizeof(T) <= kWarpColSmem;
 }
 
+// ---------------------------------------------------------------------------
+// Blocked sweeps of the dense fronts: the triangular factors in 32 x 32
+// diagonal blocks (solved by one warp per right-hand side from a shared-
+// memory copy of the block), each followed by the update of the remaining
+// rows (or columns) with the block's 32 columns (rows): a product read once
+// with coalesced loads, so the sweep is bound by reading the factor, not by
+// one dependent step per column.  A CTA takes nc <= 8 right-hand sides of a
+// front, staged in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int BLK_NC = 8;
+constexpr size_t kBlkSolveSmem = 192 * 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_solve_fwd_blk(const DFront* __restrict__ fr, const T* __restrict__ ar,
+                                                       const int* __restrict__ piv, T* __restrict__ W,
+                                                       const int* __restrict__ flist, int nrhs, int nc_max,
+                                                       int max_nf, int transpose) {
+  const DFront f = fr[flist[blockIdx.x]];
+  if (f.is_hss) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int j0 = blockIdx.y * nc_max, nc = min(nc_max, nrhs - j0);
+  if (nc <= 0) return;
+  extern __shared__ __align__(16) unsigned char blk_raw[];
+  T* xs = reinterpret_cast<T*>(blk_raw);  // nc x max_nf
+  __shared__ T B[32][33];
+  const T* F = ar + f.off;
+  const long long ld = f.nf;
+  const int nf = f.nf, ns = f.ns;
+  T* w = W + f.w_off + (long long)j0 * nf;
+  for (int e = threadIdx.x; e < nc * nf; e += blockDim.x) xs[(e / nf) * max_nf + e % nf] = w[e];
+  __syncthreads();
+  if (!transpose && threadIdx.x < nc) {  // P b_s, one thread per column
+    T* x = xs + threadIdx.x * max_nf;
+    for (int i = 0; i < ns; ++i) {
+      const int p = piv[f.piv_off + i];
+      if (p != i) { const T t = x[i]; x[i] = x[p]; x[p] = t; }
+    }
+  }
+  __syncthreads();
+  for (int cb = 0; cb < ns; cb += 32) {
+    const int cw = min(32, ns - cb);
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      const int t = e & 31, k = e >> 5;
+      B[t][k] = (t < cw && k < cw) ? F[(cb + t) + (long long)(cb + k) * ld] : T(0);
+    }
+    __syncthreads();
+    if (wid < nc) {
+      T* x = xs + wid * max_nf + cb;
+      T v = lane < cw ? x[lane] : T(0);
+      if (!transpose) {  // unit lower: x_t -= L(t, k) x_k
+        for (int k = 0; k < cw; ++k) {
+          const T xk = __shfl_sync(0xffffffffu, v, k);
+          if (lane > k) v -= B[lane][k] * xk;
+        }
+      } else {  // U^T (lower): y_k = x_k / U(k, k), then x_t -= U(k, t) y_k
+        for (int k = 0; k < cw; ++k) {
+          const T yk = __shfl_sync(0xffffffffu, v, k) / B[k][k];
+          if (lane == k) v = yk;
+          if (lane > k) v -= B[k][lane] * yk;
+        }
+      }
+      if (lane < cw) x[lane] = v;
+    }
+    __syncthreads();
+    if (!transpose) {  // rows below the block: x_r -= L(r, block) x_block (also b_u -= L21 y)
+      for (int r = cb + cw + threadIdx.x; r < nf; r += blockDim.x) {
+        T acc[BLK_NC];
+#pragma unroll
+        for (int q = 0; q < BLK_NC; ++q) acc[q] = T(0);
+        for (int k = 0; k < cw; ++k) {
+          const T l = F[r + (long long)(cb + k) * ld];
+#pragma unroll
+          for (int q = 0; q < BLK_NC; ++q)
+            if (q < nc) acc[q] += l * xs[q * max_nf + cb + k];
+        }
+#pragma unroll
+        for (int q = 0; q < BLK_NC; ++q)
+          if (q < nc) xs[q * max_nf + r] -= acc[q];
+      }
+    } else {  // columns right of the block: x_c -= U(block, c)^T y_block (also b_u -= U12^T y)
+      for (int c = cb + cw + threadIdx.x; c < nf; c += blockDim.x) {
+        T acc[BLK_NC];
+#pragma unroll
+        for (int q = 0; q < BLK_NC; ++q) acc[q] = T(0);
+        const T* Fc = F + (long long)c * ld + cb;
+        for (int k = 0; k < cw; ++k) {
+          const T u = Fc[k];
+#pragma unroll
+          for (int q = 0; q < BLK_NC; ++q)
+            if (q < nc) acc[q] += u * xs[q * max_nf + cb + k];
+        }
+#pragma unroll
+        for (int q = 0; q < BLK_NC; ++q)
+          if (q < nc) xs[q * max_nf + c] -= acc[q];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nc * nf; e += blockDim.x) w[e] = xs[(e / nf) * max_nf + e % nf];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_solve_bwd_blk(const DFront* __restrict__ fr, const T* __restrict__ ar,
+                                                       const int* __restrict__ piv, T* __restrict__ W,
+                                                       T* __restrict__ xp, const int* __restrict__ flist, int n,
+                                                       int nrhs, int nc_max, int max_nf, int transpose) {
+  const DFront f = fr[flist[blockIdx.x]];
+  if (f.is_hss) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int j0 = blockIdx.y * nc_max, nc = min(nc_max, nrhs - j0);
+  if (nc <= 0) return;
+  extern __shared__ __align__(16) unsigned char blk_raw[];
+  T* xs = reinterpret_cast<T*>(blk_raw);  // nc x max_nf
+  __shared__ T B[32][33];
+  const T* F = ar + f.off;
+  const long long ld = f.nf;
+  const int nf = f.nf, ns = f.ns;
+  const T* w = W + f.w_off + (long long)j0 * nf;
+  for (int e = threadIdx.x; e < nc * nf; e += blockDim.x) xs[(e / nf) * max_nf + e % nf] = w[e];
+  __syncthreads();
+  if (!transpose) {  // y -= U12 x_u, thread per row
+    for (int r = threadIdx.x; r < ns; r += blockDim.x) {
+      T acc[BLK_NC];
+#pragma unroll
+      for (int q = 0; q < BLK_NC; ++q) acc[q] = T(0);
+      for (int c = ns; c < nf; ++c) {
+        const T u = F[r + (long long)c * ld];
+#pragma unroll
+        for (int q = 0; q < BLK_NC; ++q)
+          if (q < nc) acc[q] += u * xs[q * max_nf + c];
+      }
+#pragma unroll
+      for (int q = 0; q < BLK_NC; ++q)
+        if (q < nc) xs[q * max_nf + r] -= acc[q];
+    }
+  } else {  // y -= L21^T x_u, warp per row of the result (column of L21)
+    for (int r = wid; r < ns; r += blockDim.x >> 5) {
+      const T* Fr = F + (long long)r * ld;
+      T acc[BLK_NC];
+#pragma unroll
+      for (int q = 0; q < BLK_NC; ++q) acc[q] = T(0);
+      for (int c = ns + lane; c < nf; c += 32) {
+        const T l = Fr[c];
+#pragma unroll
+        for (int q = 0; q < BLK_NC; ++q)
+          if (q < nc) acc[q] += l * xs[q * max_nf + c];
+      }
+#pragma unroll
+      for (int q = 0; q < BLK_NC; ++q) {
+        if (q >= nc) break;
+        const T sum = warp_allsum(acc[q]);
+        if (lane == 0) xs[q * max_nf + r] -= sum;
+      }
+    }
+  }
+  __syncthreads();
+  for (int cb = ((ns - 1) / 32) * 32; cb >= 0 && ns > 0; cb -= 32) {
+    const int cw = min(32, ns - cb);
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      const int t = e & 31, k = e >> 5;
+      B[t][k] = (t < cw && k < cw) ? F[(cb + t) + (long long)(cb + k) * ld] : T(0);
+    }
+    __syncthreads();
+    if (wid < nc) {
+      T* x = xs + wid * max_nf + cb;
+      T v = lane < cw ? x[lane] : T(0);
+      if (!transpose) {  // U11: x_k = x_k / U(k, k), then x_t -= U(t, k) x_k
+        for (int k = cw - 1; k >= 0; --k) {
+          const T xk = __shfl_sync(0xffffffffu, v, k) / B[k][k];
+          if (lane == k) v = xk;
+          if (lane < k) v -= B[lane][k] * xk;
+        }
+      } else {  // L11^T (unit upper): x_t -= L(k, t) x_k
+        for (int k = cw - 1; k >= 0; --k) {
+          const T xk = __shfl_sync(0xffffffffu, v, k);
+          if (lane < k) v -= B[k][lane] * xk;
+        }
+      }
+      if (lane < cw) x[lane] = v;
+    }
+    __syncthreads();
+    if (!transpose) {  // rows above the block: x_r -= U(r, block) x_block
+      for (int r = threadIdx.x; r < cb; r += blockDim.x) {
+        T acc[BLK_NC];
+#pragma unroll
+        for (int q = 0; q < BLK_NC; ++q) acc[q] = T(0);
+        for (int k = 0; k < cw; ++k) {
+          const T u = F[r + (long long)(cb + k) * ld];
+#pragma unroll
+          for (int q = 0; q < BLK_NC; ++q)
+            if (q < nc) acc[q] += u * xs[q * max_nf + cb + k];
+        }
+#pragma unroll
+        for (int q = 0; q < BLK_NC; ++q)
+          if (q < nc) xs[q * max_nf + r] -= acc[q];
+      }
+    } else {  // columns left of the block: x_c -= L(block, c)^T x_block
+      for (int c = threadIdx.x; c < cb; c += blockDim.x) {
+        T acc[BLK_NC];
+#pragma unroll
+        for (int q = 0; q < BLK_NC; ++q) acc[q] = T(0);
+        const T* Fc = F + (long long)c * ld + cb;
+        for (int k = 0; k < cw; ++k) {
+          const T l = Fc[k];
+#pragma unroll
+          for (int q = 0; q < BLK_NC; ++q)
+            if (q < nc) acc[q] += l * xs[q * max_nf + cb + k];
+        }
+#pragma unroll
+        for (int q = 0; q < BLK_NC; ++q)
+          if (q < nc) xs[q * max_nf + c] -= acc[q];
+      }
+    }
+    __syncthreads();
+  }
+  if (transpose && threadIdx.x < nc) {  // P^T
+    T* x = xs + threadIdx.x * max_nf;
+    for (int i = ns - 1; i >= 0; --i) {
+      const int p = piv[f.piv_off + i];
+      if (p != i) { const T t = x[i]; x[i] = x[p]; x[p] = t; }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nc * ns; e += blockDim.x) {
+    const int q = e / ns, r = e % ns;
+    xp[f.sep_begin + r + (long long)(j0 + q) * n] = xs[q * max_nf + r];
+  }
+}
+
+// right-hand sides per CTA of the blocked sweeps (0: the front does not fit)
+template <typename T>
+static int blk_cols(int max_nf, int nrhs) {
+  if (max_nf <= 0) return 0;
+  const int nc = (int)std::min<size_t>(BLK_NC, kBlkSolveSmem / ((size_t)max_nf * sizeof(T)));
+  return std::min(nc, std::max(nrhs, 1));
+}
+
 template <typename T>
 void Kern<T>::solve_fwd_dense(const DevSym& ds, const T* arena, const int* piv, T* W,
                               const int* flist, int nfr, int max_nf, int nrhs, int transpose, cudaStream_t s) {
   if (nfr <= 0) return;
-  if (warp_cols_fit<T>(max_nf, nrhs)) {
+  const int nc = blk_cols<T>(max_nf, nrhs);
+  if (nc > 0) {
+    set_func_attr((const void*)k_solve_fwd_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSolveSmem);
+    const size_t smem = (size_t)nc * max_nf * sizeof(T);
+    k_solve_fwd_blk<T><<<dim3(nfr, (nrhs + nc - 1) / nc), 256, smem, s>>>(ds.fronts, arena, piv, W, flist, nrhs, nc,
+                                                                         max_nf, transpose);
+  } else if (warp_cols_fit<T>(max_nf, nrhs)) {
     set_func_attr((const void*)k_solve_fwd_dense_wc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpColSmem);
     const size_t smem = (size_t)WC_WARPS * max_nf * sizeof(T);
     k_solve_fwd_dense_wc<T><<<dim3(nfr, (nrhs + WC_WARPS - 1) / WC_WARPS), 256, smem, s>>>(
@@ -395,7 +640,13 @@ template <typename T>
 void Kern<T>::solve_bwd_dense(const DevSym& ds, const T* arena, const int* piv, T* W, T* xp,
                               const int* flist, int nfr, int max_nf, int nrhs, int transpose, cudaStream_t s) {
   if (nfr <= 0) return;
-  if (warp_cols_fit<T>(max_nf, nrhs)) {
+  const int nc = blk_cols<T>(max_nf, nrhs);
+  if (nc > 0) {
+    set_func_attr((const void*)k_solve_bwd_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSolveSmem);
+    const size_t smem = (size_t)nc * max_nf * sizeof(T);
+    k_solve_bwd_blk<T><<<dim3(nfr, (nrhs + nc - 1) / nc), 256, smem, s>>>(ds.fronts, arena, piv, W, xp, flist, ds.n,
+                                                                         nrhs, nc, max_nf, transpose);
+  } else if (warp_cols_fit<T>(max_nf, nrhs)) {
     set_func_attr((const void*)k_solve_bwd_dense_wc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpColSmem);
     const size_t smem = (size_t)WC_WARPS * max_nf * sizeof(T);
     k_solve_bwd_dense_wc<T><<<dim3(nfr, (nrhs + WC_WARPS - 1) / WC_WARPS), 256, smem, s>>>(

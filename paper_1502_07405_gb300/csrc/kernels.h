@@ -65,6 +65,12 @@ struct Kern {
                        int nb, unsigned* status, cudaStream_t s);
   static void panel_trsm(const DevSym& ds, T* arena, const int* flist, int nfr, int k0, int nb,
                          int max_chunks, cudaStream_t s);
+  // persistent assembly + partial LU of the listed fronts (nf <= max_nf, the
+  // front held in shared memory): as many CTAs of `threads` (128 or 256) as
+  // can be resident on the nsm SMs take fronts from the work counter (device
+  // int, reset here); -1 if the front does not fit or the launch is refused
+  static int front_lu(const DevSym& ds, T* arena, const double* values, int* piv, const int* flist, int nfr,
+                      int max_nf, int threads, int nsm, int* counter, unsigned* status, cudaStream_t s);
   // solve --------------------------------------------------------------------
   static void permute_in(const double* b, long long ldb, T* bp, const int* perm, int n, int nrhs,
                          cudaStream_t s);

@@ -200,6 +200,7 @@ hssmf_status hssmf_ctx::build_plan() {
   for (size_t h = 0; h < S.levels.size(); ++h) {
     LevelPlan& L = plan[h];
     for (int f : S.levels[h]) (is_hss[f] ? L.hss : L.dense).push_back(f);
+    std::stable_sort(L.dense.begin(), L.dense.end(), [&](int a, int b) { return fr[a].nf > fr[b].nf; });
     L.all_off = (int)flist.size();
     L.nall = (int)S.levels[h].size();
     for (int f : S.levels[h]) {
@@ -219,20 +220,33 @@ hssmf_status hssmf_ctx::build_plan() {
     for (int f : L.hss) flist.push_back(f);
     // assembly tiles (32 x 32)
     L.asm_off = (int)tiles.size();
+    L.asm_prefix.assign(1, 0);
     for (int f : L.dense) {
       int t = ceil_div(fr[f].nf, 32);
       for (int tn = 0; tn < t; ++tn)
         for (int tm = 0; tm < t; ++tm) tiles.push_back(Tile{f, tm, tn});
+      L.asm_prefix.push_back((int)tiles.size() - L.asm_off);
     }
     L.asm_n = (int)tiles.size() - L.asm_off;
+    // default split: every dense front whose matrix fits the persistent
+    // kernel's shared memory goes to it (the autotuner may move the bound)
+    L.nfmax = (int)std::sqrt((double)kFrontLuSmemMax / (double)esz);
+    L.nlarge = 0;
+    while (L.nlarge < (int)L.dense.size() && fr[L.dense[L.nlarge]].nf > L.nfmax) ++L.nlarge;
     // panel steps
     for (int k0 = 0; k0 < max_ns; k0 += NB) {
       StepPlan sp;
       sp.k0 = k0;
       sp.trsm_chunks = 0;
       sp.tile_off = (int)tiles.size();
+      sp.prefix.assign(1, 0);
       for (int f : L.dense) {
         const DFront& d = fr[f];
+        struct PrefixPush {  // the prefix grows by this front's tiles, however the loop body exits
+          StepPlan& sp;
+          std::vector<Tile>& t;
+          ~PrefixPush() { sp.prefix.push_back((int)t.size() - sp.tile_off); }
+        } pp{sp, tiles};
         if (k0 >= d.ns) continue;
         int k1 = std::min(k0 + NB, d.ns);
         sp.trsm_chunks = std::max(sp.trsm_chunks, ceil_div(d.nf - k1, 128));
@@ -289,6 +303,7 @@ hssmf_status hssmf_ctx::ensure_device() {
   if (!ev0 && (st = cuda_check(cudaEventCreate(&ev0), "event"))) return st;
   if (!ev1 && (st = cuda_check(cudaEventCreate(&ev1), "event"))) return st;
   d_status = (unsigned*)dalloc(sizeof(unsigned) * 4);
+  d_counter = (int*)dalloc(sizeof(int) * 4);
   d_perm = (int*)dalloc(sizeof(int) * n);
   d_rowptr = (int*)dalloc(sizeof(int) * (n + 1));
   d_colind = (int*)dalloc(sizeof(int) * std::max(S.nnz, 1));
@@ -302,7 +317,7 @@ hssmf_status hssmf_ctx::ensure_device() {
   d_arena = dalloc(esz * std::max<long long>(arena_elems, 1));
   d_jobs = (GemmJob*)dalloc(sizeof(GemmJob) * std::max<size_t>(dense_jobs_host.size(), 1));
   d_sysoff = (int*)dalloc(sizeof(int) * (S.sys_off.size() + 1));
-  if (!d_status || !d_perm || !d_rowptr || !d_colind || !d_tpos || !d_values || !d_fronts ||
+  if (!d_status || !d_counter || !d_perm || !d_rowptr || !d_colind || !d_tpos || !d_values || !d_fronts ||
       !d_ints || !d_flist || !d_tiles || !d_piv || !d_arena || !d_jobs || !d_sysoff)
     return fail(HSSMF_ERR_OOM, "device allocation of the factor storage failed");
   std::vector<GemmJob> jobs = dense_jobs_host;
@@ -341,6 +356,90 @@ hssmf_status hssmf_ctx::ensure_device() {
 // Numerical factorization
 // ---------------------------------------------------------------------------
 template <typename T>
+int hssmf_ctx::dense_level(const LevelPlan& L, int nlarge, int nfmax, int threads) {
+  T* ar = static_cast<T*>(d_arena);
+  if (nlarge > 0) {
+    Kern<T>::assemble(ds, ar, d_values, d_tiles + L.asm_off, L.asm_prefix[nlarge], stream);
+    int max_ns = 0;
+    for (int i = 0; i < nlarge; ++i) max_ns = std::max(max_ns, fronts_host[L.dense[i]].ns);
+    for (const StepPlan& sp : L.steps) {
+      if (sp.k0 >= max_ns) break;
+      Kern<T>::panel_lu(ds, ar, d_piv, d_flist + L.dense_off, nlarge, sp.k0, NB, d_status, stream);
+      Kern<T>::panel_trsm(ds, ar, d_flist + L.dense_off, nlarge, sp.k0, NB, sp.trsm_chunks, stream);
+      Kern<T>::gemm(d_jobs, d_tiles + sp.tile_off, sp.prefix[nlarge], stream);  // K = NB: CUDA cores
+    }
+  }
+  if (nlarge < L.ndense) {
+    const int max_nf = fronts_host[L.dense[nlarge]].nf;  // largest first
+    if (max_nf > nfmax) return -1;
+    return Kern<T>::front_lu(ds, ar, d_values, d_piv, d_flist + L.dense_off + nlarge, L.ndense - nlarge, max_nf,
+                             threads, num_sms, d_counter, d_status, stream);
+  }
+  return 0;
+}
+
+// Autotuner of a level's dense fronts (timed trials, once per analysis): the
+// size bound below which fronts take the persistent shared-memory kernel
+// (every distinct split of the level among the candidate bounds, including
+// none) and its threads per CTA (128 or 256).  A level's dense work can be
+// repeated: assembly rebuilds every front from A and the children's update
+// matrices, which it does not modify.
+template <typename T>
+hssmf_status hssmf_ctx::tune_level(LevelPlan& L) {
+  const size_t esz = sizeof(T);
+  const int cap = (int)std::sqrt((double)kFrontLuSmemMax / (double)esz);
+  const int bounds[] = {0, 48, 64, 96, 128, 160, 192, cap};
+  float best = -1.f;
+  int best_nl = L.ndense, best_b = 0, best_t = 256;
+  int last_nl = -1;
+  hssmf_status st;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;  // (the context's events time the whole factorization)
+  if ((st = cuda_check(cudaEventCreate(&t0), "tuning"))) return st;
+  if ((st = cuda_check(cudaEventCreate(&t1), "tuning"))) {
+    cudaEventDestroy(t0);
+    return st;
+  }
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev_guard{t0, t1};
+  for (int b : bounds) {
+    if (b > cap) continue;
+    int nl = 0;
+    while (nl < L.ndense && fronts_host[L.dense[nl]].nf > b) ++nl;
+    if (nl == last_nl) continue;
+    last_nl = nl;
+    for (int t : {128, 256}) {
+      if (nl == L.ndense && t == 128) continue;  // no persistent launch
+      if ((st = cuda_check(cudaEventRecord(t0, stream), "tuning"))) return st;
+      const int r = dense_level<T>(L, nl, b, t);
+      if ((st = cuda_check(cudaEventRecord(t1, stream), "tuning"))) return st;
+      if ((st = cuda_check(cudaEventSynchronize(t1), "tuning"))) return st;
+      float ms = 0.f;
+      if ((st = cuda_check(cudaEventElapsedTime(&ms, t0, t1), "tuning"))) return st;
+      if (r < 0) continue;  // refused configuration
+      if (best < 0.f || ms < best) {
+        best = ms;
+        best_nl = nl;
+        best_b = b;
+        best_t = t;
+      }
+    }
+  }
+  if (best >= 0.f) {
+    L.nlarge = best_nl;
+    L.nfmax = best_b;
+    L.threads = best_t;
+    L.tuned_ms = best;
+  }
+  L.tuned = 1;
+  return HSSMF_OK;
+}
+
+template <typename T>
 hssmf_status hssmf_ctx::factor_impl() {
   T* ar = static_cast<T*>(d_arena);
   hssmf_status st;
@@ -348,14 +447,13 @@ hssmf_status hssmf_ctx::factor_impl() {
   hss_begin_factor(*this);
   for (size_t h = 0; h < plan.size(); ++h) {
     const LevelPlan& L = plan[h];
-    // dense fronts: assembly, then the blocked partial LU
+    // dense fronts: the large ones by assembly and the blocked partial LU,
+    // the others by the persistent shared-memory kernel (split tuned once)
     prof.mark(PH_DENSE, stream);
-    Kern<T>::assemble(ds, ar, d_values, d_tiles + L.asm_off, L.asm_n, stream);
-    for (const StepPlan& sp : L.steps) {
-      Kern<T>::panel_lu(ds, ar, d_piv, d_flist + L.dense_off, L.ndense, sp.k0, NB, d_status, stream);
-      Kern<T>::panel_trsm(ds, ar, d_flist + L.dense_off, L.ndense, sp.k0, NB, sp.trsm_chunks, stream);
-      Kern<T>::gemm(d_jobs, d_tiles + sp.tile_off, sp.ntiles, stream);  // K = NB: CUDA cores
-    }
+    if (autotune && !L.tuned && L.ndense > 0)
+      if ((st = tune_level<T>(plan[h]))) return st;
+    if (dense_level<T>(L, L.nlarge, L.nfmax, L.threads) < 0)
+      return fail(HSSMF_ERR_CUDA, "the persistent dense-front kernel could not be launched");
     for (int f : L.dense) {
       double ns = fronts_host[f].ns, nu = fronts_host[f].nu;
       dense_flops += 2.0 / 3.0 * ns * ns * ns + 2.0 * ns * ns * nu + 2.0 * ns * nu * nu;
@@ -1078,6 +1176,24 @@ int hssmf_get_id_launch_trace(const hssmf_ctx* c, double* rec, int max_records) 
   const int n = (int)(c->id_launch_trace.size() / 6);
   if (rec)
     for (int i = 0; i < std::min(n, max_records) * 6; ++i) rec[i] = c->id_launch_trace[i];
+  return n;
+}
+
+hssmf_status hssmf_set_autotune(hssmf_ctx* c, int on) {
+  if (!c) return HSSMF_ERR_ARG;
+  c->autotune = on != 0;
+  return HSSMF_OK;
+}
+
+int hssmf_get_tuning(const hssmf_ctx* c, int* rec, int max_levels) {
+  if (!c) return -1;
+  const int n = (int)c->plan.size();
+  if (rec)
+    for (int h = 0; h < std::min(n, max_levels); ++h) {
+      const LevelPlan& L = c->plan[h];
+      const int r[6] = {L.ndense, L.nlarge, L.nfmax, L.threads, L.tuned, (int)(L.tuned_ms * 1000.f)};
+      for (int q = 0; q < 6; ++q) rec[6 * h + q] = r[q];
+    }
   return n;
 }
 

@@ -14,14 +14,21 @@ namespace hssmf {
 
 struct StepPlan {  // one panel step of the dense partial LU of a level
   int k0 = 0, trsm_chunks = 0, tile_off = 0, ntiles = 0;
+  std::vector<int> prefix;  // GEMM tiles of the first i dense fronts of the level
 };
 
 struct LevelPlan {
-  std::vector<int> dense, hss;
+  std::vector<int> dense, hss;  // dense fronts largest first
   int all_off = 0, nall = 0, dense_off = 0, ndense = 0, hss_off = 0;
   int max_nf = 0, max_nu = 0, max_nf_dense = 0;
   int asm_off = 0, asm_n = 0;
+  std::vector<int> asm_prefix;  // assembly tiles of the first i dense fronts
   std::vector<StepPlan> steps;
+  // split of the dense fronts: the first nlarge take the blocked panel path,
+  // the others the persistent shared-memory kernel with `threads` threads
+  // (chosen by the autotuner from timed trials, else the default bound)
+  int nlarge = 0, nfmax = 0, threads = 256, tuned = 0;
+  float tuned_ms = 0.f;
 };
 
 struct HssState;  // HSS-front factor data (hss.cu)
@@ -109,6 +116,8 @@ struct hssmf_ctx {
   // device memory owned by the context
   std::vector<void*> owned, owned_host;
   unsigned* d_status = nullptr;
+  int* d_counter = nullptr;  // work queue of the persistent front kernel
+  bool autotune = true;       // time the dense-front splits at the first factorization
   int *d_perm = nullptr, *d_rowptr = nullptr, *d_colind = nullptr, *d_tpos = nullptr;
   double* d_values = nullptr;
   hssmf::DFront* d_fronts = nullptr;
@@ -168,6 +177,7 @@ struct hssmf_ctx {
   void free_all();
   void reset_device_pointers() {
     d_status = nullptr;
+    d_counter = nullptr;
     d_perm = d_rowptr = d_colind = d_tpos = nullptr;
     d_values = nullptr;
     d_fronts = nullptr;
@@ -197,6 +207,10 @@ struct hssmf_ctx {
   hssmf_status ensure_device();
   template <typename T>
   hssmf_status factor_impl();
+  template <typename T>
+  int dense_level(const hssmf::LevelPlan& L, int nlarge, int nfmax, int threads);  // -1: refused
+  template <typename T>
+  hssmf_status tune_level(hssmf::LevelPlan& L);
   template <typename T>
   hssmf_status apply_impl(const double* b, double* x, int nrhs, int transpose);
   hssmf_status apply(const double* b, double* x, int nrhs, int transpose);

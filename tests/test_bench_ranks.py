@@ -93,8 +93,8 @@ import bench
 from oracle import bench_sample as S
 S.SAMPLE_DEPTH = 9
 bench._sample_subprocess = lambda threads, depth=None: 0.25
-bench._calibration = lambda: {{"ratio": 100.0, "sample_depth": 9, "sample_fronts": 1, "sample_hss_fronts": 0,
-    "full_s": 900.0, "iterations": 9, "relres": 1e-11, "sample_s": 9.0, "machine": {{"machine": "x", "cpus": 8}}}}
+bench._calibration = lambda: {{"samples": {{"9": {{"ratio": 100.0, "fronts": 1, "hss_fronts": 0, "seconds": 9.0}}}},
+    "full_s": 900.0, "iterations": 9, "relres": 1e-11, "machine": {{"machine": "x", "cpus": 8}}}}
 class Args:
     steps, warmup = 2, 1
 bench.run_reference(Args())

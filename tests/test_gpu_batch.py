@@ -112,3 +112,48 @@ def test_more_than_65535_fronts_in_one_level():
         m = problems.grid_poisson((side, side, 1), scale=scale[g])
         xs = np.linalg.solve(m.to_scipy().toarray(), b[g * nb:(g + 1) * nb, 0])
         assert np.allclose(x[g * nb:(g + 1) * nb, 0], xs, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_dense_front_split_is_tuned_per_level_and_does_not_change_results(prec):
+    """The autotuner times every distinct split of each level's dense fronts
+    between the blocked panel path and the persistent shared-memory kernel
+    and keeps the fastest; the persistent kernel repeats the panel path's
+    operations in the same order, so every split gives the same solution
+    bit for bit (here: tuned, untuned and a 3D grid whose largest fronts
+    exceed the persistent kernel's bound)."""
+    import paper_1502_07405_gb300 as P
+    mats, A = _batch()
+    b = problems.rhs_uniform(A.n, 3, 2)
+    xs = []
+    for tune in (True, False):
+        s = _solver(maxit=0, precision=prec, **KW)
+        s.set_autotune(tune)
+        s.analyze_grids([(k, k, 1) for k, _ in GRIDS], A.rowptr, A.colind)
+        s.factor(A.values)
+        tun = s.get_tuning()
+        F = P.Solver.TUNING_FIELDS
+        assert tun.shape[1] == len(F) and tun.shape[0] == s.get_stats()["n_levels"]
+        has_dense = tun[:, F.index("dense_fronts")] > 0
+        assert (tun[has_dense, F.index("tuned")] == (1 if tune else 0)).all()
+        assert (tun[:, F.index("panel_fronts")] <= tun[:, F.index("dense_fronts")]).all()
+        xs.append(s.solve(b))
+        s.close()
+    np.testing.assert_array_equal(xs[0], xs[1])
+    dims = (20, 20, 20)  # 3D: the top fronts take the panel path in every split
+    G = problems.grid_poisson(dims)
+    bg = problems.rhs_uniform(G.n, 1, 3)
+    out = []
+    for tune in (True, False):
+        s = _solver(maxit=0, precision=prec, hss_min_front=1 << 30)
+        s.set_autotune(tune)
+        s.analyze_grid(dims, G.rowptr, G.colind)
+        s.factor(G.values)
+        tun = s.get_tuning()
+        assert tun[:, P.Solver.TUNING_FIELDS.index("panel_fronts")].max() > 0
+        out.append(s.solve(bg))
+        s.close()
+    np.testing.assert_array_equal(out[0], out[1])
+    xo = mf.apply_inverse(mf.factor(G.to_scipy(), dims, mf.Options()), bg)
+    tol = 1e-10 if prec == 0 else 1e-4
+    assert np.linalg.norm(out[0] - xo) <= tol * np.linalg.norm(xo)
