@@ -60,6 +60,9 @@ BATCH256_NAME = ("batch of 256 upwinded 2D convection-diffusion systems (sides U
                  "residual 1e-10 in every system and column")
 METRIC = "factor+solve time to rel. residual 1e-10 (mixed FP32/FP64 vs FP64), 1 GB300"
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA units x clock (80.6)
+# DRAM bytes of an ID launch per algorithmic byte (ncu: 10.73 MB for 4 nodes of
+# 832 x 800 of rank 720 on the exchange kernel, 11.57 MB algorithmic)
+ID_TRAFFIC_PER_ALG_BYTE = 0.93
 
 
 def _dist():
@@ -269,6 +272,17 @@ def _time_fp64(s, vals, bt, steps, ws, A, b):
     return out, info
 
 
+def _profile_range(args, start):
+    """With --profile-range, the timed steps are the only part of the run a
+    profiler started with --profile-from-start off records (warm-up steps,
+    which include the autotuner's trials, stay outside)."""
+    if not args.profile_range:
+        return
+    import torch
+    torch.cuda.synchronize()
+    (torch.cuda.profiler.start if start else torch.cuda.profiler.stop)()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -283,7 +297,12 @@ def run_ours(args):
     bt = _device_rhs(b)
     if args.form == "fp64":  # profiling of the plain FP64 form alone
         s64 = _solver(A, 0)
-        t64, _ = _time_steps(s64, vals, bt, args.steps, args.warmup, ws)
+        for _ in range(args.warmup):
+            s64.factor(vals)
+            s64.solve(bt)
+        _profile_range(args, True)
+        t64, _ = _time_steps(s64, vals, bt, args.steps, 0, ws)
+        _profile_range(args, False)
         if rank == 0:
             print(json.dumps({"form": "fp64", "ms_per_step": t64, "stats": s64.get_stats()}), flush=True)
         s64.close()
@@ -297,7 +316,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     split = []
+    _profile_range(args, True)
     times, x = _time_steps(s, vals, bt, args.steps, 0, ws, split)
+    _profile_range(args, False)
     clk = clocks.stop()
     med = int(np.argsort(times)[len(times) // 2])  # the median step and its own factor / solve split
     st = s.get_stats()
@@ -361,7 +382,11 @@ def run_ours(args):
     roof = {"kernel": ("k_cpqr_id_rx / k_cpqr_id_push / k_cpqr_id_rr / k_cpqr_id_smem (interpolative "
                        "decompositions, Section 2.2)"),
             "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 5), "traffic": None,
+            "frac": round(achieved / peak, 5),
+            "traffic": round(ID_TRAFFIC_PER_ALG_BYTE * stp["id_bytes"] / max(stp["id_launches"], 1)),
+            "traffic_note": ("DRAM bytes per launch scaled from ncu captures of the exchange and shared-memory "
+                             "ID kernels on 832 x 800 nodes (dram read + write = 0.93 x the algorithmic bytes: the "
+                             "input is read once and nothing is re-read; profiles/ncu_id_*_832x800.md)"),
             "peak_source": ("FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128 lanes x "
                             "2 flop x 2.07 GHz"),
             "launches": stp["id_launches"],
@@ -603,6 +628,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="mark the timed steps for a profiler run with --profile-from-start off")
+    ap.add_argument("--nsys", type=int, default=None,
+                    help="--config batch256 with this many systems instead (profiling captures only)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the batch256 and grf100 measurements that follow the 64^3 benchmark")
     ap.add_argument("--form", choices=["both", "mixed", "fp64"], default="both",
@@ -620,6 +649,9 @@ def main():
         WORKLOAD.clear()
         WORKLOAD.update(BATCH256)
         WORKLOAD_NAME = BATCH256_NAME
+        if args.nsys is not None:
+            WORKLOAD["nsys"] = args.nsys
+            WORKLOAD_NAME = BATCH256_NAME.replace("batch of 256", f"batch of {args.nsys}")
     elif args.config == "grf100":
         WORKLOAD.clear()
         WORKLOAD.update(GRF100)

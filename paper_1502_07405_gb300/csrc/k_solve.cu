@@ -255,17 +255,20 @@ __global__ void __launch_bounds__(256) k_solve_fwd_blk(const DFront* __restrict_
   if (nc <= 0) return;
   extern __shared__ __align__(16) unsigned char blk_raw[];
   T* xs = reinterpret_cast<T*>(blk_raw);  // nc x max_nf
+  int* pv = reinterpret_cast<int*>(xs + (size_t)nc * max_nf);  // max_nf: the front's pivots
   __shared__ T B[32][33];
   const T* F = ar + f.off;
   const long long ld = f.nf;
   const int nf = f.nf, ns = f.ns;
   T* w = W + f.w_off + (long long)j0 * nf;
   for (int e = threadIdx.x; e < nc * nf; e += blockDim.x) xs[(e / nf) * max_nf + e % nf] = w[e];
+  if (!transpose)
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) pv[i] = piv[f.piv_off + i];
   __syncthreads();
-  if (!transpose && threadIdx.x < nc) {  // P b_s, one thread per column
+  if (!transpose && threadIdx.x < nc) {  // P b_s: the interchanges in order, one thread per column
     T* x = xs + threadIdx.x * max_nf;
     for (int i = 0; i < ns; ++i) {
-      const int p = piv[f.piv_off + i];
+      const int p = pv[i];
       if (p != i) { const T t = x[i]; x[i] = x[p]; x[p] = t; }
     }
   }
@@ -277,8 +280,8 @@ __global__ void __launch_bounds__(256) k_solve_fwd_blk(const DFront* __restrict_
       B[t][k] = (t < cw && k < cw) ? F[(cb + t) + (long long)(cb + k) * ld] : T(0);
     }
     __syncthreads();
-    if (wid < nc) {
-      T* x = xs + wid * max_nf + cb;
+    for (int q = wid; q < nc; q += blockDim.x >> 5) {  // the diagonal block, one warp per column
+      T* x = xs + q * max_nf + cb;
       T v = lane < cw ? x[lane] : T(0);
       if (!transpose) {  // unit lower: x_t -= L(t, k) x_k
         for (int k = 0; k < cw; ++k) {
@@ -344,12 +347,15 @@ __global__ void __launch_bounds__(256) k_solve_bwd_blk(const DFront* __restrict_
   if (nc <= 0) return;
   extern __shared__ __align__(16) unsigned char blk_raw[];
   T* xs = reinterpret_cast<T*>(blk_raw);  // nc x max_nf
+  int* pv = reinterpret_cast<int*>(xs + (size_t)nc * max_nf);  // max_nf: the front's pivots
   __shared__ T B[32][33];
   const T* F = ar + f.off;
   const long long ld = f.nf;
   const int nf = f.nf, ns = f.ns;
   const T* w = W + f.w_off + (long long)j0 * nf;
   for (int e = threadIdx.x; e < nc * nf; e += blockDim.x) xs[(e / nf) * max_nf + e % nf] = w[e];
+  if (transpose)
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) pv[i] = piv[f.piv_off + i];
   __syncthreads();
   if (!transpose) {  // y -= U12 x_u, thread per row
     for (int r = threadIdx.x; r < ns; r += blockDim.x) {
@@ -394,8 +400,8 @@ __global__ void __launch_bounds__(256) k_solve_bwd_blk(const DFront* __restrict_
       B[t][k] = (t < cw && k < cw) ? F[(cb + t) + (long long)(cb + k) * ld] : T(0);
     }
     __syncthreads();
-    if (wid < nc) {
-      T* x = xs + wid * max_nf + cb;
+    for (int q = wid; q < nc; q += blockDim.x >> 5) {  // the diagonal block, one warp per column
+      T* x = xs + q * max_nf + cb;
       T v = lane < cw ? x[lane] : T(0);
       if (!transpose) {  // U11: x_k = x_k / U(k, k), then x_t -= U(t, k) x_k
         for (int k = cw - 1; k >= 0; --k) {
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(256) k_solve_bwd_blk(const DFront* __restrict_
   if (transpose && threadIdx.x < nc) {  // P^T
     T* x = xs + threadIdx.x * max_nf;
     for (int i = ns - 1; i >= 0; --i) {
-      const int p = piv[f.piv_off + i];
+      const int p = pv[i];
       if (p != i) { const T t = x[i]; x[i] = x[p]; x[p] = t; }
     }
   }
@@ -463,9 +469,19 @@ __global__ void __launch_bounds__(256) k_solve_bwd_blk(const DFront* __restrict_
 // right-hand sides per CTA of the blocked sweeps (0: the front does not fit)
 template <typename T>
 static int blk_cols(int max_nf, int nrhs) {
-  if (max_nf <= 0) return 0;
-  const int nc = (int)std::min<size_t>(BLK_NC, kBlkSolveSmem / ((size_t)max_nf * sizeof(T)));
+  if (max_nf <= 0 || sizeof(int) * (size_t)max_nf >= kBlkSolveSmem / 2) return 0;
+  const size_t room = kBlkSolveSmem - sizeof(int) * (size_t)max_nf;  // the pivots' staging
+  const int nc = (int)std::min<size_t>(BLK_NC, room / ((size_t)max_nf * sizeof(T)));
   return std::min(nc, std::max(nrhs, 1));
+}
+
+// threads of a blocked-sweep CTA: fewer for small fronts, whose blocks are short
+static int blk_threads(int max_nf) { return max_nf <= 96 ? 64 : max_nf <= 192 ? 128 : 256; }
+
+// dynamic shared memory of the blocked sweeps: nc staged columns and the pivots
+template <typename T>
+static size_t blk_smem(int nc, int max_nf) {
+  return (size_t)nc * max_nf * sizeof(T) + sizeof(int) * (size_t)max_nf;
 }
 
 template <typename T>
@@ -475,8 +491,8 @@ void Kern<T>::solve_fwd_dense(const DevSym& ds, const T* arena, const int* piv, 
   const int nc = blk_cols<T>(max_nf, nrhs);
   if (nc > 0) {
     set_func_attr((const void*)k_solve_fwd_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSolveSmem);
-    const size_t smem = (size_t)nc * max_nf * sizeof(T);
-    k_solve_fwd_blk<T><<<dim3(nfr, (nrhs + nc - 1) / nc), 256, smem, s>>>(ds.fronts, arena, piv, W, flist, nrhs, nc,
+    const size_t smem = blk_smem<T>(nc, max_nf);
+    k_solve_fwd_blk<T><<<dim3(nfr, (nrhs + nc - 1) / nc), blk_threads(max_nf), smem, s>>>(ds.fronts, arena, piv, W, flist, nrhs, nc,
                                                                          max_nf, transpose);
   } else if (warp_cols_fit<T>(max_nf, nrhs)) {
     set_func_attr((const void*)k_solve_fwd_dense_wc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpColSmem);
@@ -643,8 +659,8 @@ void Kern<T>::solve_bwd_dense(const DevSym& ds, const T* arena, const int* piv, 
   const int nc = blk_cols<T>(max_nf, nrhs);
   if (nc > 0) {
     set_func_attr((const void*)k_solve_bwd_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSolveSmem);
-    const size_t smem = (size_t)nc * max_nf * sizeof(T);
-    k_solve_bwd_blk<T><<<dim3(nfr, (nrhs + nc - 1) / nc), 256, smem, s>>>(ds.fronts, arena, piv, W, xp, flist, ds.n,
+    const size_t smem = blk_smem<T>(nc, max_nf);
+    k_solve_bwd_blk<T><<<dim3(nfr, (nrhs + nc - 1) / nc), blk_threads(max_nf), smem, s>>>(ds.fronts, arena, piv, W, xp, flist, ds.n,
                                                                          nrhs, nc, max_nf, transpose);
   } else if (warp_cols_fit<T>(max_nf, nrhs)) {
     set_func_attr((const void*)k_solve_bwd_dense_wc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWarpColSmem);

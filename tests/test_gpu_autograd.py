@@ -114,3 +114,44 @@ def test_backward_after_refactor_raises():
     vals2 = torch.tensor(A.values, device="cuda", requires_grad=True)
     (sparse_solve(s, vals2, bt) ** 2).sum().backward()
     assert torch.isfinite(vals2.grad).all()
+
+
+def test_gradients_match_central_differences_48cubed_64_entries():
+    """The 48^3 differentiation workload (shifted Laplacian, sigma ~ U[0, 10]
+    per cell, HSS on fronts >= 1024 at eps 1e-6, L = ||x - xt||^2): the
+    gradient with respect to 64 random stored entries of A (and 8 entries of
+    b) against central differences.  The solves run GMRES to 1e-13 with the
+    eps = 1e-6 preconditioner, so L carries a relative error near 1e-13 and
+    the difference quotient a rounding error near 1e-13 L / h; h = 1e-4
+    balances it against the O(h^2) truncation (h = 1e-6 would leave rounding
+    errors of the order of the smaller gradient entries)."""
+    side = 48
+    A, b, xt = _problem(side, 51)
+    s = _solver(A, side, hss_tol=1e-6, hss_min_front=1024, precision=1, rtol=1e-13, maxit=600)
+    x, gb, gv, loss0 = _grads(s, A, b, xt)
+    assert s.get_stats()["n_hss_fronts"] > 0
+    vals0 = torch.tensor(A.values, device="cuda")
+    b0 = torch.tensor(b, device="cuda")
+    xtt = torch.tensor(xt, device="cuda")
+
+    def L(vals, bb):
+        s.factor(vals)
+        xx = s.solve(bb)
+        return float(((xx - xtt) ** 2).sum())
+
+    h = 1e-4
+    rng = np.random.default_rng(7)
+    err = []
+    for p in rng.choice(A.nnz, 64, replace=False):
+        vp, vm = vals0.clone(), vals0.clone()
+        vp[p] += h
+        vm[p] -= h
+        fd = (L(vp, b0) - L(vm, b0)) / (2 * h)
+        err.append(abs(fd - gv[p]) / max(1.0, abs(fd)))
+    for i in rng.choice(A.n, 8, replace=False):
+        bp, bm = b0.clone(), b0.clone()
+        bp[i] += h
+        bm[i] -= h
+        fd = (L(vals0, bp) - L(vals0, bm)) / (2 * h)
+        err.append(abs(fd - gb[i]) / max(1.0, abs(fd)))
+    assert max(err) <= 1e-3, max(err)
