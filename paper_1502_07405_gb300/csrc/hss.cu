@@ -803,7 +803,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           const IdJob* dj = H.ring.put(kv.second, X.s);
           if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
           if (timed(400 + (kv.first & 31), kv.first & 31, (int)kv.second.size(), dd, mm, [&] {
-                return batched_id_rx(dj, (int)kv.second.size(), mm, dd, eps, rdiag, order, kv.first, X.s);
+                return batched_id_rx(dj, (int)kv.second.size(), mm, dd, eps, rdiag, order, kv.first, X.s, 0, -1, p);
               }) < 0) {
             for (int q : rx_ix[kv.first]) route_old((size_t)q);  // not schedulable: the other kernels
           } else {

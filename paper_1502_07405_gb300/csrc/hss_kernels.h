@@ -128,11 +128,14 @@ struct UlvBwdJob {
 // (njobs x min(max_m, max_d) doubles) and order (njobs x max_m ints) are
 // scratch.  spin bounds every wait (0: the default); hang_rank >= 0 makes
 // that CTA of every cluster withhold its first proposal, so that the waits
-// run out (tests of the timeout path; -1 otherwise).  Returns -1 if the
-// configuration cannot be launched (the caller falls back).
+// run out (tests of the timeout path; -1 otherwise).  fail_p >= 0 stops an
+// ID as soon as its rank exceeds d - fail_p with m > d (the adaptive scheme
+// rejects it whatever follows): it reports that rank, d - fail_p + 1, and
+// leaves X and piv unwritten; -1 runs every ID to its rank.  Returns -1 if
+// the configuration cannot be launched (the caller falls back).
 int id_rx_config(int d, int m, int family = 0);
 int batched_id_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag, int* order,
-                  int cfg, cudaStream_t s, int spin = 0, int hang_rank = -1);
+                  int cfg, cudaStream_t s, int spin = 0, int hang_rank = -1, int fail_p = -1);
 
 template <typename T>
 struct HssKern {

@@ -113,7 +113,7 @@ template <int RPL, int CPW, int CL, int NW>
 __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restrict__ jobs, double eps,
                                                             double* __restrict__ rdiag_all,
                                                             int* __restrict__ order_all, int max_m, int max_k,
-                                                            int spin, int hang_rank) {
+                                                            int spin, int hang_rank, int fail_p) {
   constexpr int P = Pow2Ceil<CPW>::value;
   constexpr int LP = Log2<P>::value;
   constexpr int LDV = 32 * RPL;  // rows of a staged column
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
 
   const int kmax = min(d, m);
   int k = kmax;
-  bool failed = false;
+  bool failed = false, doomed = false;
   float thr = 0.f;
   for (int i = 0; i < kmax; ++i) {
     const int par = i & 1;
@@ -289,6 +289,15 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
       k = i;
       break;
     }
+    // with fail_p >= 0: pivot i takes the rank past d - fail_p and the rank
+    // cannot reach m (m > d), so the ID fails whatever follows; stop with the
+    // rank i + 1 and no X (the adaptive scheme retries the node with more
+    // samples)
+    if (fail_p >= 0 && m > d && i >= d - fail_p) {
+      k = i + 1;
+      doomed = true;
+      break;
+    }
     if (rank == 0 && threadIdx.x == 0) {
       rdiag[i] = (double)beta;
       order[i] = p;
@@ -357,7 +366,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
   bool any_fail = s_fail != 0;
   if (CL > 1)
     for (int q = 0; q < CL; ++q) any_fail = any_fail || *cg::this_cluster().map_shared_rank(&s_fail, q) != 0;
-  if (!any_fail) {
+  if (!any_fail && !doomed) {
     // X = R1^-1 R2 for this CTA's non-skeleton columns: a blocked back
     // substitution over 32-row blocks from the bottom, 16 columns at a time
     // in shared memory (the staging area), R1 read from W
@@ -434,7 +443,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
       }
   }
   if (rank == 0) {
-    if (!any_fail)
+    if (!any_fail && !doomed)
       for (int t = threadIdx.x; t < k; t += (32 * NW)) jb.piv[t] = order[t];
     if (threadIdx.x == 0) *jb.rank = any_fail ? -1 : k;
   }
@@ -449,7 +458,7 @@ inline size_t rx_smem_bytes(int rpl, int nw, int cl, int max_m) {
 
 template <int RPL, int CPW, int NW, int CL>
 int launch_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag, int* order,
-              cudaStream_t s, int spin, int hang_rank) {
+              cudaStream_t s, int spin, int hang_rank, int fail_p) {
   if (max_d > 32 * RPL || max_m > CL * NW * CPW) return -1;
   auto kern = k_cpqr_id_rx<RPL, CPW, CL, NW>;
   const size_t smem = rx_smem_bytes(RPL, NW, CL, max_m);
@@ -473,7 +482,7 @@ int launch_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, do
   cfg.numAttrs = CL > 1 ? 1 : 0;
   const int max_k = std::max(std::min(max_m, max_d), 1);
   if (cudaLaunchKernelEx(&cfg, kern, jobs, eps, rdiag, order, std::max(max_m, 1), max_k,
-                         spin > 0 ? spin : RX_SPIN, hang_rank) != cudaSuccess) {
+                         spin > 0 ? spin : RX_SPIN, hang_rank, fail_p) != cudaSuccess) {
     cudaGetLastError();
     return -1;  // not schedulable: the caller falls back
   }
@@ -483,13 +492,13 @@ int launch_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, do
 
 template <int RPL, int CPW, int NW>
 int launch_rx_cl(int cl, const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
-                 int* order, cudaStream_t s, int spin, int hang_rank) {
+                 int* order, cudaStream_t s, int spin, int hang_rank, int fail_p) {
   switch (cl) {
-    case 1: return launch_rx<RPL, CPW, NW, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 2: return launch_rx<RPL, CPW, NW, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 4: return launch_rx<RPL, CPW, NW, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 8: return launch_rx<RPL, CPW, NW, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 16: return launch_rx<RPL, CPW, NW, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 1: return launch_rx<RPL, CPW, NW, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
+    case 2: return launch_rx<RPL, CPW, NW, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
+    case 4: return launch_rx<RPL, CPW, NW, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
+    case 8: return launch_rx<RPL, CPW, NW, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
+    case 16: return launch_rx<RPL, CPW, NW, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
     default: return -1;
   }
 }
@@ -516,16 +525,16 @@ int id_rx_config(int d, int m, int family) {
 }
 
 int batched_id_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag, int* order,
-                  int cfg, cudaStream_t s, int spin, int hang_rank) {
+                  int cfg, cudaStream_t s, int spin, int hang_rank, int fail_p) {
   if (njobs <= 0) return 0;
   const int t = cfg / 32, cl = cfg % 32;
   switch (t) {
-    case 0: return launch_rx_cl<8, 16, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 1: return launch_rx_cl<16, 10, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 2: return launch_rx_cl<26, 7, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 3: return launch_rx_cl<8, 8, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 4: return launch_rx_cl<16, 4, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
-    case 5: return launch_rx_cl<26, 3, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank);
+    case 0: return launch_rx_cl<8, 16, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
+    case 1: return launch_rx_cl<16, 10, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
+    case 2: return launch_rx_cl<26, 7, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
+    case 3: return launch_rx_cl<8, 8, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
+    case 4: return launch_rx_cl<16, 4, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
+    case 5: return launch_rx_cl<26, 3, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
     default: return -1;
   }
 }
