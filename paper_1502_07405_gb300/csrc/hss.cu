@@ -832,7 +832,7 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
           if (timed(100 + cl, cl, (int)smem_tier[ti].size(), sm_d[ti], sm_m[ti], [&] {
                 return HssKern<T>::batched_id_smem(dj, (int)smem_tier[ti].size(), sm_m[ti], sm_d[ti], eps, rdiag,
-                                                   order, cl, X.s);
+                                                   order, cl, X.s, p);
               }) < 0) {
             for (size_t q = 0; q < smem_tier[ti].size(); ++q) {  // not schedulable: the L2-resident kernels
               const IdJob& j = smem_tier[ti][q];

@@ -163,8 +163,10 @@ struct HssKern {
   static int id_rr_config(int d, int m);
   static int batched_id_rr(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
                            int* order, int cfg, cudaStream_t s);
+  // fail_p >= 0: a job with m > d stops, with no X and no pivots, as soon
+  // as its rank passes d - fail_p (an ID the adaptive scheme rejects)
   static int batched_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
-                             int* order, int cl, cudaStream_t s);
+                             int* order, int cl, cudaStream_t s, int fail_p = -1);
   static void basis(const BasisJob* jobs, int njobs, cudaStream_t s);
   static void lu(const LuJob* jobs, int njobs, unsigned* status, cudaStream_t s);
   // Blocked LQ, panel of rows [j0, j0 + nb) of every job with m - k > j0:

@@ -814,7 +814,7 @@ __host__ __device__ inline size_t id_smem_bytes(int d, int m, int cl, int esz) {
 template <typename T, int CL, bool OVF>
 __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __restrict__ jobs, double eps,
                                                                  double* rdiag_all, int* order_all, int max_m,
-                                                                 int max_k, int ms) {
+                                                                 int max_k, int ms, int fail_p) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = CL > 1 ? (int)cluster.block_rank() : 0;
@@ -904,11 +904,17 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
   const T thr = id_threshold<T>(eps, b);  // eps^2 |R_11|^2, rounded down to T
   const int kmax = min(d, m);
   int k = kmax;
+  bool doomed = false;
   for (int i = 0; i < kmax; ++i) {
     if (i > 0) pivot(i & 1, b, p);
     const bool stop = (i == 0 ? !(b > T(0)) : !(b > thr)) || p >= m;
     if (stop) {
       k = i;
+      break;
+    }
+    if (fail_p >= 0 && m > d && i >= d - fail_p) {  // the ID fails whatever follows (see k_cpqr_id_push)
+      k = i + 1;
+      doomed = true;
       break;
     }
     const T nrm = sqrt(b);
@@ -965,7 +971,7 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
   // X = R1^-1 R2 on the owned non-skeleton columns, R1 columns read from their owners
   const double* rd = rdiag;
   T* X = (T*)jb.X;
-  for (int g = wid; 4 * g < mo; g += nw) {
+  for (int g = wid; !doomed && 4 * g < mo; g += nw) {
     int ls[4];
     int nc = 0;
     for (int q = 0; q < 4; ++q) {
@@ -993,7 +999,7 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_smem(const IdJob* __
     }
   }
   if (rank == 0) {
-    for (int i = threadIdx.x; i < k; i += blockDim.x) jb.piv[i] = order[i];
+    for (int i = threadIdx.x; !doomed && i < k; i += blockDim.x) jb.piv[i] = order[i];
     if (threadIdx.x == 0) *jb.rank = k;
   }
   // peers may still read this CTA's R1 columns
@@ -1061,7 +1067,7 @@ __device__ __forceinline__ void fence_async() { asm volatile("fence.proxy.async.
 template <typename T, int CL, bool OVF>
 __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_push(const IdJob* __restrict__ jobs, double eps,
                                                                  double* rdiag_all, int* order_all, int max_m,
-                                                                 int max_k, int ms) {
+                                                                 int max_k, int ms, int fail_p) {
   static_assert(CL >= 2 && CL <= 16, "cluster of 2..16 CTAs");
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -1167,12 +1173,22 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_push(const IdJob* __
   const T thr = id_threshold<T>(eps, b);
   const int kmax = min(d, m);
   int k = kmax;
+  bool doomed = false;
   for (int i = 0; i < kmax; ++i) {
     const int par = i & 1;
     if (i > 0) ok = pivot(i, b, p);
     const bool stop = !ok || (i == 0 ? !(b > T(0)) : !(b > thr)) || p >= m;
     if (stop) {
       k = i;
+      break;
+    }
+    // with fail_p >= 0: pivot i takes the rank past d - fail_p and the rank
+    // cannot reach m (m > d), so the adaptive scheme rejects the ID whatever
+    // follows: stop with rank i + 1 and no X (the same decision in every CTA;
+    // the pivot column of step i has not been sent, the last copies landed)
+    if (fail_p >= 0 && m > d && i >= d - fail_p) {
+      k = i + 1;
+      doomed = true;
       break;
     }
     const T nrm = sqrt(b);
@@ -1238,7 +1254,7 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_push(const IdJob* __
   const bool failed = s_fail != 0;
   const double* rd = rdiag;
   T* X = (T*)jb.X;
-  for (int g = wid; !failed && 4 * g < mo; g += nw) {
+  for (int g = wid; !failed && !doomed && 4 * g < mo; g += nw) {
     int ls[4];
     int nc = 0;
     for (int q = 0; q < 4; ++q) {
@@ -1265,7 +1281,7 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_push(const IdJob* __
     }
   }
   if (rank == 0) {
-    for (int i = threadIdx.x; i < k; i += blockDim.x) jb.piv[i] = order[i];
+    for (int i = threadIdx.x; !doomed && i < k; i += blockDim.x) jb.piv[i] = order[i];
     if (threadIdx.x == 0) *jb.rank = failed ? -1 : k;
   }
   cluster.sync();  // peers may still read this CTA's R1 columns
@@ -1273,7 +1289,7 @@ __global__ void __launch_bounds__(IDS_THREADS, 1) k_cpqr_id_push(const IdJob* __
 
 template <typename T, int CL>
 static int launch_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
-                          int* order, cudaStream_t s) {
+                          int* order, int fail_p, cudaStream_t s) {
   // owned columns per CTA kept in shared memory; the rest stay in the job's W
   // (clusters: two pivot-column buffers and a staging column besides)
   const size_t col = sizeof(T) * (size_t)id_smem_ld(max_d);
@@ -1283,7 +1299,7 @@ static int launch_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, do
   const int ms = (int)std::min<size_t>((size_t)mo_max, (kIdSmemBudget - fixed) / col);
   const size_t smem = fixed + col * (size_t)ms;
   const bool ovf = ms < mo_max;
-  void (*kern)(const IdJob*, double, double*, int*, int, int, int);
+  void (*kern)(const IdJob*, double, double*, int*, int, int, int, int);
   if constexpr (CL > 1)
     kern = ovf ? k_cpqr_id_push<T, CL, true> : k_cpqr_id_push<T, CL, false>;
   else
@@ -1303,7 +1319,7 @@ static int launch_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, do
   cfg.attrs = at;
   cfg.numAttrs = 1;
   const int max_k = std::max(std::min(max_m, max_d), 1);
-  if (cudaLaunchKernelEx(&cfg, kern, jobs, eps, rdiag, order, std::max(max_m, 1), max_k, ms) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, kern, jobs, eps, rdiag, order, std::max(max_m, 1), max_k, ms, fail_p) != cudaSuccess) {
     cudaGetLastError();
     return -1;
   }
@@ -1320,14 +1336,14 @@ int HssKern<T>::id_smem_cluster_size(int d, int m) {
 
 template <typename T>
 int HssKern<T>::batched_id_smem(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
-                                int* order, int cl, cudaStream_t s) {
+                                int* order, int cl, cudaStream_t s, int fail_p) {
   if (njobs <= 0) return 0;
   switch (cl) {
-    case 1: return launch_id_smem<T, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
-    case 2: return launch_id_smem<T, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
-    case 4: return launch_id_smem<T, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
-    case 8: return launch_id_smem<T, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
-    case 16: return launch_id_smem<T, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s);
+    case 1: return launch_id_smem<T, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, fail_p, s);
+    case 2: return launch_id_smem<T, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, fail_p, s);
+    case 4: return launch_id_smem<T, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, fail_p, s);
+    case 8: return launch_id_smem<T, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, fail_p, s);
+    case 16: return launch_id_smem<T, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, fail_p, s);
     default: return -1;
   }
 }
@@ -2007,7 +2023,7 @@ __device__ void blk_upper_solve(const T* __restrict__ A, long long lda, T* x, in
   }
 }
 
-constexpr int ULV_THREADS = 256;
+constexpr int ULV_THREADS = 512;  // one CTA per (node, column): more loads in flight per node
 constexpr size_t kUlvSmemMax = 200 * 1024;
 
 // ---------------------------------------------------------------------------
@@ -2043,15 +2059,30 @@ __global__ void __launch_bounds__(ULV_THREADS) k_ulv_fwd(const UlvFwdJob* __rest
     } else {
       const T* w2 = wc2 + (long long)j * jb.kc2;
       const T* w1 = wc1 + (long long)j * jb.kc1;
+      // thread per row, four partial sums over the columns (independent loads in flight)
       for (int i = threadIdx.x; i < jb.k1; i += blockDim.x) {
-        T s = bh1[i + (long long)j * jb.ldbh1];
-        for (int c = 0; c < jb.kc2; ++c) s -= B12[i + (long long)c * jb.k1] * w2[c];
-        bt[i] = s;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        int c = 0;
+        for (; c + 3 < jb.kc2; c += 4) {
+          s0 += B12[i + (long long)c * jb.k1] * w2[c];
+          s1 += B12[i + (long long)(c + 1) * jb.k1] * w2[c + 1];
+          s2 += B12[i + (long long)(c + 2) * jb.k1] * w2[c + 2];
+          s3 += B12[i + (long long)(c + 3) * jb.k1] * w2[c + 3];
+        }
+        for (; c < jb.kc2; ++c) s0 += B12[i + (long long)c * jb.k1] * w2[c];
+        bt[i] = bh1[i + (long long)j * jb.ldbh1] - ((s0 + s1) + (s2 + s3));
       }
       for (int i = threadIdx.x; i < jb.k2; i += blockDim.x) {
-        T s = bh2[i + (long long)j * jb.ldbh2];
-        for (int c = 0; c < jb.kc1; ++c) s -= B21[i + (long long)c * jb.k2] * w1[c];
-        bt[jb.k1 + i] = s;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        int c = 0;
+        for (; c + 3 < jb.kc1; c += 4) {
+          s0 += B21[i + (long long)c * jb.k2] * w1[c];
+          s1 += B21[i + (long long)(c + 1) * jb.k2] * w1[c + 1];
+          s2 += B21[i + (long long)(c + 2) * jb.k2] * w1[c + 2];
+          s3 += B21[i + (long long)(c + 3) * jb.k2] * w1[c + 3];
+        }
+        for (; c < jb.kc1; ++c) s0 += B21[i + (long long)c * jb.k2] * w1[c];
+        bt[jb.k1 + i] = bh2[i + (long long)j * jb.ldbh2] - ((s0 + s1) + (s2 + s3));
       }
     }
     __syncthreads();
