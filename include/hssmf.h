@@ -278,10 +278,13 @@ int hssmf_get_tuning(const hssmf_ctx* ctx, int* rec, int max_levels);
  * fit stay in global memory);
  * use_cluster = -100 - c (c = 2, 4, 8, 16) runs the shared-memory kernel on
  * clusters of c CTAs whatever the size; use_cluster = -3 (prec 1 only) keeps
- * every matrix in the registers of a cluster of 1..16 CTAs of 256 threads
- * with one exchange of proposals per pivot step (d <= 832; m up to 2048,
- * 1280 or 896 for d <= 256, 512, 832), else HSSMF_ERR_ARG; use_cluster =
- * -4 the same on CTAs of 512 threads (m up to 2048, 1024 or 768);
+ * every matrix in the registers of a cluster of CTAs of 256 threads with one
+ * exchange of proposals per pivot step: lanes hold 32 r rows (r the smallest
+ * even number with d <= 32 r, at least 4; d <= 832) and a warp c columns
+ * (c = 32, 24, 16, 16, 14, 12, 10, 9, 8, 8, 7, 7 for r = 4, 6, ..., 26), on
+ * the smallest cluster of 1..16 CTAs with m <= 8 c x CTAs, else
+ * HSSMF_ERR_ARG; use_cluster = -4 the same on CTAs of 512 threads (m up to
+ * 2048, 1024 or 768 for d <= 256, 512, 832);
  * use_cluster = -2 (prec 1 only) keeps
  * every matrix in the registers of a
  * cluster of 1..16 CTAs, for d <= 512 and m <= 2048 (d <= 256) or m <= 1024
@@ -294,7 +297,7 @@ hssmf_status hssmf_batched_id(int prec, int njobs, const void* Y, const long lon
 
 /* Test of the failure path of the bounded waits (the paper has no
  * counterpart): one FP32 ID on the register-resident cluster kernel with
- * cl CTAs (2, 4, 8 or 16) in which CTA 0 withholds its first proposal, so
+ * cl CTAs (2 to 16) in which CTA 0 withholds its first proposal, so
  * that every wait of the cluster runs out after spin polls.  The kernel
  * then stops, meets its cluster barriers and reports rank -1; the call
  * returns HSSMF_ERR_TIMEOUT (HSSMF_OK would mean the wait did not run out),

@@ -109,18 +109,23 @@ __device__ __forceinline__ float rx_reduce(float (&y)[P], int lane) {
 
 constexpr int RX_SEG = 8;  // row blocks per segment of the Householder passes
 
-template <int RPL, int CPW, int CL, int NW>
+template <int RPL, int CPW, int NW>
 __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restrict__ jobs, double eps,
                                                             double* __restrict__ rdiag_all,
                                                             int* __restrict__ order_all, int max_m, int max_k,
-                                                            int spin, int hang_rank, int fail_p) {
+                                                            int spin, int hang_rank, int fail_p, int ncl) {
   constexpr int P = Pow2Ceil<CPW>::value;
   constexpr int LP = Log2<P>::value;
   constexpr int LDV = 32 * RPL;  // rows of a staged column
   constexpr int LDS = LDV + 4;   // + a 16-byte header: proposal norm and column
   namespace cg = cooperative_groups;
-  const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const int jid = blockIdx.x / CL;
+  const int rank = ncl > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int jid = blockIdx.x / ncl;
+  // x / ncl for 0 <= x < 8192 (columns: m <= 16 x 256) by a 32-bit
+  // multiply and a shift (exact: rounding 2^19 / ncl up adds less than
+  // x / 2^19 < 1 / ncl, and x (2^19 / ncl + 1) < 2^32)
+  const unsigned cl_mul = ((1u << 19) + ncl - 1) / ncl;
+  auto cdiv = [cl_mul](int x) { return (int)(((unsigned)x * cl_mul) >> 19); };
   const IdJob jb = jobs[jid];
   const int d = jb.d, m = jb.m;
   const float* Y = (const float*)jb.Y;
@@ -129,8 +134,8 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
   int* order = order_all + (long long)jid * max_m;
   extern __shared__ __align__(16) float rx_smem[];
   float* stage = rx_smem;                       // [2][NW][LDS]: each warp's candidate, by step parity
-  float* land = stage + 2 * NW * LDS;        // [2][CL][LDS]: the CL CTAs' candidates (CL > 1)
-  float* vm = land + (CL > 1 ? 2 * CL * LDS : 0);  // [LDV]: the step's reflector, masked
+  float* land = stage + 2 * NW * LDS;        // [2][ncl][LDS]: the ncl CTAs' candidates (ncl > 1)
+  float* vm = land + (ncl > 1 ? 2 * ncl * LDS : 0);  // [LDV]: the step's reflector, masked
   float* rdb = vm + LDV;                            // [32][33]: diagonal block (epilogue)
   unsigned char* skel = (unsigned char*)(rdb + 32 * 33);  // [m]: skeleton flags (epilogue)
   __shared__ float s_wv[NW];
@@ -142,7 +147,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
   __shared__ int s_ord[32];            // epilogue: pivot columns of a block
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int mycol = lane >> (5 - LP);  // column whose norm this lane holds after rx_reduce
-  const int myj = mycol < CPW ? rank + CL * (wid + NW * mycol) : m;
+  const int myj = mycol < CPW ? rank + ncl * (wid + NW * mycol) : m;
 
   float a[CPW][RPL];
   unsigned act = 0;  // bit c: column c of this warp exists and is not pivoted
@@ -151,7 +156,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
   for (int c = 0; c < P; ++c) y[c] = 0.f;
 #pragma unroll
   for (int c = 0; c < CPW; ++c) {
-    const int j = rank + CL * (wid + NW * c);
+    const int j = rank + ncl * (wid + NW * c);
     if (j < m) act |= 1u << c;
 #pragma unroll
     for (int s = 0; s < RPL; ++s) {
@@ -164,13 +169,13 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
   if (!(mycol < CPW && ((act >> mycol) & 1))) cn = -1.f;
   if (threadIdx.x == 0) {
     s_fail = 0;
-    if (CL > 1) {
+    if (ncl > 1) {
       for (int q = 0; q < 2; ++q)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(rx_saddr(&bar_c[q])) : "memory");
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
   }
-  if (CL > 1)
+  if (ncl > 1)
     cg::this_cluster().sync();  // every CTA's barriers exist before the first copy
   else
     __syncthreads();
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
       int bj = cn >= 0.f ? myj : m;
       id_argmax(bv, bj, 32 >> LP);
       if (bj < m) {
-        const int cs = ((bj - rank) / CL - wid) / NW;  // the candidate's slot in this warp
+        const int cs = (cdiv(bj - rank) - wid) / NW;  // the candidate's slot in this warp
         float* st = stage + ((size_t)par * NW + wid) * LDS;
 #pragma unroll
         for (int c = 0; c < CPW; ++c)
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
         s_wv[wid] = bv;
         s_wj[wid] = bj;
       }
-      if (CL > 1) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // read next by bulk copies
+      if (ncl > 1) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // read next by bulk copies
     }
     __syncthreads();
     // 2. the CTA's proposal; in a cluster, its candidate goes to every CTA
@@ -214,23 +219,23 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
     id_argmax(b, p);
     bool ok = true;
     const float* vsrc;
-    if (CL == 1) {
-      vsrc = stage + ((size_t)par * NW + (p < m ? (p / CL) % NW : 0)) * LDS;
+    if (ncl == 1) {
+      vsrc = stage + ((size_t)par * NW + (p < m ? p % NW : 0)) * LDS;
     } else {
       const unsigned bytes = (unsigned)(LDS - i0) * 4u;
       if (threadIdx.x == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(rx_saddr(&bar_c[par])),
-                     "r"(bytes * CL)
+                     "r"(bytes * ncl)
                      : "memory");
         if (p < m && !(i == 0 && rank == hang_rank)) {
-          float* st = stage + ((size_t)par * NW + (p / CL) % NW) * LDS;
+          float* st = stage + ((size_t)par * NW + cdiv(p) % NW) * LDS;
           st[LDV] = b;
           st[LDV + 1] = __int_as_float(p);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           const uint32_t src = rx_saddr(st + i0);
-          const uint32_t dst = rx_saddr(land + ((size_t)par * CL + rank) * LDS + i0);
+          const uint32_t dst = rx_saddr(land + ((size_t)par * ncl + rank) * LDS + i0);
           const uint32_t bar = rx_saddr(&bar_c[par]);
-          for (int q = 0; q < CL; ++q)
+          for (int q = 0; q < ncl; ++q)
             asm volatile(
                 "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                     rx_mapa(dst, q)),
@@ -242,9 +247,9 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
           st[LDV + 1] = __int_as_float(m);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           const uint32_t src = rx_saddr(st + i0);
-          const uint32_t dst = rx_saddr(land + ((size_t)par * CL + rank) * LDS + i0);
+          const uint32_t dst = rx_saddr(land + ((size_t)par * ncl + rank) * LDS + i0);
           const uint32_t bar = rx_saddr(&bar_c[par]);
-          for (int q = 0; q < CL; ++q)
+          for (int q = 0; q < ncl; ++q)
             asm volatile(
                 "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                     rx_mapa(dst, q)),
@@ -258,14 +263,14 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
       ok = rx_wait(rx_saddr(&bar_c[par]), (i >> 1) & 1, spin);
       b = -1.f;
       p = m;
-      if (ok && lane < CL) {
-        const float* h = land + ((size_t)par * CL + lane) * LDS + LDV;
+      if (ok && lane < ncl) {
+        const float* h = land + ((size_t)par * ncl + lane) * LDS + LDV;
         b = h[0];
         p = __float_as_int(h[1]);
       }
       id_argmax(b, p);
       if (p < 0 || p > m) p = m;
-      vsrc = land + ((size_t)par * CL + (p < m ? p % CL : 0)) * LDS;
+      vsrc = land + ((size_t)par * ncl + (p < m ? p - ncl * cdiv(p) : 0)) * LDS;
     }
     if (i == 0) thr = __double2float_rd(eps * eps * (double)fmaxf(b, 0.f));
     const bool stop = !ok || (i == 0 ? !(b > 0.f) : !(b > thr)) || p >= m;
@@ -302,7 +307,10 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
       rdiag[i] = (double)beta;
       order[i] = p;
     }
-    if (rank == p % CL && wid == (p / CL) % NW) act &= ~(1u << ((p / CL) / NW));
+    {
+      const int lp = cdiv(p);  // the pivot's local column in its owner CTA
+      if (rank == p - ncl * lp && wid == lp % NW) act &= ~(1u << (lp / NW));
+    }
 #pragma unroll
     for (int c = 0; c < P; ++c) y[c] = 0.f;
     // segments of RX_SEG row blocks: skipped when they lie wholly above row i
@@ -347,7 +355,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
   // the owned columns (R in place) go to W for the back substitution
 #pragma unroll
   for (int c = 0; c < CPW; ++c) {
-    const int j = rank + CL * (wid + NW * c);
+    const int j = rank + ncl * (wid + NW * c);
     if (j < m) {
 #pragma unroll
       for (int s = 0; s < RPL; ++s) {
@@ -359,13 +367,13 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
   if (failed && threadIdx.x == 0) s_fail = 1;
   // every CTA has left the step loop (its copies have landed: each CTA
   // waited for all of them), and W, rdiag and order are visible
-  if (CL > 1)
+  if (ncl > 1)
     cg::this_cluster().sync();
   else
     __syncthreads();
   bool any_fail = s_fail != 0;
-  if (CL > 1)
-    for (int q = 0; q < CL; ++q) any_fail = any_fail || *cg::this_cluster().map_shared_rank(&s_fail, q) != 0;
+  if (ncl > 1)
+    for (int q = 0; q < ncl; ++q) any_fail = any_fail || *cg::this_cluster().map_shared_rank(&s_fail, q) != 0;
   if (!any_fail && !doomed) {
     // X = R1^-1 R2 for this CTA's non-skeleton columns: a blocked back
     // substitution over 32-row blocks from the bottom, 16 columns at a time
@@ -376,7 +384,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
     __syncthreads();
     if (threadIdx.x == 0) {
       int n = 0;
-      for (int j = rank; j < m; j += CL)
+      for (int j = rank; j < m; j += ncl)
         if (!skel[j]) s_list[n++] = j;
       s_nl = n;
     }
@@ -447,7 +455,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_cpqr_id_rx(const IdJob* __restri
       for (int t = threadIdx.x; t < k; t += (32 * NW)) jb.piv[t] = order[t];
     if (threadIdx.x == 0) *jb.rank = any_fail ? -1 : k;
   }
-  if (CL > 1) cg::this_cluster().sync();  // peers may still read this CTA's failure flag
+  if (ncl > 1) cg::this_cluster().sync();  // peers may still read this CTA's failure flag
 }
 
 // shared memory of a configuration (bytes)
@@ -456,33 +464,33 @@ inline size_t rx_smem_bytes(int rpl, int nw, int cl, int max_m) {
   return sizeof(float) * ((2 * nw + (cl > 1 ? 2 * cl : 0)) * lds + 32 * rpl + 32 * 33) + (size_t)std::max(max_m, 1);
 }
 
-template <int RPL, int CPW, int NW, int CL>
-int launch_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag, int* order,
+template <int RPL, int CPW, int NW>
+int launch_rx(int cl, const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag, int* order,
               cudaStream_t s, int spin, int hang_rank, int fail_p) {
-  if (max_d > 32 * RPL || max_m > CL * NW * CPW) return -1;
-  auto kern = k_cpqr_id_rx<RPL, CPW, CL, NW>;
-  const size_t smem = rx_smem_bytes(RPL, NW, CL, max_m);
-  // one limit per kernel (the largest m it takes), so that the attribute set
-  // on a device never needs lowering or raising
+  if (cl < 1 || cl > 16 || max_d > 32 * RPL || max_m > cl * NW * CPW) return -1;
+  auto kern = k_cpqr_id_rx<RPL, CPW, NW>;
+  const size_t smem = rx_smem_bytes(RPL, NW, cl, max_m);
+  // one limit per kernel (the largest cluster and m it takes), so that the
+  // attribute set on a device never needs lowering or raising
   if (!set_func_attr((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                     (int)rx_smem_bytes(RPL, NW, CL, CL * NW * CPW)))
+                     (int)rx_smem_bytes(RPL, NW, 16, 16 * NW * CPW)))
     return -1;
-  if (CL > 8 && !set_func_attr((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) return -1;
+  if (cl > 8 && !set_func_attr((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) return -1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(njobs * CL, 1, 1);
+  cfg.gridDim = dim3(njobs * cl, 1, 1);
   cfg.blockDim = dim3(32 * NW, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.x = cl;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
-  cfg.numAttrs = CL > 1 ? 1 : 0;
+  cfg.numAttrs = cl > 1 ? 1 : 0;
   const int max_k = std::max(std::min(max_m, max_d), 1);
   if (cudaLaunchKernelEx(&cfg, kern, jobs, eps, rdiag, order, std::max(max_m, 1), max_k,
-                         spin > 0 ? spin : RX_SPIN, hang_rank, fail_p) != cudaSuccess) {
+                         spin > 0 ? spin : RX_SPIN, hang_rank, fail_p, cl) != cudaSuccess) {
     cudaGetLastError();
     return -1;  // not schedulable: the caller falls back
   }
@@ -490,36 +498,32 @@ int launch_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps, do
   return 0;
 }
 
-template <int RPL, int CPW, int NW>
-int launch_rx_cl(int cl, const IdJob* jobs, int njobs, int max_m, int max_d, double eps, double* rdiag,
-                 int* order, cudaStream_t s, int spin, int hang_rank, int fail_p) {
-  switch (cl) {
-    case 1: return launch_rx<RPL, CPW, NW, 1>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
-    case 2: return launch_rx<RPL, CPW, NW, 2>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
-    case 4: return launch_rx<RPL, CPW, NW, 4>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
-    case 8: return launch_rx<RPL, CPW, NW, 8>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
-    case 16: return launch_rx<RPL, CPW, NW, 16>(jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
-    default: return -1;
-  }
-}
-
 // Configurations (rows per lane RPL: d <= 32 RPL; columns per warp CPW; warps
-// per CTA NW): CPW * RPL data registers of a thread fit the 255 of a
-// 256-thread CTA (family 0) or the 128 of a 512-thread CTA (family 1).
+// per CTA NW).  Family 0 (256-thread CTAs, up to 255 registers a thread):
+// one shape per multiple of 64 in d, so that no lane holds rows beyond d,
+// with CPW * RPL data registers near 180; family 1 (512-thread CTAs, 128
+// registers a thread): three shapes.  A node of m columns takes the first
+// shape of its family with d <= 32 RPL and the smallest cluster holding its
+// columns (m <= cluster x NW x CPW): clusters of any size from 1 to 16 (the
+// GPU co-schedules 15 clusters of 7 to 9 CTAs but only 7 of 13 to 16).
 struct RxShape {
   int rpl, cpw, nw;
 };
-constexpr RxShape RX_SHAPES[6] = {{8, 16, 8}, {16, 10, 8}, {26, 7, 8}, {8, 8, 16}, {16, 4, 16}, {26, 3, 16}};
+constexpr int RX_FAMILY0 = 12;
+constexpr RxShape RX_SHAPES[RX_FAMILY0 + 3] = {
+    {4, 32, 8},  {6, 24, 8},  {8, 16, 8},  {10, 16, 8}, {12, 14, 8}, {14, 12, 8}, {16, 10, 8}, {18, 9, 8},
+    {20, 8, 8},  {22, 8, 8},  {24, 7, 8},  {26, 7, 8},  {8, 8, 16},  {16, 4, 16}, {26, 3, 16}};
 
 }  // namespace
 
 int id_rx_config(int d, int m, int family) {
-  for (int t = 3 * family; t < 3 * family + 3; ++t) {
+  const int t0 = family == 0 ? 0 : RX_FAMILY0, t1 = family == 0 ? RX_FAMILY0 : RX_FAMILY0 + 3;
+  for (int t = t0; t < t1; ++t) {
     const RxShape& c = RX_SHAPES[t];
     if (d > 32 * c.rpl) continue;
-    for (int cl = 1; cl <= 16; cl *= 2)
-      if (m <= cl * c.nw * c.cpw) return 32 * t + cl;
-    return 0;
+    const int cap = c.nw * c.cpw;
+    const int cl = std::max(1, (m + cap - 1) / cap);
+    return cl <= 16 ? 32 * t + cl : 0;
   }
   return 0;
 }
@@ -528,15 +532,27 @@ int batched_id_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps
                   int cfg, cudaStream_t s, int spin, int hang_rank, int fail_p) {
   if (njobs <= 0) return 0;
   const int t = cfg / 32, cl = cfg % 32;
+#define RX_CASE(T, R, C, N) \
+  case T: return launch_rx<R, C, N>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p)
   switch (t) {
-    case 0: return launch_rx_cl<8, 16, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
-    case 1: return launch_rx_cl<16, 10, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
-    case 2: return launch_rx_cl<26, 7, 8>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
-    case 3: return launch_rx_cl<8, 8, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
-    case 4: return launch_rx_cl<16, 4, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
-    case 5: return launch_rx_cl<26, 3, 16>(cl, jobs, njobs, max_m, max_d, eps, rdiag, order, s, spin, hang_rank, fail_p);
+    RX_CASE(0, 4, 32, 8);
+    RX_CASE(1, 6, 24, 8);
+    RX_CASE(2, 8, 16, 8);
+    RX_CASE(3, 10, 16, 8);
+    RX_CASE(4, 12, 14, 8);
+    RX_CASE(5, 14, 12, 8);
+    RX_CASE(6, 16, 10, 8);
+    RX_CASE(7, 18, 9, 8);
+    RX_CASE(8, 20, 8, 8);
+    RX_CASE(9, 22, 8, 8);
+    RX_CASE(10, 24, 7, 8);
+    RX_CASE(11, 26, 7, 8);
+    RX_CASE(12, 8, 8, 16);
+    RX_CASE(13, 16, 4, 16);
+    RX_CASE(14, 26, 3, 16);
     default: return -1;
   }
+#undef RX_CASE
 }
 
 }  // namespace hssmf

@@ -168,13 +168,23 @@ def test_largest_node_shape_all_kernel_families(prec):
 
 
 @pytest.mark.parametrize("family,shapes", [
-    (-3, [(128, 128), (192, 100), (64, 7)]),          # 8 rows per lane, one CTA
-    (-3, [(256, 256), (200, 250), (250, 33)]),        # 8 rows per lane, cluster of 2
-    (-3, [(256, 2000), (130, 1500)]),                 # 8 rows per lane, cluster of 16
-    (-3, [(320, 64), (512, 60), (300, 17)]),          # 16 rows per lane, one CTA
-    (-3, [(512, 1200), (400, 700), (257, 300)]),      # 16 rows per lane, cluster of 16
-    (-3, [(832, 800), (704, 600), (600, 130)]),       # 26 rows per lane, cluster of 16
-    (-3, [(768, 300), (520, 256)]),                   # 26 rows per lane, cluster of 8
+    # 256-thread CTAs: every shape (rows per lane r = 4, 6, ..., 26), on the
+    # smallest cluster holding the widest job (any size from 1 to 16)
+    (-3, [(128, 128), (100, 90), (64, 7)]),           # r 4, one CTA
+    (-3, [(128, 700), (96, 300)]),                    # r 4, cluster of 3
+    (-3, [(192, 1000), (150, 400)]),                  # r 6, cluster of 6
+    (-3, [(256, 2000), (130, 1500)]),                 # r 8, cluster of 16
+    (-3, [(320, 64), (300, 17)]),                     # r 10, one CTA
+    (-3, [(320, 600), (260, 300)]),                   # r 10, cluster of 5
+    (-3, [(384, 1000), (330, 500)]),                  # r 12, cluster of 9
+    (-3, [(448, 700), (400, 300)]),                   # r 14, cluster of 8
+    (-3, [(512, 1200), (400, 700), (257, 300)]),      # r 16, cluster of 15
+    (-3, [(576, 700), (540, 200)]),                   # r 18, cluster of 10
+    (-3, [(640, 760), (600, 130)]),                   # r 20, cluster of 12
+    (-3, [(704, 600), (650, 300)]),                   # r 22, cluster of 10
+    (-3, [(768, 300), (520, 256)]),                   # r 24, cluster of 6
+    (-3, [(832, 800), (704, 600), (600, 130)]),       # r 26, cluster of 15
+    (-3, [(832, 896)]),                               # r 26, cluster of 16, every register column used
     (-4, [(128, 128), (192, 100), (64, 7)]),          # 512-thread CTAs: one CTA
     (-4, [(256, 2000), (130, 1500)]),                 # cluster of 16
     (-4, [(512, 1000), (400, 700), (257, 300)]),      # 16 rows per lane, cluster of 16
@@ -218,7 +228,7 @@ def test_exchange_register_id_exact_low_rank_zero_and_full_rank(family):
     assert res[2][0] == 40 and sorted(res[2][1].tolist()) == list(range(40))
 
 
-@pytest.mark.parametrize("cl", [2, 16])
+@pytest.mark.parametrize("cl", [2, 9, 16])
 def test_bounded_wait_runs_out_and_reports_timeout(cl):
     """Failure path of the bounded waits: one CTA of the cluster withholds
     its first proposal, every wait of the cluster runs out (a few thousand
