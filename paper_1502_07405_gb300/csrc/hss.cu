@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <type_traits>
@@ -79,6 +80,8 @@ struct Ring {  // job descriptors: pinned host staging -> device, reused after a
   char* h = nullptr;
   char* d = nullptr;
   size_t cap = 0, off = 0;
+  const cudaStream_t* side = nullptr;  // other streams whose launches read the ring
+  int nside = 0;
   bool grow(size_t need) {
     if (h) cudaFreeHost(h);
     if (d) cudaFree(d);
@@ -96,6 +99,7 @@ struct Ring {  // job descriptors: pinned host staging -> device, reused after a
     size_t bytes = std::max<size_t>((v.size() * sizeof(J) + ALIGN - 1) / ALIGN * ALIGN, ALIGN);
     if (off + bytes > cap) {
       cudaStreamSynchronize(s);
+      for (int q = 0; q < nside; ++q) cudaStreamSynchronize(side[q]);
       off = 0;
       if (bytes > cap && !grow(bytes)) return nullptr;
     }
@@ -216,6 +220,14 @@ struct HssState {
   Pool gws;  // split-K partial tiles of one GEMM launch (reused by the next)
   bool transposed_ready = false;  // ULV of the transposed F11 trees built
   Ring ring;
+  // side streams of the ID launches of one batch (independent nodes, run
+  // concurrently): fork marks the batch's job arrays on the device, join[k]
+  // the end of side stream k's launches; side_state 0 = not created yet,
+  // 1 = ready, -1 = unavailable (every launch stays on the main stream)
+  static constexpr int kSide = 16;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, join[kSide] = {};
+  int side_state = 0;
   int* d_ranks = nullptr;
   int* h_ranks = nullptr;
   int rank_cap = 0;
@@ -308,6 +320,14 @@ hssmf_status hss_device_init(hssmf_ctx& c) {
 void hss_release(hssmf_ctx& c) {
   if (!c.hss) return;
   HssState& H = *c.hss;
+  for (int k = 0; k < HssState::kSide; ++k) {
+    if (H.side[k]) {
+      cudaStreamSynchronize(H.side[k]);
+      cudaStreamDestroy(H.side[k]);
+    }
+    if (H.join[k]) cudaEventDestroy(H.join[k]);
+  }
+  if (H.fork) cudaEventDestroy(H.fork);
   H.fac.release();
   H.lvl.release();
   H.keep[0].release();
@@ -323,6 +343,46 @@ void hss_release(hssmf_ctx& c) {
 }
 
 namespace {
+
+bool ensure_side_streams(HssState& H) {
+  if (H.side_state != 0) return H.side_state > 0;
+  H.side_state = -1;  // partial creations are released with the state
+  if (cudaEventCreateWithFlags(&H.fork, cudaEventDisableTiming) != cudaSuccess) {
+    H.fork = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  for (int k = 0; k < HssState::kSide; ++k) {
+    if (cudaStreamCreateWithFlags(&H.side[k], cudaStreamNonBlocking) != cudaSuccess) {
+      H.side[k] = nullptr;
+      cudaGetLastError();
+      return false;
+    }
+    if (cudaEventCreateWithFlags(&H.join[k], cudaEventDisableTiming) != cudaSuccess) {
+      H.join[k] = nullptr;
+      cudaGetLastError();
+      return false;
+    }
+  }
+  H.ring.side = H.side;
+  H.ring.nside = HssState::kSide;
+  H.side_state = 1;
+  return true;
+}
+
+// The main stream waits for every side stream that received a launch.
+struct SideJoin {
+  HssState& H;
+  cudaStream_t main;
+  bool used[HssState::kSide] = {};
+  ~SideJoin() {
+    for (int k = 0; k < HssState::kSide; ++k)
+      if (used[k]) {
+        cudaEventRecord(H.join[k], H.side[k]);
+        cudaStreamWaitEvent(main, H.join[k], 0);
+      }
+  }
+};
 
 template <typename T>
 struct Ctx {  // per-call helpers
@@ -782,95 +842,138 @@ hssmf_status compress_level(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
           md.second = std::max(md.second, j.d);
         }
         c.prof.mark(PH_IDK, X.s);
-        // with profiling on, every ID launch is timed by its own events
-        auto timed = [&](int code, int cl, int nj, int dmax, int mmax, auto&& launch) -> int {
-          cudaEvent_t e0 = nullptr, e1 = nullptr;
-          const bool rec = c.prof.on && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
-          if (rec) cudaEventRecord(e0, X.s);
-          const int r = launch();
-          if (rec) {
-            cudaEventRecord(e1, X.s);
-            c.id_ev.push_back({e0, e1});
-            const double desc[5] = {(double)code, (double)cl, (double)nj, (double)dmax, (double)mmax};
-            c.id_ev_desc.insert(c.id_ev_desc.end(), desc, desc + 5);
-          }
-          return r;
-        };
-        for (auto& kv : rx_tier) {
-          const int mm = rx_md[kv.first].first, dd = rx_md[kv.first].second;
-          double* rdiag = (double*)H.rnd.alloc(sizeof(double) * kv.second.size() * std::max(std::min(mm, dd), 1));
-          int* order = (int*)H.rnd.alloc(sizeof(int) * kv.second.size() * std::max(mm, 1));
-          const IdJob* dj = H.ring.put(kv.second, X.s);
-          if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
-          if (timed(400 + (kv.first & 31), kv.first & 31, (int)kv.second.size(), dd, mm, [&] {
-                return batched_id_rx(dj, (int)kv.second.size(), mm, dd, eps, rdiag, order, kv.first, X.s, 0, -1, p);
-              }) < 0) {
-            for (int q : rx_ix[kv.first]) route_old((size_t)q);  // not schedulable: the other kernels
-          } else {
-            ++c.id_launches;
-          }
-        }
-        for (auto& kv : rr_tier) {
-          const int mm = rr_md[kv.first].first, dd = rr_md[kv.first].second;
-          double* rdiag = (double*)H.rnd.alloc(sizeof(double) * kv.second.size() * std::max(std::min(mm, dd), 1));
-          int* order = (int*)H.rnd.alloc(sizeof(int) * kv.second.size() * std::max(mm, 1));
-          const IdJob* dj = H.ring.put(kv.second, X.s);
-          if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
-          if (timed(200 + (kv.first & 31), kv.first & 31, (int)kv.second.size(), dd, mm, [&] {
-                return HssKern<T>::batched_id_rr(dj, (int)kv.second.size(), mm, dd, eps, rdiag, order, kv.first, X.s);
-              }) < 0)
-            return c.fail(HSSMF_ERR_CUDA, "register-resident ID launch failed");
-          ++c.id_launches;
-        }
-        for (int ti = 0; ti < 5; ++ti) {
-          if (smem_tier[ti].empty()) continue;
-          const int cl = 1 << ti;
-          const int bk = std::max(std::min(sm_m[ti], sm_d[ti]), 1);
-          double* rdiag = (double*)H.rnd.alloc(sizeof(double) * smem_tier[ti].size() * bk);
-          int* order = (int*)H.rnd.alloc(sizeof(int) * smem_tier[ti].size() * std::max(sm_m[ti], 1));
-          const IdJob* dj = H.ring.put(smem_tier[ti], X.s);
-          if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
-          if (timed(100 + cl, cl, (int)smem_tier[ti].size(), sm_d[ti], sm_m[ti], [&] {
-                return HssKern<T>::batched_id_smem(dj, (int)smem_tier[ti].size(), sm_m[ti], sm_d[ti], eps, rdiag,
-                                                   order, cl, X.s, p);
-              }) < 0) {
-            for (size_t q = 0; q < smem_tier[ti].size(); ++q) {  // not schedulable: the L2-resident kernels
-              const IdJob& j = smem_tier[ti][q];
-              const int t = j.m > 256 ? 1 : 0;
-              tier[t].push_back(j);
-              tier_ix[t].push_back(smem_ix[ti][q]);
-              route[smem_ix[ti][q]] = t == 0 ? 1 : 308;
-              tm[t] = std::max(tm[t], j.m);
-              td[t] = std::max(td[t], j.d);
+        {
+          // The launches of a batch hold independent nodes: each runs on a side
+          // stream of its own once the batch's job arrays (copied on the main
+          // stream) are on the device, the longest first, so that a launch of a
+          // few large clusters does not keep the rest of the GPU idle until it
+          // ends; the main stream waits for all of them (at the end of this
+          // scope, also on an early return) before it reads the ranks.
+          const bool side = ensure_side_streams(H);
+          SideJoin join{H, X.s};
+          int n_side = 0;
+          auto next_stream = [&]() -> cudaStream_t {
+            if (!side) return X.s;
+            const int k = n_side++ % HssState::kSide;
+            cudaEventRecord(H.fork, X.s);
+            cudaStreamWaitEvent(H.side[k], H.fork, 0);
+            join.used[k] = true;
+            return H.side[k];
+          };
+          // with profiling on, every ID launch is timed by its own events
+          auto timed = [&](int code, int cl, int nj, int dmax, int mmax, auto&& launch) -> int {
+            const cudaStream_t ss = next_stream();
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            const bool rec = c.prof.on && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+            if (rec) cudaEventRecord(e0, ss);
+            const int r = launch(ss);
+            if (rec) {
+              cudaEventRecord(e1, ss);
+              c.id_ev.push_back({e0, e1});
+              const double desc[5] = {(double)code, (double)cl, (double)nj, (double)dmax, (double)mmax};
+              c.id_ev_desc.insert(c.id_ev_desc.end(), desc, desc + 5);
             }
-          } else {
+            return r;
+          };
+          // shared-memory kernels (the largest nodes, the longest launches)
+          // first; jobs a failed launch below adds to a tier after its launch go
+          // in a second launch of that tier
+          size_t smem_done[5] = {0, 0, 0, 0, 0};
+          auto launch_smem = [&](int ti) -> bool {
+            const size_t from = smem_done[ti];
+            if (smem_tier[ti].size() <= from) return true;
+            smem_done[ti] = smem_tier[ti].size();
+            const std::vector<IdJob> jobs(smem_tier[ti].begin() + from, smem_tier[ti].end());
+            const int cl = 1 << ti, nj = (int)jobs.size();
+            int mm = 0, dd = 0;
+            for (const IdJob& j : jobs) {
+              mm = std::max(mm, j.m);
+              dd = std::max(dd, j.d);
+            }
+            double* rdiag = (double*)H.rnd.alloc(sizeof(double) * nj * std::max(std::min(mm, dd), 1));
+            int* order = (int*)H.rnd.alloc(sizeof(int) * nj * std::max(mm, 1));
+            const IdJob* dj = H.ring.put(jobs, X.s);
+            if (!dj || !rdiag || !order) return false;
+            if (timed(100 + cl, cl, nj, dd, mm, [&](cudaStream_t ss) {
+                  return HssKern<T>::batched_id_smem(dj, nj, mm, dd, eps, rdiag, order, cl, ss, p);
+                }) < 0) {
+              for (size_t q = from; q < smem_tier[ti].size(); ++q) {  // not schedulable: the L2-resident kernels
+                const IdJob& j = smem_tier[ti][q];
+                const int t = j.m > 256 ? 1 : 0;
+                tier[t].push_back(j);
+                tier_ix[t].push_back(smem_ix[ti][q]);
+                route[smem_ix[ti][q]] = t == 0 ? 1 : 308;
+                tm[t] = std::max(tm[t], j.m);
+                td[t] = std::max(td[t], j.d);
+              }
+            } else {
+              ++c.id_launches;
+            }
+            return true;
+          };
+          for (int ti = 4; ti >= 0; --ti)
+            if (!launch_smem(ti)) return c.fail(HSSMF_ERR_OOM, "ID scratch");
+          // exchange kernels, longest first (pivot steps x waves of clusters)
+          std::vector<int> rx_keys;
+          for (auto& kv : rx_tier) rx_keys.push_back(kv.first);
+          auto rx_len = [&](int key) {
+            return (double)rx_md[key].second * std::ceil((double)rx_tier[key].size() * (key & 31) / c.num_sms);
+          };
+          std::stable_sort(rx_keys.begin(), rx_keys.end(), [&](int a, int b) { return rx_len(a) > rx_len(b); });
+          for (int key : rx_keys) {
+            const std::vector<IdJob>& jobs = rx_tier[key];
+            const int mm = rx_md[key].first, dd = rx_md[key].second;
+            double* rdiag = (double*)H.rnd.alloc(sizeof(double) * jobs.size() * std::max(std::min(mm, dd), 1));
+            int* order = (int*)H.rnd.alloc(sizeof(int) * jobs.size() * std::max(mm, 1));
+            const IdJob* dj = H.ring.put(jobs, X.s);
+            if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
+            if (timed(400 + (key & 31), key & 31, (int)jobs.size(), dd, mm, [&](cudaStream_t ss) {
+                  return batched_id_rx(dj, (int)jobs.size(), mm, dd, eps, rdiag, order, key, ss, 0, -1, p);
+                }) < 0) {
+              for (int q : rx_ix[key]) route_old((size_t)q);  // not schedulable: the other kernels
+            } else {
+              ++c.id_launches;
+            }
+          }
+          for (auto& kv : rr_tier) {
+            const int mm = rr_md[kv.first].first, dd = rr_md[kv.first].second;
+            double* rdiag = (double*)H.rnd.alloc(sizeof(double) * kv.second.size() * std::max(std::min(mm, dd), 1));
+            int* order = (int*)H.rnd.alloc(sizeof(int) * kv.second.size() * std::max(mm, 1));
+            const IdJob* dj = H.ring.put(kv.second, X.s);
+            if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
+            if (timed(200 + (kv.first & 31), kv.first & 31, (int)kv.second.size(), dd, mm, [&](cudaStream_t ss) {
+                  return HssKern<T>::batched_id_rr(dj, (int)kv.second.size(), mm, dd, eps, rdiag, order, kv.first, ss);
+                }) < 0)
+              return c.fail(HSSMF_ERR_CUDA, "register-resident ID launch failed");
             ++c.id_launches;
           }
-        }
-        for (int t = 2; t >= 1; --t) {
-          if (tier[t].empty()) continue;
-          const int bk = std::max(std::min(tm[t], td[t]), 1);
-          double* rdiag = (double*)H.rnd.alloc(sizeof(double) * tier[t].size() * bk);
-          int* order = (int*)H.rnd.alloc(sizeof(int) * tier[t].size() * std::max(tm[t], 1));
-          const IdJob* dj = H.ring.put(tier[t], X.s);
-          if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
-          if (timed(t == 2 ? 316 : 308, t == 2 ? 16 : 8, (int)tier[t].size(), td[t], tm[t], [&] {
-                return HssKern<T>::batched_id_cluster(dj, (int)tier[t].size(), tm[t], td[t], eps, rdiag, order, X.s,
-                                                      t == 2 ? 16 : 8);
-              }) < 0) {
-            tier[0].insert(tier[0].end(), tier[t].begin(), tier[t].end());  // one CTA per job
-            for (int q : tier_ix[t]) route[q] = 1;
-            tm[0] = std::max(tm[0], tm[t]);
-            td[0] = std::max(td[0], td[t]);
+          for (int ti = 4; ti >= 0; --ti)  // nodes of failed exchange launches
+            if (!launch_smem(ti)) return c.fail(HSSMF_ERR_OOM, "ID scratch");
+          for (int t = 2; t >= 1; --t) {
+            if (tier[t].empty()) continue;
+            const int bk = std::max(std::min(tm[t], td[t]), 1);
+            double* rdiag = (double*)H.rnd.alloc(sizeof(double) * tier[t].size() * bk);
+            int* order = (int*)H.rnd.alloc(sizeof(int) * tier[t].size() * std::max(tm[t], 1));
+            const IdJob* dj = H.ring.put(tier[t], X.s);
+            if (!dj || !rdiag || !order) return c.fail(HSSMF_ERR_OOM, "ID scratch");
+            if (timed(t == 2 ? 316 : 308, t == 2 ? 16 : 8, (int)tier[t].size(), td[t], tm[t], [&](cudaStream_t ss) {
+                  return HssKern<T>::batched_id_cluster(dj, (int)tier[t].size(), tm[t], td[t], eps, rdiag, order, ss,
+                                                        t == 2 ? 16 : 8);
+                }) < 0) {
+              tier[0].insert(tier[0].end(), tier[t].begin(), tier[t].end());  // one CTA per job
+              for (int q : tier_ix[t]) route[q] = 1;
+              tm[0] = std::max(tm[0], tm[t]);
+              td[0] = std::max(td[0], td[t]);
+            }
           }
-        }
-        if (!tier[0].empty()) {
-          const IdJob* dj = H.ring.put(tier[0], X.s);
-          if (!dj) return c.fail(HSSMF_ERR_OOM, "job ring");
-          if (timed(1, 1, (int)tier[0].size(), td[0], tm[0], [&] {
-                return HssKern<T>::batched_id(dj, (int)tier[0].size(), tm[0], td[0], eps, X.s);
-              }) < 0)
-            return c.fail(HSSMF_ERR_ARG, "an HSS node is too large for the ID kernel");
+          if (!tier[0].empty()) {
+            const IdJob* dj = H.ring.put(tier[0], X.s);
+            if (!dj) return c.fail(HSSMF_ERR_OOM, "job ring");
+            if (timed(1, 1, (int)tier[0].size(), td[0], tm[0], [&](cudaStream_t ss) {
+                  return HssKern<T>::batched_id(dj, (int)tier[0].size(), tm[0], td[0], eps, ss);
+                }) < 0)
+              return c.fail(HSSMF_ERR_ARG, "an HSS node is too large for the ID kernel");
+          }
         }
         c.prof.mark(PH_ID, X.s);
         hssmf_status st = c.cuda_check(cudaMemcpyAsync(H.h_ranks, H.d_ranks, sizeof(int) * ij.size(),
