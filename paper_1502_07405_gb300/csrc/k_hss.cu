@@ -789,7 +789,9 @@ int HssKern<T>::batched_id_cluster(const IdJob* jobs, int njobs, int max_m, int 
 // k_cpqr_id_cluster.
 // ---------------------------------------------------------------------------
 constexpr int IDS_THREADS = 1024;
-constexpr size_t kIdSmemBudget = 200 * 1024;
+// dynamic shared memory of these kernels: the 227 KB a CTA can opt into,
+// less 1 KB for their static shared memory (at most 816 bytes)
+constexpr size_t kIdSmemBudget = 226 * 1024;
 
 // column stride of the resident matrix: 16-byte aligned columns
 __host__ __device__ inline int id_smem_ld(int d) { return (d + 3) & ~3; }
