@@ -323,6 +323,9 @@ hssmf_status hssmf_id_timeout_test(int cl, int spin);
  *   - HSSMF_ERR_TIMEOUT if a bounded wait inside the kernel ran out.
  *   - The operands are split once into BF16 term arrays and the product runs
  *     as a TMA-fed tcgen05 pipeline (K split when the output has few tiles).
+ *     b_exact + 2 (bit 1 set) runs instead the kernel the factorization
+ *     uses, which stages the FP32 tiles in shared memory and splits them
+ *     inside its loop (tests and profiling of that kernel).
  *   - Device scratch (term arrays, job and tile lists) is kept by the library
  *     between calls and reused; calls are serialized; synchronizes the
  *     stream. */

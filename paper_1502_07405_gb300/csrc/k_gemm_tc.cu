@@ -12,15 +12,17 @@
 // sampling matrix R of the FP32 form) uses one term, and its products drop to
 // three.
 //
-// One CTA computes one 128 x 128 tile of C over the whole K range, 32 K per
-// stage, two stages (96 KB of shared memory: two CTAs per SM): all 256
-// threads load a stage from global memory, split
-// it and store the BF16 terms into shared memory in the canonical K-major
-// layout (8 x 8 core matrices, no swizzle); one thread issues the tcgen05.mma
-// instructions of the stage and commits them to the stage's mbarrier, which
-// the threads wait on before refilling that stage.  The accumulator (128
-// lanes x 128 FP32 columns) is read back with tcgen05.ld and scattered to the
-// rows crow(i) of C.
+// One CTA computes one 128 x 128 tile of C over its K range, 16 K per stage
+// (two CTAs per SM).  The FP32 operand tiles of the stages ahead stream into
+// a ring of three shared-memory staging slots with 4-byte asynchronous copies
+// (cp.async, zero fill outside the matrices; any leading dimension, no
+// alignment needed), two stages in flight while the current one is split:
+// all 256 threads split a staged stage into its BF16 terms, stored in the
+// canonical K-major layout (8 x 8 core matrices, no swizzle) of one of two
+// term stages; one thread issues the tcgen05.mma instructions of the stage
+// and commits them to the stage's mbarrier, which the threads wait on before
+// refilling that term stage.  The accumulator (128 lanes x 128 FP32 columns)
+// is read back with tcgen05.ld and scattered to the rows crow(i) of C.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -37,12 +39,18 @@ namespace hssmf {
 
 namespace {
 
-constexpr int TC_M = 128, TC_N = 128, TC_K = 32;
+constexpr int TC_M = 128, TC_N = 128, TC_K = 16;
 constexpr int TC_THREADS = 256;
 constexpr int TC_TERM_BYTES = TC_M * TC_K * 2;          // one BF16 term of one operand tile
 constexpr int TC_STAGE_BYTES = 6 * TC_TERM_BYTES;       // 3 terms of A, 3 terms of B
 constexpr int TC_STAGES = 2;
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;  // + alignment slack
+// FP32 staging: TC_ST slots of [A | B] tiles, each TC_K rows of TC_SLD
+// floats (element (r, k) of op(X) at k TC_SLD + r: lanes along r read and
+// write without bank conflicts whichever direction of X is contiguous)
+constexpr int TC_ST = 3;
+constexpr int TC_SLD = TC_M + 1;
+constexpr int TC_STG = TC_K * TC_SLD;  // floats of one operand tile
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + TC_ST * 2 * TC_STG * 4 + 1024;  // + alignment slack
 constexpr unsigned TC_TMEM_COLS = 128;
 constexpr long long TC_SPIN = 1LL << 26;  // bound on every mbarrier wait
 
@@ -149,52 +157,97 @@ __device__ __forceinline__ void split8(const float* x, int nt, uint4* t0, uint4*
   }
 }
 
-// A 128 x TC_K operand tile in registers: each thread holds TC_CH chunks of
-// 8 consecutive k of one row.  Element (r, k) of the operand sits at
-// P[r * sr + k * sk] (one of sr, sk is 1; rc = rows contiguous); lanes walk
-// the contiguous direction.  Rows < R and k < K are valid; k beyond K reads
-// as zero, rows beyond R are not stored (their products land in output rows
-// or columns that are never stored).
-constexpr int TC_CH = TC_M * TC_K / 8 / TC_THREADS;
-
-__device__ __forceinline__ void chunk_pos(bool rc, int q4, int& r, int& kc) {
-  const int q = threadIdx.x + TC_THREADS * q4;
-  // rows contiguous: 32 consecutive rows per warp, same k chunk;
-  // k contiguous: 8 rows x 4 chunks per warp (one row group per store phase)
-  r = rc ? (q & 127) : ((q & 7) | ((q >> 5) << 3)) & 127;
-  kc = rc ? (q >> 7) : ((q >> 3) & 3) | ((q >> 9) << 2);
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void tile_fetch(const float* __restrict__ P, long long sr, long long sk, bool rc,
-                                           int r0, int R, int k0, int K, float (&x)[TC_CH][8]) {
-  static_assert(TC_K == 32 || TC_K == 64, "stage depth");
+// One thread's share of the staging copies of an operand: element (r, k)
+// of op(X) sits at P[r * sr + k * sk]; rc: rows contiguous (sr = 1), else k
+// contiguous (sk = 1).  Per K step the thread copies 8 elements:
+//   rc:  row tid % 128, k = tid / 128 + 2 e (a warp: 32 rows of one k);
+//   !rc: k = tid % 16, rows rb + off(e), off(e) = 8 (e % 2) + 32 (e / 2),
+//        rb = tid / 32 + 16 ((tid / 16) % 2) (a warp: 16 k of two rows 16
+//        apart).
+// Both write distinct banks of the [k][r] staging layout (row length
+// TC_SLD).  Elements in rows outside the operand are not copied (their
+// products land in rows or columns of C that are never stored); k past K is
+// zero-filled.  Addresses are formed once per tile and advanced per step.
+struct Feed {
+  const float* p;    // element 0 of the current K step
+  const float* base; // the operand's first element (the source of zero fills)
+  long long sk16;    // advance per K step
+  long long de;      // rc: advance between elements (2 sk)
+  long long sr8;     // !rc: 8 sr
+  uint32_t sdst;     // byte offset of element 0 in a staging tile
+  unsigned rmask;    // bit e: element e's row lies inside the operand
+  int kt;            // k of element 0 within the step
+};
+constexpr int TC_PER = TC_M * TC_K / TC_THREADS;  // elements per thread per operand tile
+static_assert(TC_K == 16 && TC_M == 128 && TC_THREADS == 256 && TC_PER == 8, "staging map");
+
+__device__ __forceinline__ Feed feed_init(const float* P, long long sr, long long sk, bool rc, int r0, int R,
+                                          int kbeg) {
+  Feed f;
+  const int t = threadIdx.x;
+  f.base = P;
+  f.sk16 = 16 * sk;
+  f.de = 2 * sk;
+  f.sr8 = 8 * sr;
+  if (rc) {
+    const int r = t & 127;
+    f.kt = t >> 7;
+    f.p = P + (long long)(r0 + r) * sr + (long long)(kbeg + f.kt) * sk;
+    f.rmask = r0 + r < R ? 0xFFu : 0u;
+    f.sdst = 4u * (uint32_t)(f.kt * TC_SLD + r);
+  } else {
+    const int rb = (t >> 5) + 16 * ((t >> 4) & 1);
+    f.kt = t & 15;
+    f.p = P + (long long)(r0 + rb) * sr + (long long)(kbeg + f.kt) * sk;
+    f.rmask = 0u;
 #pragma unroll
-  for (int q4 = 0; q4 < TC_CH; ++q4) {
-    int r, kc;
-    chunk_pos(rc, q4, r, kc);
-    const int gr = r0 + r, kb = k0 + 8 * kc;
-    const float* p = P + (long long)gr * sr;
+    for (int e = 0; e < TC_PER; ++e)
+      if (r0 + rb + 8 * (e & 1) + 32 * (e >> 1) < R) f.rmask |= 1u << e;
+    f.sdst = 4u * (uint32_t)(f.kt * TC_SLD + rb);
+  }
+  return f;
+}
+
+// The copies of one K step (kleft: K values left from the step's start)
+// into the staging tile at shared address tile.
+template <bool RC>
+__device__ __forceinline__ void feed_issue(const Feed& f, int kleft, uint32_t tile) {
+  const uint32_t d0 = tile + f.sdst;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[q4][j] = (gr < R && kb + j < K) ? __ldg(p + (long long)(kb + j) * sk) : 0.f;
+  for (int e = 0; e < TC_PER; ++e) {
+    if (!((f.rmask >> e) & 1)) continue;
+    const bool kv = RC ? f.kt + 2 * e < kleft : f.kt < kleft;
+    const float* src = RC ? f.p + e * f.de : f.p + (e & 1) * f.sr8 + (e >> 1) * 4 * f.sr8;
+    const uint32_t dst = d0 + 4u * (uint32_t)(RC ? 2 * e * TC_SLD : 8 * (e & 1) + 32 * (e >> 1));
+    cp_async4(dst, kv ? src : f.base, kv ? 4 : 0);
   }
 }
 
-// Splits the fetched chunks into nt BF16 terms and stores them into the
-// stage's term tiles (canonical K-major layout).
-__device__ __forceinline__ void tile_store(const float (&x)[TC_CH][8], bool rc, int r0, int R, int nt, char* dst) {
+// Splits a staged 128 x TC_K tile into nt BF16 terms (canonical K-major
+// layout): thread t takes row t % 128, k chunk t / 128 (8 values).
+__device__ __forceinline__ void tile_split(const float* stg, int nt, char* dst, bool row_in) {
+  static_assert(TC_M * TC_K / 8 == TC_THREADS, "one chunk per thread");
+  if (!row_in) return;  // rows outside the operand: not staged, not needed
+  const int r = threadIdx.x & 127, kc = threadIdx.x >> 7;
+  float x[8];
 #pragma unroll
-  for (int q4 = 0; q4 < TC_CH; ++q4) {
-    int r, kc;
-    chunk_pos(rc, q4, r, kc);
-    if (r0 + r >= R) continue;
-    uint4 t0, t1, t2;
-    split8(x[q4], nt, &t0, &t1, &t2);
-    const int o = tile_off(r, 8 * kc);
-    *reinterpret_cast<uint4*>(dst + o) = t0;
-    if (nt > 1) {
-      *reinterpret_cast<uint4*>(dst + TC_TERM_BYTES + o) = t1;
-      *reinterpret_cast<uint4*>(dst + 2 * TC_TERM_BYTES + o) = t2;
-    }
+  for (int j = 0; j < 8; ++j) x[j] = stg[(8 * kc + j) * TC_SLD + r];
+  uint4 t0, t1, t2;
+  split8(x, nt, &t0, &t1, &t2);
+  const int o = tile_off(r, 8 * kc);
+  *reinterpret_cast<uint4*>(dst + o) = t0;
+  if (nt > 1) {
+    *reinterpret_cast<uint4*>(dst + TC_TERM_BYTES + o) = t1;
+    *reinterpret_cast<uint4*>(dst + 2 * TC_TERM_BYTES + o) = t2;
   }
 }
 
@@ -245,36 +298,43 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
   const int nk = (kend - kbeg + TC_K - 1) / TC_K;
   bool ok = true;
   int issued = 0;  // K steps whose MMAs were issued and committed
-  // the global loads of stage t + 1 are issued before stage t is split and
-  // stored, so that they are in flight during its MMAs
-  float xa[TC_CH][8], xb[TC_CH][8];
-  if (nk > 0) {
-    tile_fetch(A, a_sr, a_sk, jb.ta == 0, m0, M, kbeg, kend, xa);
-    tile_fetch(B, b_sr, b_sk, jb.tb != 0, n0, N, kbeg, kend, xb);
+  float* stg = (float*)(smem + TC_STAGES * TC_STAGE_BYTES);
+  const bool a_rc = jb.ta == 0, b_rc = jb.tb != 0;
+  Feed fa = feed_init(A, a_sr, a_sk, a_rc, m0, M, kbeg);
+  Feed fb = feed_init(B, b_sr, b_sk, b_rc, n0, N, kbeg);
+  auto issue = [&](int u) {  // the copies of K step u into staging slot u % TC_ST (steps in order)
+    const uint32_t d = smem_u32(stg + (size_t)(u % TC_ST) * 2 * TC_STG);
+    const int kleft = kend - (kbeg + u * TC_K);
+    if (a_rc) feed_issue<true>(fa, kleft, d); else feed_issue<false>(fa, kleft, d);
+    if (b_rc) feed_issue<true>(fb, kleft, d + 4 * TC_STG); else feed_issue<false>(fb, kleft, d + 4 * TC_STG);
+    fa.p += fa.sk16;
+    fb.p += fb.sk16;
+  };
+  const bool a_row = m0 + (int)(threadIdx.x & 127) < M, b_row = n0 + (int)(threadIdx.x & 127) < N;
+  // one commit group per K step (empty past the end), so that waiting for
+  // all but the last TC_ST - 1 groups means step t has landed
+#pragma unroll
+  for (int u = 0; u < TC_ST - 1; ++u) {
+    if (u < nk) issue(u);
+    cp_commit();
   }
   for (int t = 0; t < nk; ++t) {
     const int st = t & 1;
     char* sa = smem + st * TC_STAGE_BYTES;
     char* sb = sa + 3 * TC_TERM_BYTES;
-    float ya[TC_CH][8], yb[TC_CH][8];
-    if (t + 1 < nk) {
-      tile_fetch(A, a_sr, a_sk, jb.ta == 0, m0, M, kbeg + (t + 1) * TC_K, kend, ya);
-      tile_fetch(B, b_sr, b_sk, jb.tb != 0, n0, N, kbeg + (t + 1) * TC_K, kend, yb);
-    }
-    // stage st is free once the MMAs of step t - 2 completed; after a wait
-    // that ran out nothing more is stored or issued (drain rule below)
+    // slot (t - 1) % TC_ST was split in step t - 1, before its closing barrier
+    if (t + TC_ST - 1 < nk) issue(t + TC_ST - 1);
+    cp_commit();
+    cp_wait<TC_ST - 1>();
+    __syncthreads();  // every thread's copies of step t are visible
+    // term stage st is free once the MMAs of step t - 2 completed; after a
+    // wait that ran out nothing more is stored or issued (drain rule below)
     const bool free_ok = t < TC_STAGES || mbar_wait(smem_u32(&s_bar[st]), ((t - TC_STAGES) >> 1) & 1);
     if (free_ok) {
-      tile_store(xa, jb.ta == 0, m0, M, na, sa);
-      tile_store(xb, jb.tb != 0, n0, N, nb, sb);
+      const float* src = stg + (size_t)(t % TC_ST) * 2 * TC_STG;
+      tile_split(src, na, sa, a_row);
+      tile_split(src + TC_STG, nb, sb, b_row);
     }
-#pragma unroll
-    for (int q4 = 0; q4 < TC_CH; ++q4)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        xa[q4][j] = ya[q4][j];
-        xb[q4][j] = yb[q4][j];
-      }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (!__syncthreads_and(free_ok)) {  // the same decision in every thread
       ok = false;
@@ -296,6 +356,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
       mma_commit(smem_u32(&s_bar[st]));
     }
   }
+  cp_wait<0>();  // no copy in flight past this point (also after a stop)
   // Drain rule: the last commit covers every MMA issued before it, so one
   // wait on it (bounded) covers exactly the work that was issued; after a
   // wait that ran out the loop stopped before storing or issuing more, the
@@ -439,9 +500,9 @@ extern "C" hssmf_status hssmf_gemm_f32(int transa, int transb, int m, int n, int
   j.lda = lda; j.ldb = ldb; j.ldc = ldc;
   j.M = m; j.N = n; j.K = k;
   j.ta = transa != 0; j.tb = transb != 0;
-  j.b_exact = b_exact != 0;
+  j.b_exact = (b_exact & 1) != 0;
   j.alpha = alpha; j.beta = beta;
-  if (k > 0 && gemm_tma_available()) {  // split operands + TMA/tcgen05 pipeline
+  if (k > 0 && !(b_exact & 2) && gemm_tma_available()) {  // split operands + TMA/tcgen05 pipeline
     unsigned* st = nullptr;
     if (cudaMalloc(&st, sizeof(unsigned)) != cudaSuccess) return HSSMF_ERR_CUDA;
     unsigned hs = 0;

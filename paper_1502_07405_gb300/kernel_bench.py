@@ -4,8 +4,9 @@ at a time on synthetic inputs (ncu captures, roofline checks).
     python -m paper_1502_07405_gb300.kernel_bench gemm --m 4096 --n 128 --k 8192 --b-exact
     python -m paper_1502_07405_gb300.kernel_bench id --d 832 --m 800 --jobs 8 --mode -1
 
-``gemm`` runs hssmf_gemm_f32 (the tensor-core GEMM of the FP32
-factorization; with --b-exact the shape of the sampling products S = U R of
+``gemm`` runs hssmf_gemm_f32 (the tensor-core GEMMs of the FP32 form: the
+TMA pipeline over pre-split operands, or with --in-loop the factorization's
+kernel; with --b-exact the shape of the sampling products S = U R of
 Section 4.3); ``id`` runs hssmf_batched_id on matrices with a geometric
 singular-value decay (Section 2.2 interpolative decompositions).  Prints one
 JSON line with the CUDA-event time per call (the calls synchronize; the
@@ -30,7 +31,7 @@ def _gemm(args):
                   C.c_void_p, C.c_longlong, C.c_float, C.c_void_p, C.c_longlong, C.c_int, C.c_void_p]
     m, n, k = args.m, args.n, args.k
     g = torch.Generator(device="cuda").manual_seed(0)
-    A = torch.randn(k, m, device="cuda", generator=g)  # column-major m x k
+    A = torch.randn(m * k, device="cuda", generator=g)  # column-major m x k (k x m with --ta)
     B = torch.randn(n, k, device="cuda", generator=g)  # column-major k x n
     if args.b_exact:
         B = B.to(torch.bfloat16).to(torch.float32)
@@ -39,7 +40,8 @@ def _gemm(args):
     for it in range(args.warmup + args.reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        st = f(0, 0, m, n, k, 1.0, A.data_ptr(), m, B.data_ptr(), k, 1.0, Cm.data_ptr(), m, int(args.b_exact), None)
+        st = f(args.ta, 0, m, n, k, 1.0, A.data_ptr(), k if args.ta else m, B.data_ptr(), k, 1.0, Cm.data_ptr(), m,
+               int(args.b_exact) | (2 if args.in_loop else 0), None)
         e1.record()
         torch.cuda.synchronize()
         if st != 0:
@@ -48,7 +50,8 @@ def _gemm(args):
             times.append(e0.elapsed_time(e1))
     ms = float(np.median(times))
     flops = 2.0 * m * n * k
-    return {"kernel": "gemm_tc", "m": m, "n": n, "k": k, "b_exact": bool(args.b_exact), "ms": ms,
+    return {"kernel": "k_gemm_tc" if args.in_loop else "k_gemm_tma", "m": m, "n": n, "k": k, "ta": args.ta,
+            "b_exact": bool(args.b_exact), "ms": ms,
             "tflops": flops / ms * 1e-9, "a_bytes": 4 * m * k, "a_gbs": 4.0 * m * k / ms * 1e-6}
 
 
@@ -106,6 +109,9 @@ def main():
     g.add_argument("--n", type=int, default=128)
     g.add_argument("--k", type=int, default=8192)
     g.add_argument("--b-exact", action="store_true")
+    g.add_argument("--ta", type=int, default=0, help="1: op(A) = A^T (A stored k x m)")
+    g.add_argument("--in-loop", action="store_true",
+                   help="the factorization's kernel (FP32 tiles staged and split in its loop)")
     g.add_argument("--reps", type=int, default=5)
     g.add_argument("--warmup", type=int, default=2)
     i = sub.add_parser("id")
