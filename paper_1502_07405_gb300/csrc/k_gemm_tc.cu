@@ -417,31 +417,44 @@ void gemm_tc(const GemmJob* jobs, const Tile* tiles, int ntiles, unsigned* statu
 }
 
 // Sum of the K-split partial tiles in split order (deterministic), then
-// C[crow(i), j] = alpha sum + beta C.  One CTA per output tile (ks = 0).
+// C[crow(i), j] = alpha sum + beta C.  CTA (x, y) takes output tile x
+// (ks = 0), columns 16 y .. 16 y + 15: 2048 outputs, 8 a thread, whose loads
+// are all issued before the first sum is used.
+constexpr int TC_RED_COLS = 16;
 __global__ void __launch_bounds__(256) k_gemm_tc_reduce(const GemmJob* __restrict__ jobs,
                                                         const Tile* __restrict__ tiles) {
   const Tile tl = tiles[blockIdx.x];
   const GemmJob jb = jobs[tl.job];
   const int S = jb.ksplit;
-  const int m0 = tl.tm * TC_M, n0 = tl.tn * TC_N;
+  const int m0 = tl.tm * TC_M, n0 = tl.tn * TC_N, c0 = blockIdx.y * TC_RED_COLS;
   const float* wp = jb.ws + (size_t)(tl.tm + tl.tn * jb.tiles_m) * S * (TC_M * TC_N);
   float* C = (float*)jb.C;
   const float alpha = (float)jb.alpha, beta = (float)jb.beta;
-  for (int e = threadIdx.x; e < TC_M * TC_N; e += blockDim.x) {
+  constexpr int PER = TC_M * TC_RED_COLS / 256;
+  float sum[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) sum[q] = 0.f;
+  for (int ks = 0; ks < S; ++ks)
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = c0 * TC_M + threadIdx.x + 256 * q;  // column-major within the tile
+      sum[q] += wp[(size_t)ks * (TC_M * TC_N) + e];
+    }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = c0 * TC_M + threadIdx.x + 256 * q;
     const int i = e % TC_M, c = e / TC_M;
     const int gi = m0 + i, gj = n0 + c;
     if (gi >= jb.M || gj >= jb.N) continue;
-    float sum = 0.f;
-    for (int q = 0; q < S; ++q) sum += wp[(size_t)q * (TC_M * TC_N) + e];
     const long long row = jb.crow ? jb.crow[gi] : gi;
     float* cp = C + row + (long long)gj * jb.ldc;
-    *cp = (jb.beta == 0.0) ? alpha * sum : alpha * sum + beta * *cp;
+    *cp = (jb.beta == 0.0) ? alpha * sum[q] : alpha * sum[q] + beta * *cp;
   }
 }
 
 void gemm_tc_reduce(const GemmJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s) {
   if (ntiles <= 0) return;
-  k_gemm_tc_reduce<<<ntiles, 256, 0, s>>>(jobs, tiles);
+  k_gemm_tc_reduce<<<dim3(ntiles, TC_N / TC_RED_COLS), 256, 0, s>>>(jobs, tiles);
   count_launch();
 }
 

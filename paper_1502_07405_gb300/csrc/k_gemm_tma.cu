@@ -290,25 +290,37 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_gemm_tma(const TmaJob* __rest
   }
 }
 
-// split-K partials of the TMA GEMM (128 x 128 stride per partial tile)
+// split-K partials of the TMA GEMM (128 x 128 stride per partial tile):
+// CTA (x, y) sums columns 16 y .. 16 y + 15 of output tile x, 8 outputs a
+// thread, every load issued before the first sum is used
+constexpr int TT_RED_COLS = 16;
 __global__ void __launch_bounds__(256) k_gemm_tma_reduce(const TmaJob* __restrict__ jobs,
                                                          const Tile* __restrict__ tiles) {
   const Tile tl = tiles[blockIdx.x];
   const TmaJob* jp = jobs + tl.job;
   const int S = jp->ksplit, bn = jp->bn;
+  const int c0 = blockIdx.y * TT_RED_COLS;
+  if (c0 >= bn) return;
   const int m0 = tl.tm * TT_M, n0 = tl.tn * bn;
   const float* wp = jp->ws + (size_t)(tl.tm + tl.tn * jp->tiles_m) * S * (TT_M * 128);
   float* C = (float*)jp->C;
   const float alpha = (float)jp->alpha, beta = (float)jp->beta;
-  for (int e = threadIdx.x; e < TT_M * bn; e += blockDim.x) {
+  constexpr int PER = TT_M * TT_RED_COLS / 256;
+  float sum[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) sum[q] = 0.f;
+  for (int ks = 0; ks < S; ++ks)
+#pragma unroll
+    for (int q = 0; q < PER; ++q) sum[q] += wp[(size_t)ks * (TT_M * 128) + c0 * TT_M + threadIdx.x + 256 * q];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = c0 * TT_M + threadIdx.x + 256 * q;
     const int i = e % TT_M, c = e / TT_M;
     const int gi = m0 + i, gj = n0 + c;
-    if (gi >= jp->M || gj >= jp->N) continue;
-    float sum = 0.f;
-    for (int q = 0; q < S; ++q) sum += wp[(size_t)q * (TT_M * 128) + e];
+    if (c >= bn || gi >= jp->M || gj >= jp->N) continue;
     const long long row = jp->crow ? jp->crow[gi] : gi;
     float* cp = C + row + (long long)gj * jp->ldc;
-    *cp = (jp->beta == 0.0) ? alpha * sum : alpha * sum + beta * *cp;
+    *cp = (jp->beta == 0.0) ? alpha * sum[q] : alpha * sum[q] + beta * *cp;
   }
 }
 
@@ -448,7 +460,7 @@ int gemm_tma_batch(const std::vector<GemmJob>& gj, TmaScratch& mem, unsigned* st
   k_gemm_tma<<<(int)tiles.size(), TT_THREADS, smem, s>>>(dtj, dt, stages, status);
   count_launch();
   if (dr) {
-    k_gemm_tma_reduce<<<(int)rtiles.size(), 256, 0, s>>>(dtj, dr);
+    k_gemm_tma_reduce<<<dim3((int)rtiles.size(), 128 / TT_RED_COLS), 256, 0, s>>>(dtj, dr);
     count_launch();
   }
   return 0;
