@@ -372,8 +372,9 @@ def run_ours(args):
     s64.close()
     ms = float(times[med])
     # roofline of the dominant kernel: the interpolative decompositions
-    # (algorithmic bytes m d + k (m - k) elements per ID, timed by CUDA events
-    # around the ID launches only)
+    # (algorithmic bytes m d + k (m - k) elements and flops per ID, over the
+    # wall time of the ID phases: CUDA events on the solver's stream around
+    # each batch's ID launches, which run concurrently on side streams)
     hbm, src = _peaks()
     t_id = phases["id_kernels"]
     achieved_bw = stp["id_bytes"] / (t_id * 1e-3) / 1e9 if t_id > 0 else 0.0
@@ -393,6 +394,8 @@ def run_ours(args):
             "alg_flops_per_launch": stp["id_flops"] / max(stp["id_launches"], 1),
             "alg_bytes_per_launch": stp["id_bytes"] / max(stp["id_launches"], 1),
             "avg_launch_ms": t_id / max(stp["id_launches"], 1),
+            "timing_note": ("achieved = flops of every ID / wall time of the ID phases; the launches of a batch "
+                            "overlap on side streams, so avg_launch_ms is wall time per launch"),
             "hbm_achieved_gbs": round(achieved_bw, 2), "hbm_frac": round(achieved_bw / hbm, 5),
             "hbm_peak": hbm, "hbm_peak_source": src,
             "share_of_factor": round(t_id / max(stp["t_factor_ms"], 1e-9), 3),
