@@ -1381,7 +1381,10 @@ hssmf_status ulv_factor_f11(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     if (X.oom) return c.fail(HSSMF_ERR_OOM, "device memory exhausted during the ULV factorization");
     for (int j0 = 0; j0 < max_nk; j0 += NBQ) {
       std::vector<LqJob> cur = lq;  // staged again each step: the job ring may wrap
-      X.launch(cur, [&](const LqJob* d, int n) { HssKern<T>::lq_panel(d, n, j0, NBQ, X.s); });
+      int max_n = 0;
+      for (const LqJob& J : lq)
+        if (j0 < J.m - J.k) max_n = std::max(max_n, J.m - j0);
+      X.launch(cur, [&](const LqJob* d, int n) { HssKern<T>::lq_panel(d, n, j0, NBQ, max_n, X.s); });
       for (size_t q = 0; q < lq.size(); ++q) {
         const LqJob& J = lq[q];
         const int nk = J.m - J.k;
@@ -1419,7 +1422,10 @@ hssmf_status ulv_factor_f11(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     for (const LuJob& J : lu) max_m = std::max(max_m, J.m);
     for (int k0 = 0; k0 < max_m; k0 += NBQ) {
       std::vector<LuJob> cur = lu;
-      X.launch(cur, [&](const LuJob* d, int n) { HssKern<T>::lu_panel(d, n, k0, NBQ, c.d_status, X.s); });
+      int max_n = 0;
+      for (const LuJob& J : lu)
+        if (k0 < J.m) max_n = std::max(max_n, J.m - k0);
+      X.launch(cur, [&](const LuJob* d, int n) { HssKern<T>::lu_panel(d, n, k0, NBQ, c.d_status, max_n, X.s); });
       cur = lu;
       X.launch(cur, [&](const LuJob* d, int n) { HssKern<T>::lu_trsm(d, n, k0, NBQ, max_m, X.s); });
       for (const LuJob& J : lu) {

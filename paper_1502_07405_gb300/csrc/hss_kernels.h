@@ -173,10 +173,12 @@ struct HssKern {
   // reflectors of the panel rows (applied inside the panel), the block
   // reflector's V (nb x (m - j0), ld nb, explicit ones and zeros) into
   // Vb + vb_off[j] and its triangular factor T (nb x nb) into Tb + t_off[j].
-  static void lq_panel(const LqJob* jobs, int njobs, int j0, int nb, cudaStream_t s);
+  // (max_n: the largest m - j0 of the jobs still in range: sizes the
+  // shared-memory form of the kernel)
+  static void lq_panel(const LqJob* jobs, int njobs, int j0, int nb, int max_n, cudaStream_t s);
   // Blocked LU: panel columns [k0, k0 + nb) (pivot search over all rows),
   // then the row block of U right of the panel.
-  static void lu_panel(const LuJob* jobs, int njobs, int k0, int nb, unsigned* status, cudaStream_t s);
+  static void lu_panel(const LuJob* jobs, int njobs, int k0, int nb, unsigned* status, int max_n, cudaStream_t s);
   static void lu_trsm(const LuJob* jobs, int njobs, int k0, int nb, int max_m, cudaStream_t s);
   // row permutation of each finished LU from its interchanges
   static void lu_perm(const LuJob* jobs, int njobs, cudaStream_t s);

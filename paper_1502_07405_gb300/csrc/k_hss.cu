@@ -1823,10 +1823,118 @@ __global__ void __launch_bounds__(256) k_lq_panel(const LqJob* __restrict__ jobs
   }
 }
 
+// The same panel with the panel rows staged in shared memory: the kernel
+// above walks rows of the column-major Dt (one 32-byte sector per element);
+// here the w x n panel is loaded once with coalesced column reads
+// (P[c * 33 + q] = Dt(j0 + q, j0 + c)), factored in shared memory with the
+// same thread assignment and operation order (the same results), and
+// written back once.
+constexpr size_t kPanelSmemMax = 212 * 1024;  // dynamic part; the static arrays take up to 9 KB
 template <typename T>
-void HssKern<T>::lq_panel(const LqJob* jobs, int njobs, int j0, int nb, cudaStream_t s) {
+__global__ void __launch_bounds__(256) k_lq_panel_s(const LqJob* __restrict__ jobs, int j0, int nb) {
+  const LqJob jb = jobs[blockIdx.x];
+  const int m = jb.m, nk = jb.m - jb.k;
+  if (j0 >= nk) return;
+  const int j1 = min(j0 + nb, nk), w = j1 - j0, n = m - j0;
+  T* D = (T*)jb.Dt;
+  T* tau = (T*)jb.tau;
+  T* Vb = (T*)jb.Vb;
+  T* Tb = (T*)jb.Tb + (long long)(j0 / nb) * nb * nb;  // T of this panel, kept for the solve
+  extern __shared__ __align__(16) unsigned char lq_raw[];
+  T* P = (T*)lq_raw;
+  __shared__ T sh[33];
+  __shared__ T sT[32][33];
+  __shared__ T sg[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (long long e = threadIdx.x; e < 32LL * n; e += blockDim.x) {
+    const int q = (int)(e & 31), c = (int)(e >> 5);
+    if (q < w) P[c * 33 + q] = D[(j0 + q) + (long long)(j0 + c) * m];
+  }
+  __syncthreads();
+  for (int i = 0; i < w; ++i) {  // panel row i: row j0 + i of Dt, its diagonal at panel column i
+    T part = T(0);
+    for (int c = i + 1 + threadIdx.x; c < n; c += blockDim.x) {
+      const T v = P[c * 33 + i];
+      part += v * v;
+    }
+    const T alpha = P[i * 33 + i];
+    const T xn2 = block_sum_t<T>(part, sh);
+    T t = T(0), beta = alpha, scl = T(0);
+    if (xn2 > T(0)) {
+      const T b = sqrt(alpha * alpha + xn2);
+      beta = alpha >= T(0) ? -b : b;
+      t = (beta - alpha) / beta;
+      scl = T(1) / (alpha - beta);
+    }
+    for (int c = i + 1 + threadIdx.x; c < n; c += blockDim.x) P[c * 33 + i] *= scl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      P[i * 33 + i] = beta;
+      tau[j0 + i] = t;
+    }
+    if (t != T(0)) {  // panel rows below i: row_r[i:] -= t (row_r . v) v
+      for (int r = i + 1 + wid; r < w; r += nw) {
+        T sacc = T(0);
+        for (int c = i + 1 + lane; c < n; c += 32) sacc += P[c * 33 + r] * P[c * 33 + i];
+        sacc = wsum<T>(sacc) + P[i * 33 + r];
+        const T f = t * sacc;
+        __syncwarp();
+        if (lane == 0) P[i * 33 + r] -= f;
+        for (int c = i + 1 + lane; c < n; c += 32) P[c * 33 + r] -= f * P[c * 33 + i];
+      }
+    }
+    __syncthreads();
+  }
+  for (long long e = threadIdx.x; e < 32LL * n; e += blockDim.x) {
+    const int q = (int)(e & 31), c = (int)(e >> 5);
+    if (q < w) D[(j0 + q) + (long long)(j0 + c) * m] = P[c * 33 + q];
+  }
+  // V of the block reflector (rows beyond w are zero)
+  auto V = [&](int q, int c) -> T { return q >= w ? T(0) : c < q ? T(0) : c == q ? T(1) : P[c * 33 + q]; };
+  for (long long e = threadIdx.x; e < (long long)nb * n; e += blockDim.x) {
+    const int q = (int)(e % nb), c = (int)(e / nb);
+    Vb[q + (long long)c * nb] = V(q, c);
+  }
+  // Gram entries G(p, q) = V(p, :) . V(q, :) for p < q (warp per pair)
+  for (int pq = wid; pq < w * w; pq += nw) {
+    const int p = pq % w, q = pq / w;
+    if (p >= q) continue;
+    T sacc = T(0);
+    for (int c = q + lane; c < n; c += 32) sacc += V(p, c) * V(q, c);
+    sacc = wsum<T>(sacc);
+    if (lane == 0) sT[p][q] = sacc;  // holds G until T(:, q) replaces it below
+  }
+  __syncthreads();
+  // T(q, q) = tau_q; T(0:q, q) = -tau_q T(0:q, 0:q) G(0:q, q)
+  for (int q = 0; q < w; ++q) {
+    if (threadIdx.x < q) sg[threadIdx.x] = sT[threadIdx.x][q];
+    __syncthreads();
+    const T tq = tau[j0 + q];
+    if (threadIdx.x < q) {
+      const int pp = threadIdx.x;
+      T sacc = T(0);
+      for (int r = pp; r < q; ++r) sacc += sT[pp][r] * sg[r];
+      sT[pp][q] = -tq * sacc;
+    }
+    if (threadIdx.x == 0) sT[q][q] = tq;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int pp = e % nb, q = e / nb;
+    Tb[e] = (pp < w && q < w && pp <= q) ? sT[pp][q] : T(0);
+  }
+}
+
+template <typename T>
+void HssKern<T>::lq_panel(const LqJob* jobs, int njobs, int j0, int nb, int max_n, cudaStream_t s) {
   if (njobs <= 0) return;
-  k_lq_panel<T><<<njobs, 256, 0, s>>>(jobs, j0, nb);
+  const size_t smem = sizeof(T) * 33 * (size_t)std::max(max_n, 1);
+  if (nb <= 32 && smem <= kPanelSmemMax &&
+      set_func_attr((const void*)k_lq_panel_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmemMax)) {
+    k_lq_panel_s<T><<<njobs, 256, smem, s>>>(jobs, j0, nb);
+  } else {
+    k_lq_panel<T><<<njobs, 256, 0, s>>>(jobs, j0, nb);
+  }
   count_launch();
 }
 
@@ -1893,10 +2001,95 @@ __global__ void __launch_bounds__(256) k_lu_panel(const LuJob* __restrict__ jobs
   }
 }
 
+// The same panel staged in shared memory: rows [k0, m) of the panel
+// columns, L[c * n + r] = A(k0 + r, k0 + c), loaded and written back once
+// with coalesced column accesses; the same thread assignment and operation
+// order as above (the same pivots and factors).
 template <typename T>
-void HssKern<T>::lu_panel(const LuJob* jobs, int njobs, int k0, int nb, unsigned* status, cudaStream_t s) {
+__global__ void __launch_bounds__(256) k_lu_panel_s(const LuJob* __restrict__ jobs, int k0, int nb,
+                                                    unsigned* status) {
+  const LuJob jb = jobs[blockIdx.x];
+  const int m = jb.m;
+  if (k0 >= m) return;
+  const int k1 = min(k0 + nb, m), w = k1 - k0, n = m - k0;
+  T* A = (T*)jb.A;
+  const long long ld = m;
+  extern __shared__ __align__(16) unsigned char lu_raw[];
+  T* L = (T*)lu_raw;
+  __shared__ T s_v[8];
+  __shared__ int s_i[8];
+  __shared__ int s_p;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (long long e = threadIdx.x; e < (long long)w * n; e += blockDim.x) {
+    const int c = (int)(e / n), r = (int)(e % n);
+    L[e] = A[(k0 + r) + (long long)(k0 + c) * ld];
+  }
+  __syncthreads();
+  for (int j = k0; j < k1; ++j) {
+    const int jj = j - k0;
+    const T* Lj = L + (long long)jj * n - k0;  // Lj[r] = A(r, j) for r >= k0
+    T bv = T(-1);
+    int bi = m;
+    for (int r = j + threadIdx.x; r < m; r += blockDim.x) {
+      const T a = tabs(Lj[r]);
+      if (a > bv) { bv = a; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_down_sync(0xffffffffu, bv, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_v[wid] = bv; s_i[wid] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T b = s_v[0];
+      int ix = s_i[0];
+      for (int w2 = 1; w2 < (int)(blockDim.x >> 5); ++w2)
+        if (s_v[w2] > b || (s_v[w2] == b && s_i[w2] < ix)) { b = s_v[w2]; ix = s_i[w2]; }
+      if (!(b > T(0)) || !isfinite(b)) {
+        atomicOr(status, b == T(0) ? ST_ZERO_PIVOT : ST_NONFINITE);
+        ix = j;
+      }
+      s_p = ix;
+      jb.piv[j] = ix;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j)  // the panel columns now; the others in k_lu_trsm after the panel
+      for (int c = threadIdx.x; c < w; c += blockDim.x) {
+        T* Lc = L + (long long)c * n - k0;
+        const T t = Lc[j];
+        Lc[j] = Lc[p];
+        Lc[p] = t;
+      }
+    __syncthreads();
+    const T dj = Lj[j];
+    const T inv = dj != T(0) ? T(1) / dj : T(0);
+    for (int r = j + 1 + threadIdx.x; r < m; r += blockDim.x) {
+      T* Lr = L + r - k0;
+      const T l = Lr[(long long)jj * n] * inv;
+      Lr[(long long)jj * n] = l;
+      for (int c = jj + 1; c < w; ++c) Lr[(long long)c * n] -= l * Lj[j + (long long)(c - jj) * n];
+    }
+    __syncthreads();
+  }
+  for (long long e = threadIdx.x; e < (long long)w * n; e += blockDim.x) {
+    const int c = (int)(e / n), r = (int)(e % n);
+    A[(k0 + r) + (long long)(k0 + c) * ld] = L[e];
+  }
+}
+
+template <typename T>
+void HssKern<T>::lu_panel(const LuJob* jobs, int njobs, int k0, int nb, unsigned* status, int max_n,
+                          cudaStream_t s) {
   if (njobs <= 0) return;
-  k_lu_panel<T><<<njobs, 256, 0, s>>>(jobs, k0, nb, status);
+  const size_t smem = sizeof(T) * (size_t)nb * (size_t)std::max(max_n, 1);
+  if (smem <= kPanelSmemMax &&
+      set_func_attr((const void*)k_lu_panel_s<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmemMax)) {
+    k_lu_panel_s<T><<<njobs, 256, smem, s>>>(jobs, k0, nb, status);
+  } else {
+    k_lu_panel<T><<<njobs, 256, 0, s>>>(jobs, k0, nb, status);
+  }
   count_launch();
 }
 
