@@ -510,7 +510,7 @@ struct Ctx {  // per-call helpers
     if (cj.empty()) return;
     std::vector<Tile> tiles;
     for (size_t i = 0; i < cj.size(); ++i)
-      for (int b = 0; b < ceil_div(cj[i].cols, 32); ++b)
+      for (int b = 0; b < ceil_div(cj[i].cols, 32); b += COPY_TN)
         for (int a = 0; a < ceil_div(cj[i].rows, 32); ++a) tiles.push_back(Tile{(int)i, a, b});
     const CopyJob* d = H.ring.put(cj, s);
     const Tile* t = H.ring.put(tiles, s);

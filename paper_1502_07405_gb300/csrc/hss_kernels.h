@@ -4,6 +4,8 @@
 
 namespace hssmf {
 
+constexpr int COPY_TN = 4;  // 32-column tiles of one copy CTA
+
 struct CopyJob {  // dst(i, j) = src'(rmap[i], cmap[j]); source columns >= split come from src2
   const void* src;
   const void* src2;  // second source (columns split.. of the concatenation), lds2
@@ -139,7 +141,8 @@ int batched_id_rx(const IdJob* jobs, int njobs, int max_m, int max_d, double eps
 
 template <typename T>
 struct HssKern {
-  // tiles: 32 x 32 destination tiles (job, tm, tn)
+  // tiles: destination strips (job, tm, tn) of 32 rows x COPY_TN 32-column
+  // tiles starting at tile column tn (a multiple of COPY_TN)
   static void copy(const CopyJob* jobs, const Tile* tiles, int ntiles, cudaStream_t s);
   static void int_gather(const IntGatherJob* jobs, int njobs, cudaStream_t s);
   static void philox(const PhiloxJob* jobs, int njobs, int max_rows, unsigned long long seed,

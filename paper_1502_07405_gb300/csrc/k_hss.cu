@@ -232,8 +232,9 @@ __device__ __forceinline__ float gauss_t<float>(unsigned long long seed, unsigne
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Gather/transposing copies over 32 x 32 tiles of the destination (tile list
-// entries (job, tm, tn)); transposed sources go through a shared-memory tile
+// Gather/transposing copies over 32 x (32 COPY_TN) strips of the destination
+// (tile list entries (job, tm, tn): rows 32 tm.., the COPY_TN 32-column tiles
+// from tn); transposed sources go through a shared-memory tile
 // so that both the reads and the writes are coalesced.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(256) k_copy(const CopyJob* __restrict__ jobs, 
   const CopyJob jb = jobs[tl.job];
   __shared__ T tile[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int i0 = tl.tm * 32, j0 = tl.tn * 32;
+  const int i0 = tl.tm * 32;
   T* dst = (T*)jb.dst;
   // source element (si, sj) of the concatenated source: its address
   auto src_at = [&](int i, int j) -> const T* {
@@ -257,29 +258,42 @@ __global__ void __launch_bounds__(256) k_copy(const CopyJob* __restrict__ jobs, 
     }
     return jb.src_trans ? sp + sj + (long long)si * lds : sp + si + (long long)sj * lds;
   };
-  if (!jb.src_trans) {
+  if (!jb.src_trans) {  // every load of the CTA's COPY_TN tiles issued before the first store
+    const int i = i0 + tx;
+    T v[COPY_TN][4];
+#pragma unroll
+    for (int q = 0; q < COPY_TN; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = (tl.tn + q) * 32 + ty + 8 * u;
+        v[q][u] = (i < jb.rows && j < jb.cols) ? *src_at(i, j) : T(0);
+      }
+#pragma unroll
+    for (int q = 0; q < COPY_TN; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = (tl.tn + q) * 32 + ty + 8 * u;
+        if (i < jb.rows && j < jb.cols) dst[i + (long long)j * jb.ldd] = jb.scale_neg ? -v[q][u] : v[q][u];
+      }
+    return;
+  }
+  for (int q = 0; q < COPY_TN; ++q) {
+    const int j0 = (tl.tn + q) * 32;
+    if (j0 >= jb.cols) break;  // uniform in the CTA
+    for (int ii = ty; ii < 32; ii += 8) {  // lanes along the source's contiguous index (j)
+      const int i = i0 + ii, j = j0 + tx;
+      if (i < jb.rows && j < jb.cols) tile[ii][tx] = *src_at(i, j);
+    }
+    __syncthreads();
     const int i = i0 + tx;
     for (int jj = ty; jj < 32; jj += 8) {
       const int j = j0 + jj;
       if (i < jb.rows && j < jb.cols) {
-        const T v = *src_at(i, j);
+        const T v = tile[tx][jj];
         dst[i + (long long)j * jb.ldd] = jb.scale_neg ? -v : v;
       }
     }
-    return;
-  }
-  for (int ii = ty; ii < 32; ii += 8) {  // lanes along the source's contiguous index (j)
-    const int i = i0 + ii, j = j0 + tx;
-    if (i < jb.rows && j < jb.cols) tile[ii][tx] = *src_at(i, j);
-  }
-  __syncthreads();
-  const int i = i0 + tx;
-  for (int jj = ty; jj < 32; jj += 8) {
-    const int j = j0 + jj;
-    if (i < jb.rows && j < jb.cols) {
-      const T v = tile[tx][jj];
-      dst[i + (long long)j * jb.ldd] = jb.scale_neg ? -v : v;
-    }
+    __syncthreads();
   }
 }
 
