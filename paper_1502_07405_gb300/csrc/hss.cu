@@ -469,6 +469,12 @@ struct Ctx {  // per-call helpers
   }
   // Tensor-core launches with fewer tiles than about two CTAs per SM split
   // the K range of their long-K jobs (partials summed in split order)
+  // K split of a tensor-core launch: the tiles run about two CTAs per SM, so
+  // t tiles take ceil(t / slots) waves; splitting K in S shortens each CTA
+  // about S times but multiplies the CTAs and adds a reduction of S t
+  // partial tiles, so S (1..8) minimizes, in units of one unsplit CTA,
+  // ceil(S t / slots) / S + 0.03 S t / slots (S > 1); a job is split at most
+  // K / 128 ways (eight 16-deep steps per part at least).
   void split_k() {
     static int nsm = 0;
     if (!nsm) {
@@ -479,13 +485,22 @@ struct Ctx {  // per-call helpers
     long long t0 = 0;
     for (const GemmJob& j : gj)
       if (j.N > GEMV_MAX_N) t0 += (long long)ceil_div(j.M, GEMM_TILE_TC) * ceil_div(j.N, GEMM_TILE_TC);
-    const long long target = 2LL * nsm;
-    if (t0 == 0 || t0 >= target) return;
-    const int S = (int)std::min<long long>(8, (target + t0 - 1) / t0);
+    if (t0 == 0) return;
+    const long long slots = 2LL * nsm;
+    int S = 1;
+    double best = 1e300;
+    for (int q = 1; q <= 8; ++q) {
+      const double cost = (double)((q * t0 + slots - 1) / slots) / q + (q > 1 ? 0.03 * q * t0 / slots : 0.0);
+      if (cost < best - 1e-9) {
+        best = cost;
+        S = q;
+      }
+    }
+    if (S < 2) return;
     H.gws.reset();
     for (GemmJob& j : gj) {
-      if (j.N <= GEMV_MAX_N || j.K < 512) continue;
-      const int sj = std::min(S, j.K / 256);
+      if (j.N <= GEMV_MAX_N) continue;
+      const int sj = std::min(S, j.K / 128);
       if (sj < 2) continue;
       const int tm = ceil_div(j.M, GEMM_TILE_TC), tn = ceil_div(j.N, GEMM_TILE_TC);
       float* ws = (float*)H.gws.alloc(sizeof(float) * (size_t)tm * tn * sj * GEMM_TILE_TC * GEMM_TILE_TC);
