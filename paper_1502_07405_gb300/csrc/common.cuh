@@ -26,7 +26,9 @@ struct GemmJob {
   int M, N, K;
   int ta, tb;  // 1 = use the transpose
   // FP32 tensor-core path: operand values exactly representable in BF16
-  // (one split term instead of three)
+  // (one split term instead of three); b_exact = 2: B is stored as BF16
+  // (op(B)(k, j) at B[k + j ldb]: ldb a multiple of 8, B 16-byte aligned;
+  // tensor-core tiles only)
   int a_exact, b_exact;
   double alpha, beta;
   // tensor-core split-K (ksplit > 1): tile (tm, tn) of split ks writes its

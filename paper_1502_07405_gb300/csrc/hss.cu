@@ -119,6 +119,10 @@ struct Ring {  // job descriptors: pinned host staging -> device, reused after a
   }
 };
 
+// leading dimension of a child's sampling matrix R(I^upd_child, :) stored as
+// BF16 in the FP32 form: 16-byte aligned columns for 16-byte copies
+inline int rch_ld(int nu) { return (nu + 7) & ~7; }
+
 struct NodeRt {
   int m = 0, mc = 0, n = 0;  // ID row counts (S^r, S^c) and node size
   int kr = 0, kc = 0;
@@ -434,7 +438,7 @@ struct Ctx {  // per-call helpers
       std::vector<Tile> tiles, rtiles;
       if (pass == K_TILES && tc) split_k();
       for (size_t i = 0; i < gj.size(); ++i) {
-        const bool mv = gj[i].N <= GEMV_MAX_N;
+        const bool mv = gj[i].N <= GEMV_MAX_N && gj[i].b_exact != 2;  // BF16 B: tensor-core tiles only
         if (mv != (pass == K_GEMV)) continue;
         if (mv) {
           const int rows = gj[i].ta ? GEMV_ROWS_T : GEMV_ROWS_N;
@@ -563,7 +567,9 @@ void sample_fronts(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
     for (int k = 0; k < f.nchild; ++k) {
       const DFront& ch = c.fronts_host[f.child[k]];
       if (ch.nu == 0) continue;
-      pj.push_back(PhiloxJob{X.ints(F->rch_off[k]), F->Rch[k], ch.nu, ch.nu, c0, c1, 0});
+      const bool b16 = std::is_same<T, float>::value;
+      pj.push_back(PhiloxJob{X.ints(F->rch_off[k]), F->Rch[k], b16 ? rch_ld(ch.nu) : ch.nu, ch.nu, c0, c1,
+                             b16 ? 1 : 0});
       max_rows = std::max(max_rows, ch.nu);
     }
     sj.push_back(SampleAJob{F->Sr, F->Sc, F->R, F->nf, F->f, c0, c1, 0});
@@ -579,12 +585,15 @@ void sample_fronts(Ctx<T>& X, const std::vector<FrontRt*>& fs) {
       const int c0 = F->dprev, w = F->d - F->dprev;
       if (ch.nu == 0 || w <= 0) continue;
       const T* U = X.arena() + ch.u_off;
-      const T* Rk = (const T*)F->Rch[k] + (long long)c0 * ch.nu;
+      // FP32 form: R_child in BF16 (b_exact 2); FP64 form: R_child in T
+      const bool b16 = std::is_same<T, float>::value;
+      const long long ldr = b16 ? rch_ld(ch.nu) : ch.nu;
+      const void* Rk = (const char*)F->Rch[k] + (b16 ? 2 : sizeof(T)) * (size_t)c0 * ldr;
       const int* pos = X.ints(F->pos_off[k]);
-      X.gemm(U, ch.u_ld, 0, Rk, ch.nu, 0, (T*)F->Sr + (long long)c0 * F->nf, F->nf, ch.nu, w, ch.nu,
-             1.0, 1.0, pos, 1);
-      X.gemm(U, ch.u_ld, 1, Rk, ch.nu, 0, (T*)F->Sc + (long long)c0 * F->nf, F->nf, ch.nu, w, ch.nu,
-             1.0, 1.0, pos, 1);
+      X.gemm(U, ch.u_ld, 0, Rk, ldr, 0, (T*)F->Sr + (long long)c0 * F->nf, F->nf, ch.nu, w, ch.nu,
+             1.0, 1.0, pos, b16 ? 2 : 1);
+      X.gemm(U, ch.u_ld, 1, Rk, ldr, 0, (T*)F->Sc + (long long)c0 * F->nf, F->nf, ch.nu, w, ch.nu,
+             1.0, 1.0, pos, b16 ? 2 : 1);
     }
     X.flush_gemm();
   }
@@ -604,7 +613,19 @@ void ensure_cols(Ctx<T>& X, FrontRt& F, const FrontSym& f) {
   grow(F.R, F.nf);
   grow(F.Sr, F.nf);
   grow(F.Sc, F.nf);
-  for (int k = 0; k < f.nchild; ++k) grow(F.Rch[k], X.c.fronts_host[f.child[k]].nu);
+  for (int k = 0; k < f.nchild; ++k) {
+    const int nu = X.c.fronts_host[f.child[k]].nu;
+    if (std::is_same<T, float>::value) {  // BF16, leading dimension rch_ld (16-byte aligned columns)
+      const int ld = rch_ld(nu);
+      void* q = X.H.lvl.alloc(2 * (size_t)ld * na);
+      if (!q) X.oom = true;
+      if (F.Rch[k] && F.dprev > 0 && q)
+        cudaMemcpyAsync(q, F.Rch[k], 2 * (size_t)ld * F.dprev, cudaMemcpyDeviceToDevice, X.s);
+      F.Rch[k] = q;
+    } else {
+      grow(F.Rch[k], nu);
+    }
+  }
   F.dalloc = na;
 }
 

@@ -32,7 +32,8 @@ struct PhiloxJob {  // out(i, c) = G(seed, gidx[i], c), c in [c0, c1)
   const int* gidx;
   void* out;
   long long ld;
-  int rows, c0, c1, pad;
+  int rows, c0, c1;
+  int bf16;  // FP32 form: out holds BF16 values (G is BF16-rounded there, so exactly)
 };
 
 struct SampleAJob {  // Sr(:, c) = A_i R(:, c), Sc(:, c) = A_i^T R(:, c), c in [c0, c1)

@@ -160,6 +160,9 @@ __device__ __forceinline__ void split8(const float* x, int nt, uint4* t0, uint4*
 __device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, int bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -300,17 +303,32 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
   int issued = 0;  // K steps whose MMAs were issued and committed
   float* stg = (float*)(smem + TC_STAGES * TC_STAGE_BYTES);
   const bool a_rc = jb.ta == 0, b_rc = jb.tb != 0;
+  // b_exact 2: B is BF16 with k contiguous (ldb a multiple of 8, 16-byte
+  // aligned): thread t copies the 16 bytes of row t % 128, k chunk t / 128
+  // straight into the canonical term layout of the staging slot
+  const bool b16 = jb.b_exact == 2;
+  const bool a_row = m0 + (int)(threadIdx.x & 127) < M, b_row = n0 + (int)(threadIdx.x & 127) < N;
+  const int b16_off = tile_off(threadIdx.x & 127, 8 * (threadIdx.x >> 7));
+  const __nv_bfloat16* B16 = (const __nv_bfloat16*)jb.B;
+  const __nv_bfloat16* b16_row = B16 + (long long)(n0 + (int)(threadIdx.x & 127)) * jb.ldb + 8 * (threadIdx.x >> 7);
   Feed fa = feed_init(A, a_sr, a_sk, a_rc, m0, M, kbeg);
   Feed fb = feed_init(B, b_sr, b_sk, b_rc, n0, N, kbeg);
   auto issue = [&](int u) {  // the copies of K step u into staging slot u % TC_ST (steps in order)
     const uint32_t d = smem_u32(stg + (size_t)(u % TC_ST) * 2 * TC_STG);
-    const int kleft = kend - (kbeg + u * TC_K);
+    const int k = kbeg + u * TC_K;
+    const int kleft = kend - k;
     if (a_rc) feed_issue<true>(fa, kleft, d); else feed_issue<false>(fa, kleft, d);
-    if (b_rc) feed_issue<true>(fb, kleft, d + 4 * TC_STG); else feed_issue<false>(fb, kleft, d + 4 * TC_STG);
+    if (b16) {
+      const int nv = min(max(kleft - 8 * (int)(threadIdx.x >> 7), 0), 8);  // valid k of the chunk
+      if (b_row) cp_async16(d + 4 * TC_STG + b16_off, nv > 0 ? (const void*)(b16_row + k) : (const void*)B16, 2 * nv);
+    } else if (b_rc) {
+      feed_issue<true>(fb, kleft, d + 4 * TC_STG);
+    } else {
+      feed_issue<false>(fb, kleft, d + 4 * TC_STG);
+    }
     fa.p += fa.sk16;
     fb.p += fb.sk16;
   };
-  const bool a_row = m0 + (int)(threadIdx.x & 127) < M, b_row = n0 + (int)(threadIdx.x & 127) < N;
   // one commit group per K step (empty past the end), so that waiting for
   // all but the last TC_ST - 1 groups means step t has landed
 #pragma unroll
@@ -333,7 +351,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc(const GemmJob* __rest
     if (free_ok) {
       const float* src = stg + (size_t)(t % TC_ST) * 2 * TC_STG;
       tile_split(src, na, sa, a_row);
-      tile_split(src + TC_STG, nb, sb, b_row);
+      if (b16) {
+        if (b_row)
+          *reinterpret_cast<uint4*>(sb + b16_off) =
+              *reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(src + TC_STG) + b16_off);
+      } else {
+        tile_split(src + TC_STG, nb, sb, b_row);
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (!__syncthreads_and(free_ok)) {  // the same decision in every thread

@@ -329,6 +329,14 @@ __global__ void k_philox(const PhiloxJob* __restrict__ jobs, unsigned long long 
   const int i = blockIdx.y * blockDim.x + threadIdx.x;
   if (i >= jb.rows) return;
   const unsigned g = (unsigned)jb.gidx[i];
+  if constexpr (std::is_same<T, float>::value) {
+    if (jb.bf16) {
+      __nv_bfloat16* o16 = (__nv_bfloat16*)jb.out;
+      for (int c = jb.c0; c < jb.c1; ++c)
+        o16[i + (long long)c * jb.ld] = __float2bfloat16_rn(gauss_t<T>(seed, g, (unsigned)c));
+      return;
+    }
+  }
   T* out = (T*)jb.out;
   for (int c = jb.c0; c < jb.c1; ++c) out[i + (long long)c * jb.ld] = gauss_t<T>(seed, g, (unsigned)c);
 }
