@@ -21,8 +21,11 @@
 // canonical K-major layout (8 x 8 core matrices, no swizzle) of one of two
 // term stages; one thread issues the tcgen05.mma instructions of the stage
 // and commits them to the stage's mbarrier, which the threads wait on before
-// refilling that term stage.  The accumulator (128 lanes x 128 FP32 columns)
-// is read back with tcgen05.ld and scattered to the rows crow(i) of C.
+// refilling that term stage.  A B operand stored as BF16 (b_exact = 2: the
+// FP32 form's sampling matrix) is copied 16 bytes at a time straight into
+// the canonical layout of its staging slot and moved to the term stage
+// without a split.  The accumulator (128 lanes x 128 FP32 columns) is read
+// back with tcgen05.ld and scattered to the rows crow(i) of C.
 #include <cuda_bf16.h>
 
 #include <algorithm>
